@@ -1,0 +1,257 @@
+"""ctypes loader for the FP64 CPU oracle (flame_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: this module is imported by the test suite, by the
+smoke check and by the CPU-baseline leg of the benchmark, never by the
+product path.  It compiles ``flame_oracle.c`` with the host C compiler on
+first use (or when the source is newer than the built library) and exposes
+numpy-friendly wrappers.  All arrays are float64 / complex128.
+
+State layout (shared convention, not shared code): the compact half spectrum,
+rows k1 = -K1..K1, columns k2 = 0..K2, complex128 of shape (2K1+1, K2+1);
+the k = 0 entry is ignored and the mean mode is a separate float.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "flame_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libflame_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LINEAR_ONLY = 1
+NONLINEAR_ONLY = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/libflame_oracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int),
+                ("K1", ctypes.c_int), ("K2", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("s1", ctypes.c_double),
+                ("s2", ctypes.c_double), ("t0", ctypes.c_double),
+                ("dt", ctypes.c_double), ("flags", ctypes.c_uint)]
+
+
+@dataclasses.dataclass
+class Params:
+    """Model and grid parameters (eq. (SivCurv1c), Sec. 2-3)."""
+    n1: int
+    n2: int
+    K1: int = 0          # 0 -> floor((n1 - 1) / 4)
+    K2: int = 0
+    gamma: float = 0.8
+    s1: float = 1.0      # kappa = (s1 k1, s2 k2); theta_pi = 1 as printed
+    s2: float = 1.0
+    t0: float = 200.0
+    dt: float = 1e-3
+    flags: int = 0
+
+    def __post_init__(self):
+        if self.K1 == 0:
+            self.K1 = (self.n1 - 1) // 4
+        if self.K2 == 0:
+            self.K2 = (self.n2 - 1) // 4
+
+    @property
+    def box_shape(self):
+        return (2 * self.K1 + 1, self.K2 + 1)
+
+    def _c(self):
+        return _Params(self.n1, self.n2, self.K1, self.K2, self.gamma,
+                       self.s1, self.s2, self.t0, self.dt, self.flags)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(_Params)
+            vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+            pd = ctypes.POINTER(ctypes.c_double)
+            sigs = {
+                "orc_dft": (None, [i, vp, vp, i]),
+                "orc_fft": (i, [i, vp, i]),
+                "orc_rfft2": (i, [i, i, vp, vp]),
+                "orc_irfft2": (i, [i, i, vp, vp]),
+                "orc_check": (i, [P]),
+                "orc_grad2_hat": (None, [P, vp, vp]),
+                "orc_grad2_brute": (None, [P, vp, vp]),
+                "orc_omega": (d, [P, i, i, d]),
+                "orc_step": (None, [P, vp, pd, pd, i]),
+                "orc_area": (d, [P, vp, d, d, vp, pd]),
+                "orc_step_vjp": (None, [P, vp, d, vp, pd]),
+                "orc_step_jvp": (None, [P, vp, d, vp]),
+                "orc_area_grad": (d, [P, vp, d, d, i, vp, pd]),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _check(p: Params):
+    if _load().orc_check(ctypes.byref(p._c())) != 0:
+        raise ValueError(f"invalid oracle parameters {p}")
+
+
+# ---------------------------------------------------------------- transforms
+def dft(x, sign=-1):
+    """Brute-force DFT (definition), any length."""
+    x = _c128(x)
+    y = np.empty_like(x)
+    _load().orc_dft(len(x), _ptr(x), _ptr(y), int(sign))
+    return y
+
+
+def fft(x, sign=-1):
+    """Plain recursive radix-2 FFT (power-of-two length), unnormalised."""
+    x = _c128(x).copy()
+    if _load().orc_fft(len(x), _ptr(x), int(sign)) != 0:
+        raise ValueError("length must be a power of two")
+    return x
+
+
+def rfft2(x):
+    """Unnormalised 2-D analysis of a real (n1, n2) array -> (n1, n2/2+1)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n1, n2 = x.shape
+    out = np.empty((n1, n2 // 2 + 1), dtype=np.complex128)
+    if _load().orc_rfft2(n1, n2, _ptr(x), _ptr(out)) != 0:
+        raise ValueError("sizes must be powers of two")
+    return out
+
+
+def irfft2(X, n2):
+    """Unnormalised 2-D synthesis from a (n1, n2/2+1) half spectrum."""
+    X = _c128(X)
+    n1 = X.shape[0]
+    assert X.shape[1] == n2 // 2 + 1
+    out = np.empty((n1, n2), dtype=np.float64)
+    if _load().orc_irfft2(n1, n2, _ptr(X), _ptr(out)) != 0:
+        raise ValueError("sizes must be powers of two")
+    return out
+
+
+# --------------------------------------------------------------------- model
+def grad2_hat(p: Params, state):
+    """Box coefficients of |grad Phi|^2 through the FFT (k = 0 = mean)."""
+    _check(p)
+    s = _c128(state)
+    assert s.shape == p.box_shape
+    out = np.empty_like(s)
+    _load().orc_grad2_hat(ctypes.byref(p._c()), _ptr(s), _ptr(out))
+    return out
+
+
+def grad2_brute(p: Params, state):
+    """Literal convolution sum of eq. (SivCurv1c) (tiny boxes only)."""
+    _check(p)
+    s = _c128(state)
+    out = np.empty_like(s)
+    _load().orc_grad2_brute(ctypes.byref(p._c()), _ptr(s), _ptr(out))
+    return out
+
+
+def omega(p: Params, k1: int, k2: int, t: float) -> float:
+    return _load().orc_omega(ctypes.byref(p._c()), int(k1), int(k2), float(t))
+
+
+def step(p: Params, state, mean: float, t: float, nsteps: int = 1):
+    """nsteps explicit Euler steps; returns (state, mean, t) (copies)."""
+    _check(p)
+    s = _c128(state).copy()
+    assert s.shape == p.box_shape
+    m = ctypes.c_double(mean)
+    tt = ctypes.c_double(t)
+    _load().orc_step(ctypes.byref(p._c()), _ptr(s), ctypes.byref(m),
+                     ctypes.byref(tt), int(nsteps))
+    return s, m.value, tt.value
+
+
+def area(p: Params, state, mean: float, t: float, grad: bool = False):
+    """Surface area; with grad=True also (dA/dPhi box, dA/dPhi_0)."""
+    _check(p)
+    s = _c128(state)
+    g = np.empty_like(s) if grad else None
+    gm = ctypes.c_double(0.0)
+    A = _load().orc_area(ctypes.byref(p._c()), _ptr(s), float(mean), float(t),
+                         _ptr(g) if grad else None, ctypes.byref(gm))
+    if grad:
+        return A, g, gm.value
+    return A
+
+
+def step_vjp(p: Params, state, t: float, lam):
+    """Transposed step Jacobian applied to lam; returns (lam', dgamma)."""
+    s = _c128(state)
+    lam = _c128(lam).copy()
+    dg = ctypes.c_double(0.0)
+    _load().orc_step_vjp(ctypes.byref(p._c()), _ptr(s), float(t), _ptr(lam),
+                         ctypes.byref(dg))
+    return lam, dg.value
+
+
+def step_jvp(p: Params, state, t: float, d):
+    """Step Jacobian applied to d (k = 0 slot = mean-mode component)."""
+    s = _c128(state)
+    d = _c128(d).copy()
+    _load().orc_step_jvp(ctypes.byref(p._c()), _ptr(s), float(t), _ptr(d))
+    return d
+
+
+def area_grad(p: Params, state0, mean0: float, t: float, nsteps: int):
+    """(L, dL/dPhi0 box with k=0 slot = dL/dPhi_0, dL/dgamma) for L = A(T)."""
+    _check(p)
+    s = _c128(state0)
+    g = np.empty_like(s)
+    dg = ctypes.c_double(0.0)
+    L = _load().orc_area_grad(ctypes.byref(p._c()), _ptr(s), float(mean0),
+                              float(t), int(nsteps), _ptr(g), ctypes.byref(dg))
+    return L, g, dg.value
+
+
+def half_weights(p: Params):
+    """Weights of the full-spectrum inner product on the compact box."""
+    w = np.full(p.box_shape, 2.0)
+    w[:, 0] = 1.0
+    return w
+
+
+def inner(p: Params, a, b) -> float:
+    """<a, b> = Re sum over the full spectrum of conj(a) b (Hermitian a, b)."""
+    return float(np.sum(half_weights(p) * np.real(np.conj(a) * b)))
