@@ -1,0 +1,292 @@
+"""Benchmark of the spectral flame step on GB300.
+
+Workload (the large memory-bound configuration): one flame on a 4096 x 8192
+(theta, phi) grid, FP32 FFTs and pointwise work with the FP64 mean mode and
+time, seeded spectrum |k| <= 256 of amplitude 1e-3 (1+|k|)^-2, gamma = 0.8,
+t0 = 200, dt = 1e-3.  A "step" is one explicit Euler step of the model
+(passes A, B, C: the whole hot path).  Metric: grid-point updates per second
+(N1 N2 per step) and the HBM roofline of the dominant pass.
+
+--impl ours (default): the CUDA library through its C ABI.
+--impl reference: the FP64 CPU oracle on the host cores, on a bounded
+  sample of the same workload.
+
+Multi-GPU: every rank steps its own independent flame (replicas, no
+collective on the data path); value = all ranks' updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="flame-step-4096x8192-fp32mixed", n1=4096, n2=8192, prec="fp32", kmax=256,
+                seed=0, gamma=0.8, t0=200.0, dt=1e-3)
+L2_BYTES = 129 * 1024 * 1024
+FLUSH_BYTES = 512 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def pass_bytes(n1, n2, K1, K2, esz):
+    """Algorithmic HBM bytes of passes A, B, C (each array read or written once)."""
+    box = (2 * K1 + 1) * (K2 + 1) * esz
+    col = n1 * (K2 + 1) * esz
+    return [box + 2 * col, 2 * col + col, col + 2 * box]
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_step_time(w, nsteps=1):
+    """Seconds per oracle step (FP64 C oracle, OpenMP over rows/columns) on
+    the full workload grid; returns (seconds per step, threads)."""
+    from oracle import oracle
+    from paper_0911_2889_gb300 import inputs
+    oracle.build()
+    p = oracle.Params(w["n1"], w["n2"], gamma=w["gamma"], t0=w["t0"], dt=w["dt"])
+    st = inputs.spectrum_ic(w["n1"], w["n2"], w["kmax"], w["seed"])
+    t0 = time.perf_counter()
+    oracle.step(p, st, 0.0, w["t0"], nsteps)
+    dt = (time.perf_counter() - t0) / nsteps
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dt, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOAD
+    pts = w["n1"] * w["n2"]
+    for _ in range(args.warmup):
+        cpu_oracle_step_time(w)
+    times = []
+    threads = 1
+    for _ in range(args.steps):
+        dt, threads = cpu_oracle_step_time(w)
+        times.append(dt)
+    sec = sum(times) / len(times)
+    v = pts / sec
+    line = {
+        "impl": "reference", "metric": "grid_point_updates_per_s", "value": v, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["workload"], "grid": [w["n1"], w["n2"]]},
+        "cpu_baseline": {"value": v, "unit": "points/s", "cores": threads, "kind": "oracle",
+                         "sample": "one full FP64 oracle step of the 4096x8192 workload per timed step"},
+        "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_0911_2889_gb300 import flame, inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = WORKLOAD
+    n1, n2 = w["n1"], w["n2"]
+    f = flame.Flame(n1, n2, gamma=w["gamma"], t0=w["t0"], dt=w["dt"], prec=w["prec"])
+    st0 = inputs.spectrum_ic(n1, n2, w["kmax"], w["seed"] + rank, K1=f.K1, K2=f.K2)
+    state = torch.from_numpy(st0).cuda().to(f.cdtype)
+    mean = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), w["t0"], dtype=torch.float64, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    esz = 8 if w["prec"] == "fp32" else 16
+    pbytes = pass_bytes(n1, n2, f.K1, f.K2, esz)
+
+    def one_step(ev=None):
+        for ps in range(3):
+            if ev is not None:
+                ev[ps].record(stream)
+            flame.flame_step_pass(f.h, ps, state, mean, t, stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    f.sync_status()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()  # > L2, outside the timed interval of the step
+            one_step(evs[k])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    f.sync_status()
+    per_pass = [[evs[k][ps].elapsed_time(evs[k][ps + 1]) for k in range(args.steps)] for ps in range(3)]
+    step_ms = [sum(per_pass[ps][k] for ps in range(3)) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    pts = n1 * n2
+    value = pts * args.steps * world / (total_ms * 1e-3)
+    avg = [sum(v) / len(v) for v in per_pass]
+    dom = max(range(3), key=lambda i: avg[i])
+    peak, peak_kind = _peaks()
+    achieved = pbytes[dom] / (avg[dom] * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers (pinned), copies
+    # of the step's inputs and results inside the timed region
+    hs = state.cpu().pin_memory()
+    hm = mean.cpu().pin_memory()
+    ht = t.cpu().pin_memory()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        e0.record(stream)
+        state.copy_(hs, non_blocking=True)
+        mean.copy_(hm, non_blocking=True)
+        t.copy_(ht, non_blocking=True)
+        f.step(state, mean, t, 1, stream)
+        hs.copy_(state, non_blocking=True)
+        hm.copy_(mean, non_blocking=True)
+        ht.copy_(t, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        nk = k + 1
+    e2e_value = pts * nk / (e2e_ms * 1e-3) * world
+    io_bytes = state.numel() * state.element_size() + 16
+
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tr = json.load(open(prof))
+            key = f"{w['workload']}:pass{'ABC'[dom]}"
+            traffic = tr.get(key)
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            sec, threads = cpu_oracle_step_time(w)
+            cpu = {"value": pts / sec, "unit": "points/s", "cores": threads, "kind": "oracle",
+                   "sample": "one FP64 oracle step of the same 4096x8192 workload"}
+        line = {
+            "metric": "grid_point_updates_per_s", "value": value, "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["workload"], "grid": [n1, n2], "kmax": w["kmax"],
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "hbm", "kernel": f"pass{'ABC'[dom]}", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "alg_bytes": pbytes[dom], "avg_ms": avg[dom]},
+            "passes_ms": {"A": avg[0], "B": avg[1], "C": avg[2]},
+            "step_effective_gbs": sum(pbytes) / (total_ms / args.steps * 1e-3) / 1e9,
+            "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk.summary(),
+            "wall_s": wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    f.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

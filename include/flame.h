@@ -1,0 +1,195 @@
+/*
+ * flame.h -- C ABI of the GB300 (sm_103a) spectral stepper for the
+ * Sivashinsky-type model of an expanding spherical flame
+ * (V. Karlin, "Global communications in multiprocessor simulations of
+ * flames", Sec. 2 eq. (SivCurv1c) and Sec. 3).
+ *
+ * Model (eq. (SivCurv1c), forcing f = 0, r0(t) = t, Sec. 2):
+ *   d Phi_k/dt = omega_k(t) Phi_k + c(t) [|grad Phi|^2]_k,
+ *   omega_k(t) = -|kappa|^2/r0^2 + gamma |kappa|/(2 r0),  c(t) = 1/(2 r0^2),
+ *   kappa = (s1 k1, s2 k2)   (s1 = s2 = theta_pi as printed in eq. (SivCurv1c)).
+ * The quadratic term of eq. (SivCurv1c), -theta_pi^2/(2 r0^2) sum_l
+ * l.(k-l) Phi_l Phi_{k-l}, is exactly c(t) times the coefficient of
+ * |grad Phi|^2; it is evaluated through zero-padded FFTs (the augmented
+ * array of Sec. 3, alias-free because N_i >= 4 K_i + 1).
+ *
+ * Grid and coefficients: x_i = 2 pi j_i / N_i on an N1 x N2 (theta, phi) grid,
+ * Phi(x) = sum_k Phi_k exp(i k.x).
+ *
+ * STATE LAYOUT ("compact box"): the retained half spectrum, rows
+ * k1 = -K1..K1, columns k2 = 0..K2, row-major with k2 fastest, complex
+ * interleaved (re, im): double2 for FLAME_FP64, float2 for FLAME_FP32_MIXED.
+ * (2 K1 + 1) * (K2 + 1) entries.  The k2 = 0 column is Hermitian
+ * (Phi_{-k1,0} = conj(Phi_{k1,0}), the symmetrization of Sec. 3); the k = 0
+ * entry is ignored and written as 0: the mean mode Phi_0 lives in a separate
+ * double.  The time t is a double on the device.
+ *
+ * OWNERSHIP: the caller owns every buffer passed in (device memory unless
+ * stated).  A handle owns its plan tables, its workspace and its captured
+ * graphs.  All calls are asynchronous on the given stream (a cudaStream_t
+ * passed as void*; NULL = the legacy default stream) except flame_create,
+ * flame_destroy and flame_sync_status, which synchronise.
+ *
+ * ERRORS: no call aborts.  A call that returns a non-OK status has enqueued
+ * no work on the stream.  flame_last_error() gives a thread-local message for
+ * the last failing call.  Errors detected on the device (non-finite values)
+ * set a status word in the handle, read and cleared by flame_sync_status().
+ *
+ * A handle is not thread-safe: calls on one handle must not overlap in time
+ * on the host, and two enqueued calls on one handle must be ordered (same
+ * stream or an event), because they share the handle's workspace.
+ */
+#ifndef FLAME_H
+#define FLAME_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FLAME_OK = 0,
+    FLAME_EINVAL = 1,        /* bad argument (null pointer, size, params)   */
+    FLAME_ENOMEM = 2,        /* device or host allocation failed            */
+    FLAME_ECUDA = 3,         /* a CUDA runtime call failed                  */
+    FLAME_EUNSUPPORTED = 4,  /* valid request the library does not handle   */
+    FLAME_ETIMEOUT = 5,      /* a bounded device-side wait ran out          */
+    FLAME_ENONFINITE = 6     /* a step produced NaN or Inf                  */
+} flame_status;
+
+typedef enum {
+    FLAME_FP64 = 0,          /* everything in double precision              */
+    FLAME_FP32_MIXED = 1     /* FFTs and pointwise work in FP32; twiddles
+                                generated in FP64; mean mode, time and the
+                                step coefficients in FP64                    */
+} flame_precision;
+
+/* Test modes (flags): drop one of the two terms of eq. (SivCurv1c). */
+#define FLAME_LINEAR_ONLY 1u
+#define FLAME_NONLINEAR_ONLY 2u
+
+typedef struct {
+    int n_theta;       /* N1, power of two, 16..4096                        */
+    int n_phi;         /* N2, power of two, 32..8192                        */
+    int K1, K2;        /* retained harmonics; 0 = floor((N-1)/4); 4K+1 <= N */
+    double gamma;      /* density contrast gamma = 1 - rho_b/rho_u          */
+    double theta_pi;   /* integer theta_pi of eq. (SivCurv1c)               */
+    double s1, s2;     /* kappa = (s1 k1, s2 k2); 0 = theta_pi              */
+    double t0;         /* initial time (r0 = t), t0 > 0                     */
+    double dt;         /* explicit Euler step, dt > 0                       */
+    flame_precision prec;
+    unsigned flags;    /* FLAME_LINEAR_ONLY, FLAME_NONLINEAR_ONLY or 0      */
+} flame_params;
+
+typedef struct flame_ctx *flame_t;
+
+/* Creates a handle: validates params (EINVAL / EUNSUPPORTED), resolves K and
+ * s, builds the FP64-generated twiddle tables and allocates the workspace on
+ * the current CUDA device (ENOMEM, ECUDA).  *out is set only on success.
+ * Synchronises the device. */
+flame_status flame_create(const flame_params *params, flame_t *out);
+
+/* Destroys a handle (NULL is accepted).  Synchronises the device. */
+flame_status flame_destroy(flame_t h);
+
+/* Copies the resolved parameters (K1, K2, s1, s2 filled in) into *out. */
+flame_status flame_get_params(flame_t h, flame_params *out);
+
+/* Number of complex entries of the compact box, (2 K1 + 1) * (K2 + 1). */
+size_t flame_state_len(flame_t h);
+
+/* Standalone 2-D real FFTs over the handle's N1 x N2 grid, unnormalised,
+ * in the handle's precision (double or float):
+ *   r2c: spec_out[k1][k2] = sum_{j1,j2} real_in[j1][j2]
+ *                            exp(-2 pi i (k1 j1/N1 + k2 j2/N2)),
+ *        real_in N1 x N2 row-major, spec_out N1 x (N2/2+1) complex row-major.
+ *   c2r: real_out[j1][j2] = sum over the Hermitian-extended spectrum of
+ *        spec_in[k1][k2] exp(+2 pi i (...)), so c2r(r2c(x)) = N1 N2 x.
+ *        spec_in is not modified (the handle's workspace is used).
+ * The 2-D transform is the tensor product of 1-D ones (Sec. 2): rows, then
+ * columns for r2c; columns, then rows for c2r (Sec. 3).  EINVAL on null
+ * pointers.  Buffers must be 16-byte aligned. */
+flame_status flame_fft_r2c(flame_t h, const void *real_in, void *spec_out,
+                           void *stream);
+flame_status flame_fft_c2r(flame_t h, const void *spec_in, void *real_out,
+                           void *stream);
+
+/* Advances the state by nsteps explicit Euler steps of eq. (SivCurv1c):
+ *   Phi_k <- Phi_k + dt (omega_k(t_n) Phi_k + c(t_n) ghat_k)   (k != 0),
+ *   Phi_0 <- Phi_0 + dt c(t_n) ghat_0,
+ * where ghat is the box part of the normalised analysis of |grad Phi|^2,
+ * followed by the symmetrization of the k2 = 0 column (Sec. 3) and
+ * t <- t0 + (n + 1) dt with n = round((t - t0)/dt).
+ * state: compact box (see above), in place.  mean_mode, t: one device double
+ * each, in place.  nsteps >= 0 (0 is a no-op).  For nsteps > 1 the step
+ * sequence is replayed from a captured CUDA graph (captured on first use per
+ * (state, mean_mode, t, nsteps) binding).  Non-finite results set
+ * FLAME_ENONFINITE in the handle's device status word. */
+flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
+                        int nsteps, void *stream);
+
+/* Enqueues one pass of one step: pass 0 = A (derivatives and column
+ * inverse FFT), 1 = B (row inverse FFT, |grad Phi|^2, row forward FFT),
+ * 2 = C (column forward FFT, linear operator, Euler update, symmetrization,
+ * mean mode, time).  Calling passes 0, 1, 2 in order on one stream is
+ * exactly flame_step(h, state, mean_mode, t, 1, stream); the split exists so
+ * that each kernel can be timed with events on the launching stream.
+ * EINVAL for pass outside 0..2 or null pointers. */
+flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode, double *t,
+                             void *stream);
+
+/* Advances nflames independent flames (each with its own handle, state,
+ * mean mode and time; grids may differ; all handles must have the same
+ * precision) by nsteps steps.  Flames of equal grid size are grouped so that
+ * each pass is one launch per size class; the nsteps loop is one captured
+ * CUDA graph.  Results equal nflames separate flame_step calls.  hs, states,
+ * mean_modes and ts are HOST arrays of nflames entries (device pointers). */
+flame_status flame_step_batch(const flame_t *hs, void *const *states,
+                              double *const *mean_modes, double *const *ts,
+                              int nflames, int nsteps, void *stream);
+
+/* Flame surface area of the state at time *t (project-defined objective,
+ * the equatorial surface element of the model's geometry):
+ *   A = sum_grid (2 pi)^2/(N1 N2 s1 s2) R sqrt(R^2 + |grad Phi|^2),
+ *   R = r0(t) + Phi(x).
+ * Writes A (double, device) to area_out.  If dA_dstate is not NULL it
+ * receives dA/dPhi_k on the compact box (precision of the handle) for the
+ * full-spectrum inner product <X, Y> = Re sum_{all k} conj(X_k) Y_k, and
+ * dA_dmean (device double, may be NULL) receives dA/dPhi_0. */
+flame_status flame_area(flame_t h, const void *state, const double *mean_mode,
+                        const double *t, double *area_out, void *dA_dstate,
+                        double *dA_dmean, void *stream);
+
+/* Reverse-mode gradient through nsteps Euler steps (the discrete adjoint of
+ * flame_step) starting from (state0, mean0, t_start = t0 of the handle's
+ * lattice, read from the device double t_start):
+ *   given lambda_T = dL/dPhi(T) (compact box) and lambda0_T = dL/dPhi_0(T),
+ *   returns grad_state0 = dL/dPhi(t_start) (compact box), grad_mean0 =
+ *   dL/dPhi_0(t_start) and grad_gamma = dL/dgamma (device doubles).
+ * The forward trajectory is recomputed from checkpoints stored every
+ * ckpt_every steps (1 <= ckpt_every <= nsteps).  Gradients use the
+ * full-spectrum inner product of flame_area.  state0, lambda_T and
+ * grad_state0 are device buffers in the handle's precision; mean0,
+ * t_start, lambda0_T, grad_mean0, grad_gamma are device doubles. */
+flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0,
+                           const double *t_start, int nsteps, int ckpt_every,
+                           const void *lambda_T, const double *lambda0_T,
+                           void *grad_state0, double *grad_mean0,
+                           double *grad_gamma, void *stream);
+
+/* Synchronises the handle's device status word and returns it
+ * (FLAME_OK, FLAME_ENONFINITE or FLAME_ETIMEOUT); clears it. */
+flame_status flame_sync_status(flame_t h);
+
+/* Static description of a status code. */
+const char *flame_status_str(flame_status s);
+
+/* Thread-local message of the last failing call on this host thread. */
+const char *flame_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLAME_H */

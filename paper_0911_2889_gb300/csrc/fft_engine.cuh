@@ -1,0 +1,300 @@
+// fft_engine.cuh -- device-side FFT building blocks for sm_103a.
+//
+// A "line" is one 1-D transform (a row or a column of the 2-D grid, Sec. 2:
+// the 2-D FFT is the tensor product of 1-D ones).  Every thread carries TWO
+// independent lines in lock step (the two halves of a V = float2 / double2):
+// the FP32 path then runs on the paired FP32 instructions of sm_100+
+// (__fadd2_rn / __fmul2_rn / __ffma2_rn), which halves the issue slots of
+// the butterflies.
+//
+// Layout of a length-N line (N = 2^logN, 16 <= N <= 8192) over T = N/16
+// threads: thread t holds x[r] = element t + r*T, r = 0..15.  A transform is
+// a sequence of radix-16 Stockham passes (stride Ns = 16^s) followed, when
+// logN is not a multiple of 4, by one radix-2/4/8 pass.  Between passes the
+// line is exchanged through shared memory (two planes, re and im, padded by
+// one slot every 16 to keep stores bank-conflict free).  The input of the
+// first pass and the output of the last pass are both in the t + r*T layout,
+// so global loads and stores of consecutive t are coalesced.
+//
+// Twiddles come from a per-length table generated in FP64 on the device
+// (sincospi) and rounded once to the working precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <type_traits>
+#include <utility>
+
+namespace flame {
+
+// ----------------------------------------------------------------------------
+// Two-line vector arithmetic
+// ----------------------------------------------------------------------------
+template <class R> struct VecOf;
+template <> struct VecOf<float> { using type = float2; using c = float2; };
+template <> struct VecOf<double> { using type = double2; using c = double2; };
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vbc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 vzero(float2) { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vbc(double s) { return make_double2(s, s); }
+__device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+
+// Complex number whose re and im each hold the two lines.
+template <class V> struct CV { V re, im; };
+
+template <class V> __device__ __forceinline__ CV<V> cadd(CV<V> a, CV<V> b) {
+    return {vadd(a.re, b.re), vadd(a.im, b.im)};
+}
+template <class V> __device__ __forceinline__ CV<V> csub(CV<V> a, CV<V> b) {
+    return {vsub(a.re, b.re), vsub(a.im, b.im)};
+}
+// a + s*i*b and a - s*i*b for s = +-1 (no explicit negation needed)
+template <int S, class V> __device__ __forceinline__ CV<V> cadd_rot(CV<V> a, CV<V> b) {
+    if constexpr (S > 0) return {vsub(a.re, b.im), vadd(a.im, b.re)};
+    else return {vadd(a.re, b.im), vsub(a.im, b.re)};
+}
+template <int S, class V> __device__ __forceinline__ CV<V> csub_rot(CV<V> a, CV<V> b) {
+    return cadd_rot<-S>(a, b);
+}
+// a * (wr + i wi) with the same scalar twiddle on both lines
+template <class V, class R> __device__ __forceinline__ CV<V> cmul_s(CV<V> a, R wr, R wi) {
+    V vr = vbc(wr), vi = vbc(wi);
+    return {vsub(vmul(a.re, vr), vmul(a.im, vi)), vfma(a.re, vi, vmul(a.im, vr))};
+}
+template <class V, class R> __device__ __forceinline__ CV<V> cscale(CV<V> a, R s) {
+    V v = vbc(s);
+    return {vmul(a.re, v), vmul(a.im, v)};
+}
+
+// compile-time loop
+template <int B, int E, class F> __device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// cos / sin of 2 pi e / 16
+struct Roots16 {
+    static constexpr double C1 = 0.923879532511286756128183189396788933;  // cos(pi/8)
+    static constexpr double S1 = 0.382683432365089771728459984030398866;  // sin(pi/8)
+    static constexpr double H = 0.707106781186547524400844362104849039;   // sqrt(2)/2
+    static constexpr double c[16] = {1.0, C1, H, S1, 0.0, -S1, -H, -C1,
+                                     -1.0, -C1, -H, -S1, 0.0, S1, H, C1};
+    static constexpr double s[16] = {0.0, S1, H, C1, 1.0, C1, H, S1,
+                                     0.0, -S1, -H, -C1, -1.0, -C1, -H, -S1};
+};
+
+// a * exp(DIR 2 pi i E / R), R | 16, everything decided at compile time
+template <int E, int R, int DIR, class V> __device__ __forceinline__ CV<V> tw_const(CV<V> a) {
+    using Real = decltype(a.re.x);
+    constexpr int e = ((E % R) * (16 / R)) & 15;
+    constexpr double cr = Roots16::c[e];
+    constexpr double ci = DIR * Roots16::s[e];
+    if constexpr (ci == 0.0) {
+        if constexpr (cr > 0) return a;
+        else return {vsub(vzero(a.re), a.re), vsub(vzero(a.im), a.im)};
+    } else if constexpr (cr == 0.0) {
+        // multiply by +-i
+        if constexpr (ci > 0) return {vsub(vzero(a.re), a.im), a.re};
+        else return {a.im, vsub(vzero(a.im), a.re)};
+    } else if constexpr (cr == ci || cr == -ci) {
+        // (cr + i ci) a = cr (a + i (ci/cr) a)
+        constexpr int sg = (cr == ci) ? 1 : -1;
+        CV<V> b = cadd_rot<sg>(a, a);
+        return cscale(b, (Real)cr);
+    } else {
+        return cmul_s(a, (Real)cr, (Real)ci);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// In-register DFTs, natural order in and out.  DIR = -1 forward, +1 inverse.
+// ----------------------------------------------------------------------------
+template <int R, int DIR, class V> __device__ __forceinline__ void dft(CV<V> *x);
+
+template <int DIR, class V> __device__ __forceinline__ void dft2(CV<V> *x) {
+    CV<V> a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+}
+template <int DIR, class V> __device__ __forceinline__ void dft4(CV<V> *x) {
+    CV<V> s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
+    CV<V> s13 = cadd(x[1], x[3]), d13 = csub(x[1], x[3]);
+    x[0] = cadd(s02, s13);
+    x[2] = csub(s02, s13);
+    x[1] = cadd_rot<DIR>(d02, d13);
+    x[3] = csub_rot<DIR>(d02, d13);
+}
+
+// R = R1 * R2: R2 DFTs of size R1 over n = R2 n1 + n2, twiddles
+// w_R^(n2 k1), then R1 DFTs of size R2 over n2; output index k1 + R1 k2.
+template <int R1, int R2, int DIR, class V> __device__ __forceinline__ void dft_split(CV<V> *x) {
+    constexpr int R = R1 * R2;
+    CV<V> y[R];
+    static_for<0, R2>([&](auto n2c) {
+        constexpr int n2 = decltype(n2c)::value;
+        CV<V> s[R1];
+        static_for<0, R1>([&](auto n1c) {
+            constexpr int n1 = decltype(n1c)::value;
+            s[n1] = x[R2 * n1 + n2];
+        });
+        dft<R1, DIR>(s);
+        static_for<0, R1>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            y[n2 * R1 + k1] = tw_const<n2 * k1, R, DIR>(s[k1]);
+        });
+    });
+    static_for<0, R1>([&](auto k1c) {
+        constexpr int k1 = decltype(k1c)::value;
+        CV<V> s[R2];
+        static_for<0, R2>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            s[n2] = y[n2 * R1 + k1];
+        });
+        dft<R2, DIR>(s);
+        static_for<0, R2>([&](auto k2c) {
+            constexpr int k2 = decltype(k2c)::value;
+            x[k1 + R1 * k2] = s[k2];
+        });
+    });
+}
+
+template <int R, int DIR, class V> __device__ __forceinline__ void dft(CV<V> *x) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) dft2<DIR>(x);
+    else if constexpr (R == 4) dft4<DIR>(x);
+    else if constexpr (R == 8) dft_split<4, 2, DIR>(x);
+    else if constexpr (R == 16) dft_split<4, 4, DIR>(x);
+    else static_assert(R <= 16, "radix");
+}
+
+// ----------------------------------------------------------------------------
+// Twiddle tables.  For a line of length N = 2^logN the table holds, in order:
+//   for each radix-16 pass s >= 1 (stride Ns = 16^s):
+//       w[(r-1) Ns + m] = exp(2 pi i r m / (16 Ns)),  r = 1..15, m < Ns
+//   for the final radix-rho pass (rho = 2^(logN mod 4) > 1, Ns = N / rho):
+//       w[(q-1) Ns + m] = exp(2 pi i q m / N),        q = 1..rho-1, m < Ns
+//   real-transform table (used when N is the half length of a 2N real FFT):
+//       w[k] = exp(2 pi i k / (2N)),                  k < N
+// Stored with the + sign; forward transforms use the conjugate.
+// ----------------------------------------------------------------------------
+__host__ __device__ inline int tw_pass_offset(int s) {  // offset of pass s >= 1
+    int off = 0, ns = 16;
+    for (int q = 1; q < s; ++q) { off += 15 * ns; ns <<= 4; }
+    return off;
+}
+__host__ __device__ inline int tw_final_offset(int logN) { return tw_pass_offset(logN >> 2); }
+__host__ __device__ inline int tw_real_offset(int logN) {
+    int rho = 1 << (logN & 3);
+    int N = 1 << logN;
+    return tw_final_offset(logN) + (rho - 1) * (N / rho);
+}
+__host__ __device__ inline int tw_table_len(int logN) { return tw_real_offset(logN) + (1 << logN); }
+
+// ----------------------------------------------------------------------------
+// Shared-memory exchange
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ inline int plane_len(int N) { return N + (N >> 4); }
+
+// Barrier over the threads that share the exchange buffers.
+struct CtaBarrier {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+template <class V> struct Planes {
+    V *re, *im;
+    __device__ __forceinline__ void st(int i, CV<V> v) const { re[spad(i)] = v.re; im[spad(i)] = v.im; }
+    __device__ __forceinline__ CV<V> ld(int i) const { return {re[spad(i)], im[spad(i)]}; }
+};
+
+// Loads the twiddle of a table entry (stored with + sign) for direction DIR.
+template <int DIR, class C> __device__ __forceinline__ void load_tw(const C *tab, int i, decltype(C::x) &wr,
+                                                                    decltype(C::x) &wi) {
+    C w = __ldg(tab + i);
+    wr = w.x;
+    wi = (DIR > 0) ? w.y : -w.y;
+}
+
+// Full transform of one pair of lines of length N = 2^logN held as x[16].
+// tw: twiddle table of this length (see above).  All threads of the barrier
+// must call this with the same logN.  On return the result is in x in the
+// same t + r*T layout; shared memory may still be read by other threads, so
+// callers synchronise before reusing it.
+template <int DIR, class V, class C, class Bar>
+__device__ __forceinline__ void line_fft(CV<V> (&x)[16], int logN, int t, const Planes<V> &sm,
+                                         const C *__restrict__ tw, Bar bar) {
+    using Real = decltype(C::x);
+    const int N = 1 << logN;
+    const int T = N >> 4;
+    const int P16 = logN >> 2;
+    const int lr = logN & 3;
+    const C *twp = tw;
+#pragma unroll 1
+    for (int s = 0; s < P16; ++s) {
+        const int Ns = 1 << (4 * s);
+        if (s > 0) {
+            const int m = t & (Ns - 1);
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                Real wr, wi;
+                load_tw<DIR>(twp, (r - 1) * Ns + m, wr, wi);
+                x[r] = cmul_s(x[r], wr, wi);
+            }
+            twp += 15 * Ns;
+        }
+        dft<16, DIR>(x);
+        const bool last = (s == P16 - 1) && (lr == 0);
+        if (!last) {
+            const int idxD = ((t >> (4 * s)) << (4 * s + 4)) + (t & (Ns - 1));
+            bar();
+#pragma unroll
+            for (int r = 0; r < 16; ++r) sm.st(idxD + r * Ns, x[r]);
+            bar();
+#pragma unroll
+            for (int r = 0; r < 16; ++r) x[r] = sm.ld(t + r * T);
+        }
+    }
+    if (lr > 0) {
+        auto final_pass = [&](auto rhoc) {
+            constexpr int rho = decltype(rhoc)::value;
+            constexpr int B = 16 / rho;  // butterflies per thread
+            const int Ns = N / rho;
+            const C *twf = tw + tw_final_offset(logN);
+#pragma unroll
+            for (int mm = 0; mm < B; ++mm) {
+                const int j = t + mm * T;
+                CV<V> y[rho];
+#pragma unroll
+                for (int q = 0; q < rho; ++q) y[q] = x[mm + q * B];
+#pragma unroll
+                for (int q = 1; q < rho; ++q) {
+                    Real wr, wi;
+                    load_tw<DIR>(twf, (q - 1) * Ns + j, wr, wi);
+                    y[q] = cmul_s(y[q], wr, wi);
+                }
+                dft<rho, DIR>(y);
+#pragma unroll
+                for (int q = 0; q < rho; ++q) x[mm + q * B] = y[q];
+            }
+        };
+        if (lr == 1) final_pass(std::integral_constant<int, 2>{});
+        else if (lr == 2) final_pass(std::integral_constant<int, 4>{});
+        else final_pass(std::integral_constant<int, 8>{});
+    }
+}
+
+}  // namespace flame

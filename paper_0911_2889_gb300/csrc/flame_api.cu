@@ -1,0 +1,504 @@
+// flame_api.cu -- host runtime behind the C ABI of include/flame.h:
+// parameter validation, handle and workspace ownership, twiddle tables,
+// launch sequencing, CUDA-graph capture of multi-step calls, ensembles,
+// error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "flame.h"
+#include "flame_internal.h"
+#include "fft_engine.cuh"
+
+using flame::FlameDesc;
+using flame::Ops;
+using flame::StepArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+flame_status fail(flame_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) return fail(FLAME_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Host-side fault injection for the error-path tests:
+// FLAME_FAULT_INJECT=alloc|launch|param makes the next matching call fail
+// before it touches the device.
+bool inject(const char *what) {
+    const char *v = getenv("FLAME_FAULT_INJECT");
+    return v && strcmp(v, what) == 0;
+}
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+constexpr int kGraphChunk = 256;  // steps per captured graph
+constexpr int kGraphCache = 8;
+
+}  // namespace
+
+struct GraphEntry {
+    const void *state;
+    const double *mean, *t;
+    int n;
+    cudaGraphExec_t exec;
+};
+
+struct flame_ctx {
+    flame_params p;  // resolved
+    StepArgs sa;
+    int logn1, logm;
+    int device;
+    size_t csz;       // bytes of one complex element
+    void *tw1, *twm;  // twiddle tables
+    void *uv, *gk;    // step workspaces
+    void *spec;       // c2r workspace, N1 x (N2/2 + 1)
+    double *dscal;    // [0]: t_n copy
+    int *status;
+    cudaStream_t cap;  // capture stream
+    std::vector<GraphEntry> graphs;
+    // ensemble state (owned by the first handle of a batch call)
+    void *batch_desc = nullptr;
+    size_t batch_cap = 0;
+    std::vector<FlameDesc> batch_key;
+    int batch_n = 0;
+    cudaGraphExec_t batch_exec = nullptr;
+};
+
+namespace {
+
+template <class R> flame_status alloc_tables(flame_ctx *h) {
+    using C = typename Ops<R>::C;
+    CUDA_TRY(Ops<R>::prepare());
+    CUDA_TRY(Ops<R>::init_twiddles(static_cast<C *>(h->tw1), h->logn1, h->cap));
+    CUDA_TRY(Ops<R>::init_twiddles(static_cast<C *>(h->twm), h->logm, h->cap));
+    return FLAME_OK;
+}
+
+void free_ctx(flame_ctx *h) {
+    if (!h) return;
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+    cudaFree(h->batch_desc);
+    cudaFree(h->tw1);
+    cudaFree(h->twm);
+    cudaFree(h->uv);
+    cudaFree(h->gk);
+    cudaFree(h->spec);
+    cudaFree(h->dscal);
+    cudaFree(h->status);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
+    FlameDesc d;
+    memset(&d, 0, sizeof d);  // descriptors are compared bytewise
+    d.a = h->sa;
+    d.state = state;
+    d.uv = h->uv;
+    d.gk = h->gk;
+    d.tw1 = h->tw1;
+    d.twm = h->twm;
+    d.t_in = t;
+    d.t_copy = h->dscal;
+    d.mean = mean;
+    d.t_out = t;
+    d.status = h->status;
+    return d;
+}
+
+cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
+    cudaError_t e;
+    if (h->p.prec == FLAME_FP64) {
+        if ((e = Ops<double>::passA(d, s)) != cudaSuccess) return e;
+        if ((e = Ops<double>::passB(d, s)) != cudaSuccess) return e;
+        return Ops<double>::passC(d, s);
+    }
+    if ((e = Ops<float>::passA(d, s)) != cudaSuccess) return e;
+    if ((e = Ops<float>::passB(d, s)) != cudaSuccess) return e;
+    return Ops<float>::passC(d, s);
+}
+
+// Captures n steps of one flame on the handle's capture stream.
+flame_status capture_steps(flame_ctx *h, const FlameDesc &d, int n, cudaGraphExec_t *out) {
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < n && le == cudaSuccess; ++i) le = enqueue_step(h, d, h->cap);
+    cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(FLAME_ECUDA, "graph capture failed: %s",
+                    cudaGetErrorString(le != cudaSuccess ? le : ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(FLAME_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+    return FLAME_OK;
+}
+
+flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int n, cudaGraphExec_t *out) {
+    for (auto &g : h->graphs)
+        if (g.state == state && g.mean == mean && g.t == t && g.n == n) {
+            *out = g.exec;
+            return FLAME_OK;
+        }
+    if ((int)h->graphs.size() >= kGraphCache) {
+        // an evicted graph may still be pending on some stream
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+    }
+    cudaGraphExec_t exec;
+    flame_status st = capture_steps(h, make_desc(h, state, mean, t), n, &exec);
+    if (st != FLAME_OK) return st;
+    h->graphs.push_back(GraphEntry{state, mean, t, n, exec});
+    *out = exec;
+    return FLAME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *flame_status_str(flame_status s) {
+    switch (s) {
+    case FLAME_OK: return "ok";
+    case FLAME_EINVAL: return "invalid argument";
+    case FLAME_ENOMEM: return "out of memory";
+    case FLAME_ECUDA: return "CUDA error";
+    case FLAME_EUNSUPPORTED: return "unsupported";
+    case FLAME_ETIMEOUT: return "device wait timed out";
+    case FLAME_ENONFINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+const char *flame_last_error(void) { return g_err.c_str(); }
+
+flame_status flame_create(const flame_params *params, flame_t *out) {
+    if (!params || !out) return fail(FLAME_EINVAL, "flame_create: null pointer");
+    if (inject("param")) return fail(FLAME_EINVAL, "flame_create: injected parameter fault");
+    flame_params p = *params;
+    if (p.prec != FLAME_FP64 && p.prec != FLAME_FP32_MIXED)
+        return fail(FLAME_EINVAL, "flame_create: unknown precision %d", (int)p.prec);
+    if (!pow2_in(p.n_theta, 16, 4096))
+        return fail(FLAME_EUNSUPPORTED, "n_theta=%d: need a power of two in [16, 4096]", p.n_theta);
+    if (!pow2_in(p.n_phi, 32, 8192))
+        return fail(FLAME_EUNSUPPORTED, "n_phi=%d: need a power of two in [32, 8192]", p.n_phi);
+    if (p.K1 < 0 || p.K2 < 0) return fail(FLAME_EINVAL, "negative K");
+    if (p.K1 == 0) p.K1 = (p.n_theta - 1) / 4;
+    if (p.K2 == 0) p.K2 = (p.n_phi - 1) / 4;
+    if (4 * p.K1 + 1 > p.n_theta || 4 * p.K2 + 1 > p.n_phi)
+        return fail(FLAME_EINVAL, "need 4K+1 <= N (alias-free padding): K=(%d,%d) N=(%d,%d)", p.K1, p.K2,
+                    p.n_theta, p.n_phi);
+    if (!(std::isfinite(p.gamma)) || !(p.theta_pi > 0) || !std::isfinite(p.theta_pi))
+        return fail(FLAME_EINVAL, "gamma must be finite and theta_pi > 0");
+    if (!(p.s1 >= 0) || !(p.s2 >= 0) || !std::isfinite(p.s1) || !std::isfinite(p.s2))
+        return fail(FLAME_EINVAL, "s1, s2 must be >= 0");
+    if (p.s1 == 0) p.s1 = p.theta_pi;
+    if (p.s2 == 0) p.s2 = p.theta_pi;
+    if (!(p.t0 > 0) || !(p.dt > 0) || !std::isfinite(p.t0) || !std::isfinite(p.dt))
+        return fail(FLAME_EINVAL, "need t0 > 0 and dt > 0");
+    if ((p.flags & ~3u) || p.flags == 3u) return fail(FLAME_EINVAL, "bad flags %u", p.flags);
+    if (inject("alloc")) return fail(FLAME_ENOMEM, "flame_create: injected allocation fault");
+
+    flame_ctx *h = new flame_ctx();
+    h->p = p;
+    h->logn1 = ilog2(p.n_theta);
+    h->logm = ilog2(p.n_phi / 2);
+    h->csz = p.prec == FLAME_FP64 ? sizeof(double2) : sizeof(float2);
+    StepArgs &a = h->sa;
+    a.n1 = p.n_theta;
+    a.n2 = p.n_phi;
+    a.logn1 = h->logn1;
+    a.logm = h->logm;
+    a.K1 = p.K1;
+    a.K2 = p.K2;
+    a.ldk = p.K2 + 1;
+    a.s1 = p.s1;
+    a.s2 = p.s2;
+    a.gamma = p.gamma;
+    a.t0 = p.t0;
+    a.dt = p.dt;
+    a.flags = p.flags;
+
+    auto dev_alloc = [&](void **ptr, size_t bytes) -> bool {
+        return cudaMalloc(ptr, bytes) == cudaSuccess;
+    };
+    cudaError_t ge = cudaGetDevice(&h->device);
+    if (ge != cudaSuccess) {
+        delete h;
+        return fail(FLAME_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ge));
+    }
+    const size_t n1 = p.n_theta, ldk = a.ldk, m1 = p.n_phi / 2 + 1;
+    bool ok = dev_alloc(&h->tw1, flame::tw_table_len(h->logn1) * h->csz) &&
+              dev_alloc(&h->twm, flame::tw_table_len(h->logm) * h->csz) &&
+              dev_alloc(&h->uv, n1 * ldk * 2 * h->csz) && dev_alloc(&h->gk, n1 * ldk * h->csz) &&
+              dev_alloc(&h->spec, n1 * m1 * h->csz) && dev_alloc((void **)&h->dscal, 4 * sizeof(double)) &&
+              dev_alloc((void **)&h->status, sizeof(int));
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(h);
+        return fail(FLAME_ENOMEM, "flame_create: device allocation failed");
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        h->cap = nullptr;
+        free_ctx(h);
+        return fail(FLAME_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    flame_status st = p.prec == FLAME_FP64 ? alloc_tables<double>(h) : alloc_tables<float>(h);
+    if (st == FLAME_OK) {
+        e = cudaMemsetAsync(h->status, 0, sizeof(int), h->cap);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->dscal, 0, 4 * sizeof(double), h->cap);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap);
+        if (e != cudaSuccess) st = fail(FLAME_ECUDA, "flame_create: %s", cudaGetErrorString(e));
+    }
+    if (st != FLAME_OK) {
+        free_ctx(h);
+        return st;
+    }
+    *out = h;
+    return FLAME_OK;
+}
+
+flame_status flame_destroy(flame_t h) {
+    if (!h) return FLAME_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_ctx(h);
+    if (e != cudaSuccess) return fail(FLAME_ECUDA, "flame_destroy: %s", cudaGetErrorString(e));
+    return FLAME_OK;
+}
+
+flame_status flame_get_params(flame_t h, flame_params *out) {
+    if (!h || !out) return fail(FLAME_EINVAL, "flame_get_params: null pointer");
+    *out = h->p;
+    return FLAME_OK;
+}
+
+size_t flame_state_len(flame_t h) { return h ? (size_t)(2 * h->p.K1 + 1) * (size_t)(h->p.K2 + 1) : 0; }
+
+flame_status flame_fft_r2c(flame_t h, const void *real_in, void *spec_out, void *stream) {
+    if (!h || !real_in || !spec_out) return fail(FLAME_EINVAL, "flame_fft_r2c: null pointer");
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_fft_r2c: injected launch fault");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int M = h->p.n_phi / 2;
+    if (h->p.prec == FLAME_FP64) {
+        using C = double2;
+        CUDA_TRY(Ops<double>::rows_r2c(static_cast<const double *>(real_in), static_cast<C *>(spec_out),
+                                       h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+        CUDA_TRY(Ops<double>::cols(static_cast<C *>(spec_out), static_cast<C *>(spec_out), h->logn1, M + 1,
+                                   M + 1, -1, static_cast<const C *>(h->tw1), s));
+    } else {
+        using C = float2;
+        CUDA_TRY(Ops<float>::rows_r2c(static_cast<const float *>(real_in), static_cast<C *>(spec_out),
+                                      h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+        CUDA_TRY(Ops<float>::cols(static_cast<C *>(spec_out), static_cast<C *>(spec_out), h->logn1, M + 1,
+                                  M + 1, -1, static_cast<const C *>(h->tw1), s));
+    }
+    return FLAME_OK;
+}
+
+flame_status flame_fft_c2r(flame_t h, const void *spec_in, void *real_out, void *stream) {
+    if (!h || !spec_in || !real_out) return fail(FLAME_EINVAL, "flame_fft_c2r: null pointer");
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_fft_c2r: injected launch fault");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int M = h->p.n_phi / 2;
+    if (h->p.prec == FLAME_FP64) {
+        using C = double2;
+        CUDA_TRY(Ops<double>::cols(static_cast<const C *>(spec_in), static_cast<C *>(h->spec), h->logn1, M + 1,
+                                   M + 1, 1, static_cast<const C *>(h->tw1), s));
+        CUDA_TRY(Ops<double>::rows_c2r(static_cast<const C *>(h->spec), static_cast<double *>(real_out),
+                                       h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+    } else {
+        using C = float2;
+        CUDA_TRY(Ops<float>::cols(static_cast<const C *>(spec_in), static_cast<C *>(h->spec), h->logn1, M + 1,
+                                  M + 1, 1, static_cast<const C *>(h->tw1), s));
+        CUDA_TRY(Ops<float>::rows_c2r(static_cast<const C *>(h->spec), static_cast<float *>(real_out),
+                                      h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+    }
+    return FLAME_OK;
+}
+
+flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, int nsteps, void *stream) {
+    if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step: null pointer");
+    if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step: nsteps=%d < 0", nsteps);
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_step: injected launch fault");
+    if (nsteps == 0) return FLAME_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (nsteps == 1) {
+        CUDA_TRY(enqueue_step(h, make_desc(h, state, mean_mode, t), s));
+        return FLAME_OK;
+    }
+    // All graphs are captured before the first one is launched, so that a
+    // capture failure leaves nothing enqueued.
+    const int full = nsteps / kGraphChunk, rest = nsteps % kGraphChunk;
+    cudaGraphExec_t gfull = nullptr, grest = nullptr;
+    if (full) {
+        flame_status st = step_graph(h, state, mean_mode, t, kGraphChunk, &gfull);
+        if (st != FLAME_OK) return st;
+    }
+    if (rest) {
+        flame_status st = step_graph(h, state, mean_mode, t, rest, &grest);
+        if (st != FLAME_OK) return st;
+    }
+    for (int i = 0; i < full; ++i) CUDA_TRY(cudaGraphLaunch(gfull, s));
+    if (rest) CUDA_TRY(cudaGraphLaunch(grest, s));
+    return FLAME_OK;
+}
+
+flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode, double *t, void *stream) {
+    if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step_pass: null pointer");
+    if (pass < 0 || pass > 2) return fail(FLAME_EINVAL, "flame_step_pass: pass=%d not in 0..2", pass);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const FlameDesc d = make_desc(h, state, mean_mode, t);
+    if (h->p.prec == FLAME_FP64)
+        CUDA_TRY(pass == 0 ? Ops<double>::passA(d, s) : pass == 1 ? Ops<double>::passB(d, s) : Ops<double>::passC(d, s));
+    else
+        CUDA_TRY(pass == 0 ? Ops<float>::passA(d, s) : pass == 1 ? Ops<float>::passB(d, s) : Ops<float>::passC(d, s));
+    return FLAME_OK;
+}
+
+flame_status flame_step_batch(const flame_t *hs, void *const *states, double *const *mean_modes,
+                              double *const *ts, int nflames, int nsteps, void *stream) {
+    if (!hs || !states || !mean_modes || !ts) return fail(FLAME_EINVAL, "flame_step_batch: null pointer");
+    if (nflames < 0 || nsteps < 0) return fail(FLAME_EINVAL, "flame_step_batch: negative count");
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_batch: injected launch fault");
+    if (nflames == 0 || nsteps == 0) return FLAME_OK;
+    flame_ctx *h0 = hs[0];
+    if (!h0) return fail(FLAME_EINVAL, "flame_step_batch: null handle 0");
+    for (int i = 0; i < nflames; ++i) {
+        if (!hs[i] || !states[i] || !mean_modes[i] || !ts[i])
+            return fail(FLAME_EINVAL, "flame_step_batch: null entry %d", i);
+        if (hs[i]->p.prec != h0->p.prec || hs[i]->device != h0->device)
+            return fail(FLAME_EINVAL, "flame_step_batch: flame %d differs in precision or device", i);
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(FLAME_EINVAL, "flame_step_batch: handle %d repeated (shared workspace)", i);
+    }
+    // group by grid: one launch per pass and size class
+    std::map<std::vector<int>, std::vector<FlameDesc>> classes;
+    for (int i = 0; i < nflames; ++i) {
+        const StepArgs &a = hs[i]->sa;
+        classes[{a.n1, a.n2, a.K1, a.K2}].push_back(make_desc(hs[i], states[i], mean_modes[i], ts[i]));
+    }
+    std::vector<FlameDesc> flat;
+    std::vector<std::pair<size_t, size_t>> ranges;  // (offset, count) per class
+    for (auto &kv : classes) {
+        ranges.emplace_back(flat.size(), kv.second.size());
+        flat.insert(flat.end(), kv.second.begin(), kv.second.end());
+    }
+    const size_t bytes = flat.size() * sizeof(FlameDesc);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool same = h0->batch_exec && h0->batch_n == nsteps && h0->batch_key.size() == flat.size() &&
+                      memcmp(h0->batch_key.data(), flat.data(), bytes) == 0;
+    if (!same) {
+        if (h0->batch_exec) {
+            CUDA_TRY(cudaDeviceSynchronize());
+            cudaGraphExecDestroy(h0->batch_exec);
+            h0->batch_exec = nullptr;
+        }
+        if (h0->batch_cap < bytes) {
+            CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(h0->batch_desc);
+            h0->batch_desc = nullptr;
+            h0->batch_cap = 0;
+            if (cudaMalloc(&h0->batch_desc, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FLAME_ENOMEM, "flame_step_batch: descriptor allocation failed");
+            }
+            h0->batch_cap = bytes;
+        }
+        CUDA_TRY(cudaMemcpy(h0->batch_desc, flat.data(), bytes, cudaMemcpyHostToDevice));
+        const FlameDesc *dev = static_cast<const FlameDesc *>(h0->batch_desc);
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int st = 0; st < nsteps && le == cudaSuccess; ++st) {
+            for (int pass = 0; pass < 3 && le == cudaSuccess; ++pass) {
+                for (auto &rg : ranges) {
+                    const StepArgs &a = flat[rg.first].a;
+                    const FlameDesc *d = dev + rg.first;
+                    const int n = (int)rg.second;
+                    if (h0->p.prec == FLAME_FP64)
+                        le = pass == 0 ? Ops<double>::passA_batch(d, n, a, h0->cap)
+                           : pass == 1 ? Ops<double>::passB_batch(d, n, a, h0->cap)
+                                       : Ops<double>::passC_batch(d, n, a, h0->cap);
+                    else
+                        le = pass == 0 ? Ops<float>::passA_batch(d, n, a, h0->cap)
+                           : pass == 1 ? Ops<float>::passB_batch(d, n, a, h0->cap)
+                                       : Ops<float>::passC_batch(d, n, a, h0->cap);
+                    if (le != cudaSuccess) break;
+                }
+            }
+        }
+        cudaError_t ee = cudaStreamEndCapture(h0->cap, &graph);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(FLAME_ECUDA, "flame_step_batch capture: %s",
+                        cudaGetErrorString(le != cudaSuccess ? le : ee));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&h0->batch_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            h0->batch_exec = nullptr;
+            return fail(FLAME_ECUDA, "flame_step_batch instantiate: %s", cudaGetErrorString(ie));
+        }
+        h0->batch_key = flat;
+        h0->batch_n = nsteps;
+    }
+    CUDA_TRY(cudaGraphLaunch(h0->batch_exec, s));
+    return FLAME_OK;
+}
+
+flame_status flame_area(flame_t h, const void *state, const double *mean_mode, const double *t,
+                        double *area_out, void *dA_dstate, double *dA_dmean, void *stream) {
+    (void)state; (void)mean_mode; (void)t; (void)area_out; (void)dA_dstate; (void)dA_dmean; (void)stream;
+    if (!h) return fail(FLAME_EINVAL, "flame_area: null handle");
+    return fail(FLAME_EUNSUPPORTED, "flame_area: not built yet");
+}
+
+flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, const double *t_start, int nsteps,
+                           int ckpt_every, const void *lambda_T, const double *lambda0_T, void *grad_state0,
+                           double *grad_mean0, double *grad_gamma, void *stream) {
+    (void)state0; (void)mean0; (void)t_start; (void)nsteps; (void)ckpt_every; (void)lambda_T;
+    (void)lambda0_T; (void)grad_state0; (void)grad_mean0; (void)grad_gamma; (void)stream;
+    if (!h) return fail(FLAME_EINVAL, "flame_adjoint: null handle");
+    return fail(FLAME_EUNSUPPORTED, "flame_adjoint: not built yet");
+}
+
+flame_status flame_sync_status(flame_t h) {
+    if (!h) return fail(FLAME_EINVAL, "flame_sync_status: null handle");
+    CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    CUDA_TRY(cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(h->status, 0, sizeof(int)));
+    if (v & (1 << flame::kStatusTimeout)) return fail(FLAME_ETIMEOUT, "a device-side wait timed out");
+    if (v & (1 << flame::kStatusNonfinite)) return fail(FLAME_ENONFINITE, "a step produced NaN or Inf");
+    return FLAME_OK;
+}
+
+}  // extern "C"

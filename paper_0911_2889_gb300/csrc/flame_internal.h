@@ -1,0 +1,72 @@
+// flame_internal.h -- declarations shared by the host runtime and the
+// per-precision kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <type_traits>
+
+namespace flame {
+
+constexpr unsigned kLinearOnly = 1u;
+constexpr unsigned kNonlinearOnly = 2u;
+constexpr int kStatusNonfinite = 0;
+constexpr int kStatusTimeout = 1;
+
+// Plain-old-data arguments of the step kernels.
+struct StepArgs {
+    int n1, n2;        // grid
+    int logn1, logm;   // log2 N1, log2 (N2/2)
+    int K1, K2;        // retained harmonics
+    int ldk;           // row length of the compact box and workspaces (K2+1)
+    double s1, s2;     // kappa = (s1 k1, s2 k2)
+    double gamma, t0, dt;
+    unsigned flags;
+};
+
+// Everything one flame's step passes need: parameters, the caller's state
+// buffers and the handle's tables and workspace.  Passed by value for a
+// single flame, or as a device array indexed by blockIdx.y for an ensemble.
+struct FlameDesc {
+    StepArgs a;
+    void *state;            // compact box (in place)
+    void *uv;               // N1 x ldk x (U, V) workspace
+    void *gk;               // N1 x ldk workspace
+    const void *tw1;        // twiddles of length N1
+    const void *twm;        // twiddles of length N2/2 (+ real table)
+    const double *t_in;     // caller's t (read by pass B)
+    double *t_copy;         // t_n for pass C (handle scalar)
+    double *mean;           // caller's mean mode
+    double *t_out;          // caller's t (written by pass C)
+    int *status;            // handle's device status word
+};
+
+// Launch geometry of a line-FFT kernel.
+struct Geom {
+    int threads;       // blockDim.x
+    int blocks;        // gridDim.x
+    size_t smem;       // dynamic shared memory bytes
+};
+
+// Per-precision launchers (defined in flame_f32.cu / flame_f64.cu).
+template <class R> struct Ops {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    static cudaError_t init_twiddles(C *tab, int logN, cudaStream_t s);
+    static cudaError_t rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s);
+    static cudaError_t rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s);
+    static cudaError_t cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw,
+                            cudaStream_t s);
+    // One step pass for one flame (desc by value) or for nflames flames of
+    // the same grid (descs: device array of nflames entries, shape from a).
+    static cudaError_t passA(const FlameDesc &d, cudaStream_t s);
+    static cudaError_t passB(const FlameDesc &d, cudaStream_t s);
+    static cudaError_t passC(const FlameDesc &d, cudaStream_t s);
+    static cudaError_t passA_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
+    static cudaError_t passB_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
+    static cudaError_t passC_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
+    // geometry used by the step passes (for the autotuner and the tests)
+    static Geom geom_cols(int logn, int nlines, int groups_hint);
+    static Geom geom_rows(int logm, int nlines, int groups_hint);
+    static cudaError_t prepare();  // opt-in shared memory sizes (idempotent)
+};
+
+}  // namespace flame

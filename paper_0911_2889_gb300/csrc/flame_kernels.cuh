@@ -1,0 +1,488 @@
+// flame_kernels.cuh -- the kernels of the spectral flame step and of the
+// standalone 2-D real FFTs, templated on the working precision R.
+//
+// Step of eq. (SivCurv1c) (Sec. 2) with the FFT evaluation of the quadratic
+// term (Sec. 3), in three passes over HBM:
+//   pass A (columns): i kappa_1 Phi and Phi -> zero-padded inverse FFT along
+//                     k1 (the first index, Sec. 3) -> U(j1,k2), V(j1,k2)
+//   pass B (rows):    inverse FFT along k2 of U + iV -> u + iv on the grid,
+//                     g = u^2 + v^2 = |grad Phi|^2, forward real FFT of g
+//                     along j2, keep k2 <= K2 -> G(j1,k2)
+//   pass C (columns): forward FFT along j1, keep |k1| <= K1, scale,
+//                     Euler update with the linear operator, symmetrization
+//                     of the k2 = 0 column (Sec. 3), FP64 mean mode and time.
+// The transposition the paper performs with MPI_ALLTOALL between the column
+// and row transforms (Sec. 3) is the change of access direction between
+// passes: each pass reads and writes whole tiles, and the reordering inside a
+// transform goes through shared memory.
+#pragma once
+
+#include "fft_engine.cuh"
+#include "flame_internal.h"
+
+namespace flame {
+
+template <class R> using CplxT = typename VecOf<R>::c;  // float2 / double2
+static_assert(sizeof(float2) == sizeof(VecOf<float>::type) && sizeof(double2) == sizeof(VecOf<double>::type), "C and V sizes");
+
+// FP32 kernels fit 128 registers (two CTAs of 256 threads per SM); FP64
+// kernels need up to 255 (one CTA per SM).
+template <class R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
+
+// Element of the interleaved (U, V) workspace: two complex numbers.
+template <class R> struct UV { CplxT<R> u, v; };
+
+template <class R> __device__ __forceinline__ UV<R> ld_uv(const CplxT<R> *p) {
+    if constexpr (std::is_same<R, float>::value) {
+        float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+    } else {
+        return {__ldg(p), __ldg(p + 1)};
+    }
+}
+template <class R> __device__ __forceinline__ void st_uv(CplxT<R> *p, CplxT<R> u, CplxT<R> v) {
+    if constexpr (std::is_same<R, float>::value) {
+        *reinterpret_cast<float4 *>(p) = make_float4(u.x, u.y, v.x, v.y);
+    } else {
+        p[0] = u;
+        p[1] = v;
+    }
+}
+
+template <class R> __device__ __forceinline__ CV<typename VecOf<R>::type> pack2(CplxT<R> a, CplxT<R> b) {
+    using V = typename VecOf<R>::type;
+    return {V{a.x, b.x}, V{a.y, b.y}};
+}
+template <class R> __device__ __forceinline__ CplxT<R> lane0(CV<typename VecOf<R>::type> z) {
+    return CplxT<R>{z.re.x, z.im.x};
+}
+template <class R> __device__ __forceinline__ CplxT<R> lane1(CV<typename VecOf<R>::type> z) {
+    return CplxT<R>{z.re.y, z.im.y};
+}
+
+// ----------------------------------------------------------------------------
+// Twiddle table generation (FP64 sincospi, rounded once)
+// ----------------------------------------------------------------------------
+template <class R> __global__ void k_twiddles(CplxT<R> *tab, int logN) {
+    const int N = 1 << logN;
+    const int len = tw_table_len(logN);
+    const int fin = tw_final_offset(logN);
+    const int real = tw_real_offset(logN);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+        long num, den;  // angle = 2 pi num / den
+        if (i < fin) {
+            int s = 1, off = 0, ns = 16;
+            while (i >= off + 15 * ns) { off += 15 * ns; ns <<= 4; ++s; }
+            int r = (i - off) / ns + 1, m = (i - off) % ns;
+            num = (long)r * m;
+            den = 16L * ns;
+        } else if (i < real) {
+            int rho = 1 << (logN & 3), ns = N / rho;
+            int q = (i - fin) / ns + 1, m = (i - fin) % ns;
+            num = (long)q * m;
+            den = N;
+        } else {
+            num = i - real;
+            den = 2L * N;
+        }
+        double s, c;
+        sincospi(2.0 * (double)(num % den) / (double)den, &s, &c);
+        tab[i] = CplxT<R>{(R)c, (R)s};
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Standalone 2-D real FFT passes
+// ----------------------------------------------------------------------------
+// Row pass of r2c: two rows per thread group (row 2p, 2p+1), half-length
+// complex FFT of h[m] = x[2m] + i x[2m+1] followed by the real-input
+// post-processing  Y[k] = E[k] + exp(-2 pi i k/N2) O[k],
+// E = (H[k] + conj H[M-k])/2, O = (H[k] - conj H[M-k])/(2i).
+template <class R>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_r2c(const R *__restrict__ in, CplxT<R> *__restrict__ out, int n1,
+                                                  int logm, const CplxT<R> *__restrict__ tw) {
+    using V = typename VecOf<R>::type;
+    using C = CplxT<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M = 1 << logm, T = M >> 4, ldo = M + 1;
+    const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
+    const int pair = blockIdx.x * G + g;
+    const bool valid = pair < (n1 >> 1);
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(M);
+    Planes<V> sm{base, base + plane_len(M)};
+    const C *ra = reinterpret_cast<const C *>(in) + (size_t)(2 * pair) * M;
+    const C *rb = ra + M;
+    CV<V> x[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        C a = valid ? __ldg(ra + t + r * T) : C{0, 0};
+        C b = valid ? __ldg(rb + t + r * T) : C{0, 0};
+        x[r] = pack2<R>(a, b);
+    }
+    line_fft<-1>(x, logm, t, sm, tw, CtaBarrier{});
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm.st(t + r * T, x[r]);
+    __syncthreads();
+    const C *P = tw + tw_real_offset(logm);
+    C *oa = out + (size_t)(2 * pair) * ldo, *ob = oa + ldo;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = t + r * T;
+        CV<V> h = x[r], hc = sm.ld((M - k) & (M - 1));
+        const R hf = (R)0.5;
+        CV<V> E{vmul(vadd(h.re, hc.re), vbc(hf)), vmul(vsub(h.im, hc.im), vbc(hf))};
+        // O = (h - conj hc) / (2i) = (D.im/2, -D.re/2), D = (h.re - hc.re, h.im + hc.im)
+        CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
+        C w = __ldg(P + k);  // exp(+2 pi i k/N2); forward uses the conjugate
+        CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
+        if (valid) {
+            oa[k] = lane0<R>(Y);
+            ob[k] = lane1<R>(Y);
+        }
+    }
+    if (valid && t == 0) {
+        CV<V> h0 = x[0];
+        oa[M] = C{h0.re.x - h0.im.x, 0};
+        ob[M] = C{h0.re.y - h0.im.y, 0};
+    }
+}
+
+// Row pass of c2r: pre-processing H[k] = (Y[k] + conj Y[M-k]) +
+// i exp(+2 pi i k/N2) (Y[k] - conj Y[M-k]), half-length inverse FFT, then
+// x[2m] = Re h[m], x[2m+1] = Im h[m].
+template <class R>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_c2r(const CplxT<R> *__restrict__ in, R *__restrict__ out, int n1,
+                                                  int logm, const CplxT<R> *__restrict__ tw) {
+    using V = typename VecOf<R>::type;
+    using C = CplxT<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M = 1 << logm, T = M >> 4, ldi = M + 1;
+    const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
+    const int pair = blockIdx.x * G + g;
+    const bool valid = pair < (n1 >> 1);
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(M);
+    Planes<V> sm{base, base + plane_len(M)};
+    const C *ia = in + (size_t)(2 * pair) * ldi, *ib = ia + ldi;
+    const C *P = tw + tw_real_offset(logm);
+    CV<V> x[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = t + r * T;
+        C a = valid ? __ldg(ia + k) : C{0, 0};
+        C b = valid ? __ldg(ib + k) : C{0, 0};
+        C ac = valid ? __ldg(ia + M - k) : C{0, 0};
+        C bc = valid ? __ldg(ib + M - k) : C{0, 0};
+        CV<V> y = pack2<R>(a, b), yc = pack2<R>(ac, bc);
+        CV<V> S{vadd(y.re, yc.re), vsub(y.im, yc.im)};
+        CV<V> D{vsub(y.re, yc.re), vadd(y.im, yc.im)};
+        C w = __ldg(P + k);
+        CV<V> wD = cmul_s(D, w.x, w.y);
+        x[r] = cadd_rot<1>(S, wD);
+    }
+    line_fft<1>(x, logm, t, sm, tw, CtaBarrier{});
+    if (valid) {
+        C *oa = reinterpret_cast<C *>(out) + (size_t)(2 * pair) * M, *ob = oa + M;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            oa[t + r * T] = lane0<R>(x[r]);
+            ob[t + r * T] = lane1<R>(x[r]);
+        }
+    }
+}
+
+// Column FFT of length n = 2^logn over ncols columns of a row-major array
+// with row stride ld (complex units); columns 2p, 2p+1 form one thread
+// group; in may equal out.
+template <class R, int DIR>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_cols(const CplxT<R> *in, CplxT<R> *out, int logn, int ncols, int ld,
+                                              const CplxT<R> *__restrict__ tw) {
+    using V = typename VecOf<R>::type;
+    using C = CplxT<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = 1 << logn, T = n >> 4;
+    const int G = blockDim.x / T, g = threadIdx.x % G, t = threadIdx.x / G;
+    const int c0 = 2 * (blockIdx.x * G + g);
+    const bool va = c0 < ncols, vb = c0 + 1 < ncols;
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(n);
+    Planes<V> sm{base, base + plane_len(n)};
+    CV<V> x[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const size_t row = (size_t)(t + r * T) * ld;
+        C a = va ? in[row + c0] : C{0, 0};
+        C b = vb ? in[row + c0 + 1] : C{0, 0};
+        x[r] = pack2<R>(a, b);
+    }
+    line_fft<DIR>(x, logn, t, sm, tw, CtaBarrier{});
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const size_t row = (size_t)(t + r * T) * ld;
+        if (va) out[row + c0] = lane0<R>(x[r]);
+        if (vb) out[row + c0 + 1] = lane1<R>(x[r]);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Step passes
+// ----------------------------------------------------------------------------
+// Pass A (a1 + a2): column k2 of the compact box -> inverse FFT along k1 of
+// a = i s1 k1 Phi and b = Phi (one pair of lines), zero padded outside
+// |k1| <= K1 (positions K1 < n < N1 - K1; with N1 >= 4 K1 + 1 the registers
+// r = 4..11 of the first pass are always zero and are dropped at compile
+// time).  Writes UV[j1][k2] = (U, V) with U = synthesis of a, V = i s2 k2 x
+// synthesis of b.
+template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile) {
+    using V = typename VecOf<R>::type;
+    using C = CplxT<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const StepArgs &a = d.a;
+    const C *__restrict__ state = static_cast<const C *>(d.state);
+    C *__restrict__ uv = static_cast<C *>(d.uv);
+    const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
+    const int N1 = 1 << a.logn1, T = N1 >> 4;
+    const int G = blockDim.x / T, g = threadIdx.x % G, t = threadIdx.x / G;
+    const int k2 = tile * G + g;
+    const bool valid = k2 <= a.K2;
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
+    Planes<V> sm{base, base + plane_len(N1)};
+    const R s1 = (R)a.s1, s2k2 = (R)(a.s2 * k2);
+    CV<V> x[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        x[r] = CV<V>{vzero(V{}), vzero(V{})};
+        if (r < 4 || r >= 12) {
+            const int n = t + r * T;
+            int k1 = (r < 4) ? n : n - N1;
+            bool in_box = valid && ((r < 4) ? (n <= a.K1) : (k1 >= -a.K1));
+            if (in_box) {
+                C phi = __ldg(state + (size_t)(k1 + a.K1) * a.ldk + k2);
+                if (k1 == 0 && k2 == 0) phi = C{0, 0};
+                const R f = s1 * (R)k1;
+                C da{-f * phi.y, f * phi.x};  // i s1 k1 Phi
+                x[r] = pack2<R>(da, phi);
+            }
+        }
+    }
+    line_fft<1>(x, a.logn1, t, sm, tw1, CtaBarrier{});
+    if (valid) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            C U = lane0<R>(x[r]);
+            C Vb = lane1<R>(x[r]);
+            C Vv{-s2k2 * Vb.y, s2k2 * Vb.x};  // i s2 k2 (synthesis of Phi)
+            st_uv<R>(uv + 2 * ((size_t)n * a.ldk + k2), U, Vv);
+        }
+    }
+}
+
+// Pass B (a3..a6): rows 2p and 2p+1 of UV.  For each row the full spectrum
+// Z[k] = U[k] + i V[k] (k = -K2..K2, U[-k] = conj U[k]) is transformed by
+// two half-length inverse FFTs (even and odd grid points:
+// z[2m+q] = sum_k Z[k] exp(2 pi i k q/N2) exp(2 pi i k m/M)), giving
+// u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
+// forward with the real-input post-processing; G[k], k <= K2, is written.
+// G[j1][0] is the row sum of g used for the FP64 mean mode.
+template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile) {
+    using V = typename VecOf<R>::type;
+    using C = CplxT<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const StepArgs &a = d.a;
+    const C *__restrict__ uv = static_cast<const C *>(d.uv);
+    C *__restrict__ gk = static_cast<C *>(d.gk);
+    const C *__restrict__ twm = static_cast<const C *>(d.twm);
+    const int M = 1 << a.logm, T = M >> 4, half = M >> 1;
+    const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
+    const int pair = tile * G + g;
+    const bool valid = pair < (a.n1 >> 1);
+    // per group: two exchange planes, then M entries of C (sizeof(C) ==
+    // sizeof(V) in both precisions)
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len(M) + M);
+    Planes<V> sm{base, base + plane_len(M)};
+    const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
+    if (tile == 0 && threadIdx.x == 0) *d.t_copy = *d.t_in;
+
+    // |z|^2 of the first row is parked in shared memory (h_first, M entries
+    // per group, after the two exchange planes) while the second row is
+    // transformed; the second row's stays in registers.
+    C *h_first = reinterpret_cast<C *>(base + 2 * plane_len(M));
+    auto row_ifft = [&](int q, CV<V>(&x)[16]) {
+        const int row = 2 * pair + q;
+        const C *src = uv + 2 * (size_t)row * a.ldk;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            const int k = (n < half) ? n : n - M;  // signed wavenumber
+            const int kk = k < 0 ? -k : k;
+            C z{0, 0};
+            if (valid && kk <= a.K2) {
+                UV<R> e = ld_uv<R>(src + 2 * kk);
+                if (k >= 0) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
+                else z = C{e.u.x + e.v.y, e.v.x - e.u.y};          // conj U + i conj V
+            }
+            C w = __ldg(P + kk);                                 // exp(2 pi i |k|/N2)
+            C z1 = (k >= 0) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
+                            : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
+            x[r] = pack2<R>(z, z1);
+        }
+        line_fft<1>(x, a.logm, t, sm, twm, CtaBarrier{});
+    };
+    CV<V> x[16];
+    row_ifft(0, x);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        // g at grid points 2m and 2m+1: |z_0|^2, |z_1|^2
+        V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
+        h_first[t + r * T] = C{sq.x, sq.y};
+    }
+    row_ifft(1, x);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
+        x[r] = pack2<R>(h_first[t + r * T], C{sq.x, sq.y});
+    }
+    line_fft<-1>(x, a.logm, t, sm, twm, CtaBarrier{});
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm.st(t + r * T, x[r]);
+    __syncthreads();
+    C *oa = gk + (size_t)(2 * pair) * a.ldk, *ob = oa + a.ldk;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int k = t + r * T;
+        if (valid && k <= a.K2) {
+            CV<V> h = x[r], hc = sm.ld((M - k) & (M - 1));
+            const R hf = (R)0.5;
+            CV<V> E{vmul(vadd(h.re, hc.re), vbc(hf)), vmul(vsub(h.im, hc.im), vbc(hf))};
+            CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
+            C w = __ldg(P + k);
+            CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
+            oa[k] = lane0<R>(Y);
+            ob[k] = lane1<R>(Y);
+        }
+    }
+}
+
+// Step coefficients at t_n, evaluated in FP64 (then rounded for FP32).
+struct Coef {
+    double tn, a, b, c;  // a = 1/r0^2, b = gamma/(2 r0), c = 1/(2 r0^2)
+};
+__device__ __forceinline__ Coef step_coef(const StepArgs &s, double t) {
+    long n = __double2ll_rn((t - s.t0) / s.dt);
+    double tn = s.t0 + (double)n * s.dt;
+    Coef k;
+    k.tn = tn;
+    k.a = 1.0 / (tn * tn);
+    k.b = s.gamma / (2.0 * tn);
+    k.c = 0.5 * k.a;
+    return k;
+}
+
+template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
+    if constexpr (std::is_same<R, float>::value) return __fsqrt_rn(fmaf(s1k1, s1k1, s2k2 * s2k2));
+    else return sqrt(fma(s1k1, s1k1, s2k2 * s2k2));
+}
+
+// Pass C (a7..a10): columns k2, k2+1 of G -> forward FFT along j1 (outputs
+// outside |k1| <= K1 unused and dropped at compile time), scaled by
+// 1/(N1 N2) -> ghat; Phi <- Phi + dt (omega Phi + c ghat); the k2 = 0 column
+// is written from its k1 > 0 half and its conjugate mirror; the block owning
+// column 0 sums G[j1][0] in FP64 for the mean mode and advances t.
+template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile) {
+    using V = typename VecOf<R>::type;
+    using C = CplxT<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[32];
+    const StepArgs &a = d.a;
+    const C *__restrict__ gk = static_cast<const C *>(d.gk);
+    C *__restrict__ state = static_cast<C *>(d.state);
+    const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
+    const int N1 = 1 << a.logn1, T = N1 >> 4;
+    const int G = blockDim.x / T, g = threadIdx.x % G, t = threadIdx.x / G;
+    const int c0 = 2 * (tile * G + g);
+    const bool va = c0 <= a.K2, vb = c0 + 1 <= a.K2;
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
+    Planes<V> sm{base, base + plane_len(N1)};
+    CV<V> x[16];
+    double colsum = 0.0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const size_t row = (size_t)(t + r * T) * a.ldk;
+        C p = va ? gk[row + c0] : C{0, 0};
+        C q = vb ? gk[row + c0 + 1] : C{0, 0};
+        if (c0 == 0) colsum += (double)p.x;
+        x[r] = pack2<R>(p, q);
+    }
+    if (tile == 0) {  // block-uniform: FP64 row-sum reduction of column 0
+        for (int o = 16; o > 0; o >>= 1) colsum += __shfl_xor_sync(0xffffffffu, colsum, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = colsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            red[0] = s;
+        }
+        // red[0] is read after the transform's barriers
+    }
+    line_fft<-1>(x, a.logn1, t, sm, tw1, CtaBarrier{});
+
+    const Coef cf = step_coef(a, *d.t_copy);
+    const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
+    const double inv = 1.0 / ((double)N1 * (double)a.n2);
+    const R ra = (R)cf.a, rb = (R)cf.b, rcs = (R)(cf.c * inv), rdt = (R)a.dt;
+    int bad = 0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        if (r < 4 || r >= 12) {
+            const int n = t + r * T;
+            const int k1 = (r < 4) ? n : n - N1;
+            const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int k2 = c0 + side;
+                const bool ok = in_box && (side == 0 ? va : vb);
+                if (!ok) continue;
+                if (k2 == 0 && k1 < 0) continue;  // written as the mirror of +k1
+                const size_t idx = (size_t)(k1 + a.K1) * a.ldk + k2;
+                if (k1 == 0 && k2 == 0) {
+                    state[idx] = C{0, 0};
+                    continue;
+                }
+                C gh = side == 0 ? lane0<R>(x[r]) : lane1<R>(x[r]);
+                C phi = state[idx];
+                const R kap = kappa_norm<R>((R)a.s1 * (R)k1, (R)a.s2 * (R)k2);
+                const R om = lin ? kap * (rb - kap * ra) : (R)0;
+                const R cn = nl ? rcs : (R)0;
+                C nw{phi.x + rdt * (om * phi.x + cn * gh.x), phi.y + rdt * (om * phi.y + cn * gh.y)};
+                bad |= !(isfinite(nw.x) && isfinite(nw.y));
+                state[idx] = nw;
+                if (k2 == 0) state[(size_t)(-k1 + a.K1) * a.ldk] = C{nw.x, -nw.y};
+            }
+        }
+    }
+    if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
+    if (tile == 0 && threadIdx.x == 0) {
+        const double mg = red[0] * inv;  // mean of |grad Phi|^2
+        if (nl) *d.mean += a.dt * cf.c * mg;
+        long n = __double2ll_rn((cf.tn - a.t0) / a.dt);
+        *d.t_out = a.t0 + (double)(n + 1) * a.dt;
+    }
+}
+
+// Kernel entry points: one flame (descriptor by value) or an ensemble of
+// equal-size flames (descriptor array, flame = blockIdx.y).
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA(FlameDesc d) { passA_body<R>(d, blockIdx.x); }
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d) { passB_body<R>(d, blockIdx.x); }
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d) { passC_body<R>(d, blockIdx.x); }
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds) {
+    passA_body<R>(ds[blockIdx.y], blockIdx.x);
+}
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds) {
+    passB_body<R>(ds[blockIdx.y], blockIdx.x);
+}
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC_n(const FlameDesc *__restrict__ ds) {
+    passC_body<R>(ds[blockIdx.y], blockIdx.x);
+}
+
+}  // namespace flame

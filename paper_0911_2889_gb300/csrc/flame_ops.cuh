@@ -1,0 +1,123 @@
+// flame_ops.cuh -- launch geometry and launchers of the kernels, instantiated
+// once per precision by flame_f32.cu and flame_f64.cu.
+#pragma once
+
+#include "flame_kernels.cuh"
+
+namespace flame {
+
+constexpr size_t kMaxSmem = 227 * 1024;     // opt-in limit per CTA on sm_103a
+constexpr size_t kSmemBudget = 200 * 1024;  // what one CTA may take here
+constexpr int kThreadsTarget = 256;
+constexpr int kMaxThreads = 256;  // launch bound of every line-FFT kernel
+
+template <class R> static size_t group_smem(int logn) {
+    return 2 * (size_t)plane_len(1 << logn) * sizeof(typename VecOf<R>::type);
+}
+
+template <class R> static Geom make_geom(int logn, int nlines, int hint, size_t extra = 0) {
+    const int T = (1 << logn) >> 4;
+    int G = hint > 0 ? hint : (T >= kThreadsTarget ? 1 : kThreadsTarget / T);
+    const size_t per = group_smem<R>(logn) + extra;
+    while (G > 1 && (G * per > kSmemBudget || G * T > kMaxThreads)) G >>= 1;
+    Geom g;
+    g.threads = G * T;
+    g.blocks = (nlines + G - 1) / G;
+    g.smem = G * per;
+    return g;
+}
+
+template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { return make_geom<R>(logn, nlines, hint); }
+template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
+
+template <class R> cudaError_t Ops<R>::prepare() {
+    static bool done = false;  // per process; all devices of one process share the attribute
+    if (done) return cudaSuccess;
+    const int b = (int)kMaxSmem;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (r != cudaSuccess) e = r;
+    };
+    set((const void *)k_rows_r2c<R>);
+    set((const void *)k_rows_c2r<R>);
+    set((const void *)k_cols<R, -1>);
+    set((const void *)k_cols<R, 1>);
+    set((const void *)k_passA<R>);
+    set((const void *)k_passB<R>);
+    set((const void *)k_passC<R>);
+    set((const void *)k_passA_n<R>);
+    set((const void *)k_passB_n<R>);
+    set((const void *)k_passC_n<R>);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStream_t s) {
+    const int len = tw_table_len(logN);
+    k_twiddles<R><<<(len + 255) / 256, 256, 0, s>>>(tab, logN);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t Ops<R>::rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s) {
+    Geom g = geom_rows(logm, n1 / 2, 0);
+    k_rows_r2c<R><<<g.blocks, g.threads, g.smem, s>>>(in, out, n1, logm, tw);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t Ops<R>::rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s) {
+    Geom g = geom_rows(logm, n1 / 2, 0);
+    k_rows_c2r<R><<<g.blocks, g.threads, g.smem, s>>>(in, out, n1, logm, tw);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw, cudaStream_t s) {
+    Geom g = geom_cols(logn, (ncols + 1) / 2, 0);
+    if (dir < 0) k_cols<R, -1><<<g.blocks, g.threads, g.smem, s>>>(in, out, logn, ncols, ld, tw);
+    else k_cols<R, 1><<<g.blocks, g.threads, g.smem, s>>>(in, out, logn, ncols, ld, tw);
+    return cudaGetLastError();
+}
+
+template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s) {
+    Geom g = geom_cols(d.a.logn1, d.a.K2 + 1, 0);
+    k_passA<R><<<g.blocks, g.threads, g.smem, s>>>(d);
+    return cudaGetLastError();
+}
+// pass B parks one row of |z|^2 (N2/2 complex) per group in shared memory
+template <class R> static Geom geom_passB(int logm, int nlines) {
+    return make_geom<R>(logm, nlines, 0, (size_t)(1 << logm) * sizeof(typename VecOf<R>::c));
+}
+
+template <class R> cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s) {
+    Geom g = geom_passB<R>(d.a.logm, d.a.n1 / 2);
+    k_passB<R><<<g.blocks, g.threads, g.smem, s>>>(d);
+    return cudaGetLastError();
+}
+template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
+    Geom g = geom_cols(d.a.logn1, (d.a.K2 + 2) / 2, 0);
+    k_passC<R><<<g.blocks, g.threads, g.smem, s>>>(d);
+    return cudaGetLastError();
+}
+template <class R>
+cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
+    Geom g = geom_cols(a.logn1, a.K2 + 1, 0);
+    k_passA_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds);
+    return cudaGetLastError();
+}
+template <class R>
+cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
+    Geom g = geom_passB<R>(a.logm, a.n1 / 2);
+    k_passB_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds);
+    return cudaGetLastError();
+}
+template <class R>
+cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
+    Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
+    k_passC_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds);
+    return cudaGetLastError();
+}
+
+}  // namespace flame

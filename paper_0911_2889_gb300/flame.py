@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in include/flame.h (argument marshalling only).
+
+Every step of the computation runs in the sm_103a kernels of libflame.so;
+this module only converts torch CUDA tensors to device pointers and the
+current torch stream to a cudaStream_t.  It never computes anything itself
+and there is no CPU fallback: if the library cannot be loaded, every call
+raises.
+
+Functions carry the C names (flame_create, flame_step, ...); ``Flame`` is a
+small convenience wrapper that owns one handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+FLAME_OK, FLAME_EINVAL, FLAME_ENOMEM, FLAME_ECUDA = 0, 1, 2, 3
+FLAME_EUNSUPPORTED, FLAME_ETIMEOUT, FLAME_ENONFINITE = 4, 5, 6
+FLAME_FP64, FLAME_FP32_MIXED = 0, 1
+FLAME_LINEAR_ONLY, FLAME_NONLINEAR_ONLY = 1, 2
+
+_STATUS = {0: "FLAME_OK", 1: "FLAME_EINVAL", 2: "FLAME_ENOMEM", 3: "FLAME_ECUDA",
+           4: "FLAME_EUNSUPPORTED", 5: "FLAME_ETIMEOUT", 6: "FLAME_ENONFINITE"}
+
+
+class FlameError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class flame_params(ctypes.Structure):
+    _fields_ = [("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("K1", ctypes.c_int), ("K2", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("theta_pi", ctypes.c_double),
+                ("s1", ctypes.c_double), ("s2", ctypes.c_double),
+                ("t0", ctypes.c_double), ("dt", ctypes.c_double),
+                ("prec", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# every symbol the header declares, with (restype, argtypes)
+_vp, _i, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+SIGNATURES = {
+    "flame_create": (_i, [ctypes.POINTER(flame_params), ctypes.POINTER(_vp)]),
+    "flame_destroy": (_i, [_vp]),
+    "flame_get_params": (_i, [_vp, ctypes.POINTER(flame_params)]),
+    "flame_state_len": (_sz, [_vp]),
+    "flame_fft_r2c": (_i, [_vp, _vp, _vp, _vp]),
+    "flame_fft_c2r": (_i, [_vp, _vp, _vp, _vp]),
+    "flame_step": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "flame_step_pass": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
+    "flame_area": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "flame_adjoint": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "flame_sync_status": (_i, [_vp]),
+    "flame_status_str": (ctypes.c_char_p, [_i]),
+    "flame_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libflame.so (building it in-tree first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not os.path.exists(path):
+                _build.build_library()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libflame.so not found at {path}; run build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != FLAME_OK:
+        msg = load().flame_last_error().decode(errors="replace")
+        raise FlameError(status, msg)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor, dtype=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _optr(t, dtype=None, name="tensor"):
+    return ctypes.c_void_p(None) if t is None else _ptr(t, dtype, name)
+
+
+# ----------------------------------------------------------------- raw C names
+def flame_create(params: flame_params) -> int:
+    h = ctypes.c_void_p()
+    _check(load().flame_create(ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def flame_destroy(h: int):
+    _check(load().flame_destroy(ctypes.c_void_p(h)))
+
+
+def flame_get_params(h: int) -> flame_params:
+    p = flame_params()
+    _check(load().flame_get_params(ctypes.c_void_p(h), ctypes.byref(p)))
+    return p
+
+
+def flame_fft_r2c(h, real_in, spec_out, stream=None):
+    _check(load().flame_fft_r2c(ctypes.c_void_p(h), _ptr(real_in, name="real_in"),
+                                _ptr(spec_out, name="spec_out"), _stream(stream)))
+
+
+def flame_fft_c2r(h, spec_in, real_out, stream=None):
+    _check(load().flame_fft_c2r(ctypes.c_void_p(h), _ptr(spec_in, name="spec_in"),
+                                _ptr(real_out, name="real_out"), _stream(stream)))
+
+
+def flame_step(h, state, mean_mode, t, nsteps=1, stream=None):
+    _check(load().flame_step(ctypes.c_void_p(h), _ptr(state, name="state"),
+                             _ptr(mean_mode, torch.float64, "mean_mode"),
+                             _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
+
+
+def flame_step_pass(h, pass_, state, mean_mode, t, stream=None):
+    _check(load().flame_step_pass(ctypes.c_void_p(h), int(pass_), _ptr(state, name="state"),
+                                  _ptr(mean_mode, torch.float64, "mean_mode"),
+                                  _ptr(t, torch.float64, "t"), _stream(stream)))
+
+
+def flame_step_batch(hs, states, mean_modes, ts, nsteps=1, stream=None):
+    n = len(hs)
+    if not (len(states) == len(mean_modes) == len(ts) == n):
+        raise ValueError("flame_step_batch: list lengths differ")
+    H = (ctypes.c_void_p * n)(*hs)
+    S = (ctypes.c_void_p * n)(*[_ptr(s, name="state").value for s in states])
+    M = (ctypes.c_void_p * n)(*[_ptr(m, torch.float64, "mean").value for m in mean_modes])
+    T = (ctypes.c_void_p * n)(*[_ptr(t, torch.float64, "t").value for t in ts])
+    _check(load().flame_step_batch(ctypes.cast(H, ctypes.c_void_p), ctypes.cast(S, ctypes.c_void_p),
+                                   ctypes.cast(M, ctypes.c_void_p), ctypes.cast(T, ctypes.c_void_p),
+                                   n, int(nsteps), _stream(stream)))
+
+
+def flame_area(h, state, mean_mode, t, area_out, dA_dstate=None, dA_dmean=None, stream=None):
+    _check(load().flame_area(ctypes.c_void_p(h), _ptr(state, name="state"),
+                             _ptr(mean_mode, torch.float64, "mean_mode"), _ptr(t, torch.float64, "t"),
+                             _ptr(area_out, torch.float64, "area_out"), _optr(dA_dstate, name="dA_dstate"),
+                             _optr(dA_dmean, torch.float64, "dA_dmean"), _stream(stream)))
+
+
+def flame_adjoint(h, state0, mean0, t_start, nsteps, ckpt_every, lambda_T, lambda0_T,
+                  grad_state0, grad_mean0, grad_gamma, stream=None):
+    f64 = torch.float64
+    _check(load().flame_adjoint(ctypes.c_void_p(h), _ptr(state0, name="state0"), _ptr(mean0, f64, "mean0"),
+                                _ptr(t_start, f64, "t_start"), int(nsteps), int(ckpt_every),
+                                _ptr(lambda_T, name="lambda_T"), _ptr(lambda0_T, f64, "lambda0_T"),
+                                _ptr(grad_state0, name="grad_state0"), _ptr(grad_mean0, f64, "grad_mean0"),
+                                _ptr(grad_gamma, f64, "grad_gamma"), _stream(stream)))
+
+
+def flame_sync_status(h):
+    _check(load().flame_sync_status(ctypes.c_void_p(h)))
+
+
+def flame_status_str(s: int) -> str:
+    return load().flame_status_str(int(s)).decode()
+
+
+def flame_last_error() -> str:
+    return load().flame_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------- convenience
+class Flame:
+    """One handle: grid, model parameters and precision (see flame_params)."""
+
+    def __init__(self, n_theta, n_phi, K1=0, K2=0, gamma=0.8, theta_pi=1.0, s1=0.0, s2=0.0,
+                 t0=200.0, dt=1e-3, prec="fp64", flags=0):
+        code = {"fp64": FLAME_FP64, "fp32": FLAME_FP32_MIXED}[prec]
+        p = flame_params(n_theta, n_phi, K1, K2, gamma, theta_pi, s1, s2, t0, dt, code, flags)
+        self.h = flame_create(p)
+        self.params = flame_get_params(self.h)
+        self.prec = prec
+        self.cdtype = torch.complex128 if prec == "fp64" else torch.complex64
+        self.rdtype = torch.float64 if prec == "fp64" else torch.float32
+
+    @property
+    def K1(self):
+        return self.params.K1
+
+    @property
+    def K2(self):
+        return self.params.K2
+
+    @property
+    def state_shape(self):
+        return (2 * self.params.K1 + 1, self.params.K2 + 1)
+
+    def step(self, state, mean_mode, t, nsteps=1, stream=None):
+        if state.dtype != self.cdtype or tuple(state.shape) != self.state_shape:
+            raise ValueError(f"state must be {self.cdtype} {self.state_shape}")
+        flame_step(self.h, state, mean_mode, t, nsteps, stream)
+
+    def fft_r2c(self, x, out=None, stream=None):
+        n1, n2 = self.params.n_theta, self.params.n_phi
+        if x.dtype != self.rdtype or tuple(x.shape) != (n1, n2):
+            raise ValueError(f"input must be {self.rdtype} ({n1}, {n2})")
+        if out is None:
+            out = torch.empty((n1, n2 // 2 + 1), dtype=self.cdtype, device=x.device)
+        flame_fft_r2c(self.h, x, out, stream)
+        return out
+
+    def fft_c2r(self, X, out=None, stream=None):
+        n1, n2 = self.params.n_theta, self.params.n_phi
+        if X.dtype != self.cdtype or tuple(X.shape) != (n1, n2 // 2 + 1):
+            raise ValueError(f"input must be {self.cdtype} ({n1}, {n2 // 2 + 1})")
+        if out is None:
+            out = torch.empty((n1, n2), dtype=self.rdtype, device=X.device)
+        flame_fft_c2r(self.h, X, out, stream)
+        return out
+
+    def sync_status(self):
+        flame_sync_status(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            flame_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

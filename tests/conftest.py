@@ -18,3 +18,31 @@ def orc():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+def pytest_collection_modifyitems(config, items):
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        return
+    skip = pytest.mark.skip(reason="no CUDA device in this environment")
+    for it in items:
+        if "gpu" in it.keywords:
+            it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def fl():
+    """The CUDA library binding (built in-tree on first use)."""
+    from paper_0911_2889_gb300 import build, flame
+    build.build_library()
+    flame.load()
+    return flame
+
+
+def rel_l2(a, b):
+    import numpy as np
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))

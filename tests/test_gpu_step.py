@@ -1,0 +1,212 @@
+"""Parity of flame_step (the hot path: passes A, B, C) against the oracle,
+through the C ABI.
+
+Bars: FP64 1e-12 relative L2 per step (one step from identical input and
+the trajectory at every step); FP32-mixed 2e-5 relative L2 for one step from
+identical input, with the trajectory drift measured and bounded.  The time
+is compared bit for bit (same FP64 formula on both sides); the mean mode to
+1e-12 (FP64) / 1e-6 relative (FP32: per-row sums of |grad Phi|^2 in FP32,
+accumulated over rows in FP64).
+"""
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_l2
+from paper_0911_2889_gb300 import inputs
+
+
+def _setup(fl, n1, n2, prec, kmax, seed, amp=1e-3, **kw):
+    f = fl.Flame(n1, n2, prec=prec, **kw)
+    st0 = inputs.spectrum_ic(n1, n2, kmax, seed, amp=amp, K1=f.K1, K2=f.K2)
+    state = torch.from_numpy(st0).cuda().to(f.cdtype)
+    st0 = state.cpu().numpy().astype(np.complex128)  # the exact input the GPU sees
+    mean = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), float(f.params.t0), dtype=torch.float64, device="cuda")
+    return f, st0, state, mean, t
+
+
+def _oparams(orc, f):
+    p = f.params
+    return orc.Params(p.n_theta, p.n_phi, K1=p.K1, K2=p.K2, gamma=p.gamma, s1=p.s1, s2=p.s2,
+                      t0=p.t0, dt=p.dt, flags=p.flags)
+
+
+def _box_err(a, b, K1):
+    a = np.array(a)
+    b = np.array(b)
+    a[K1, 0] = 0
+    b[K1, 0] = 0
+    return rel_l2(a, b)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("gamma", [0.8, 0.5])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_fp64_config1_trajectory(fl, orc, gamma, seed):
+    # 128 x 256, |k| <= 16, 100 explicit steps, dt = 1e-3, t0 = 200
+    f, st0, state, mean, t = _setup(fl, 128, 256, "fp64", 16, seed, gamma=gamma)
+    p = _oparams(orc, f)
+    ref, mref, tref = st0.copy(), 0.0, p.t0
+    worst = 0.0
+    for n in range(100):
+        # one step from the oracle's current state (identical input) ...
+        if n % 25 == 0:
+            s1 = torch.from_numpy(ref).cuda()
+            m1 = torch.tensor([mref], dtype=torch.float64, device="cuda")
+            t1 = torch.tensor([tref], dtype=torch.float64, device="cuda")
+            f.step(s1, m1, t1, 1)
+        ref, mref, tref = orc.step(p, ref, mref, tref, 1)
+        if n % 25 == 0:
+            assert _box_err(s1.cpu().numpy(), ref, f.K1) < 1e-12
+        # ... and the free-running trajectory, compared at every step
+        f.step(state, mean, t, 1)
+        e = _box_err(state.cpu().numpy(), ref, f.K1)
+        worst = max(worst, e)
+        assert e < 1e-12, (n, e)
+        assert t.item() == tref
+        assert abs(mean.item() - mref) <= 1e-12 * abs(mref) + 1e-300
+    f.sync_status()
+    f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("shape,K,s", [
+    ((16, 32), (0, 0), (1.0, 1.0)),      # smallest grid
+    ((32, 64), (5, 3), (1.0, 1.0)),      # truncation below the padding limit
+    ((64, 32), (0, 0), (2.0, 0.5)),      # anisotropic kappa, N1 > N2
+    ((256, 512), (0, 0), (1.0, 1.0)),
+    ((512, 256), (40, 63), (1.0, 1.0)),  # ragged column count (K2 + 1 odd)
+    ((2048, 4096), (0, 0), (1.0, 1.0)),
+])
+def test_one_step_identical_input(fl, orc, prec, tol, shape, K, s):
+    n1, n2 = shape
+    f, st0, state, mean, t = _setup(fl, n1, n2, prec, 1e9, 7, amp=1e-2, K1=K[0], K2=K[1],
+                                    s1=s[0], s2=s[1], t0=20.0, dt=1e-2)
+    mean.fill_(0.125)
+    f.step(state, mean, t, 1)
+    ref, mref, tref = orc.step(_oparams(orc, f), st0, 0.125, 20.0, 1)
+    assert _box_err(state.cpu().numpy(), ref, f.K1) < tol
+    assert t.item() == tref
+    assert abs(mean.item() - mref) <= (1e-14 if prec == "fp64" else 1e-7) * abs(mref)
+    out = state.cpu().numpy()
+    assert out[f.K1, 0] == 0
+    np.testing.assert_array_equal(out[: f.K1, 0], np.conj(out[f.K1 + 1:, 0][::-1]))
+    f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("flags", [1, 2])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_linear_and_nonlinear_only(fl, orc, flags, prec, tol):
+    f, st0, state, mean, t = _setup(fl, 64, 128, prec, 30, 3, amp=1e-2, flags=flags, t0=10.0, dt=1e-2)
+    f.step(state, mean, t, 3)
+    ref, mref, _ = orc.step(_oparams(orc, f), st0, 0.0, 10.0, 3)
+    assert _box_err(state.cpu().numpy(), ref, f.K1) < tol
+    if flags == 1:
+        assert mean.item() == 0.0
+    else:
+        assert abs(mean.item() - mref) <= 1e-6 * mref
+    f.close()
+
+
+@pytest.mark.gpu
+def test_fp32_config2_one_step_and_drift(fl, orc):
+    # 1024 x 2048, FP32 FFTs and pointwise work, FP64 mean mode and time,
+    # |k| <= 256, compared with the FP64 oracle every 100 steps over 1000.
+    f, st0, state, mean, t = _setup(fl, 1024, 2048, "fp32", 256, 0)
+    p = _oparams(orc, f)
+    s1 = state.clone()
+    m1, t1 = mean.clone(), t.clone()
+    f.step(s1, m1, t1, 1)
+    ref1, _, _ = orc.step(p, st0, 0.0, p.t0, 1)
+    e1 = _box_err(s1.cpu().numpy(), ref1, f.K1)
+    assert e1 < 2e-5
+    ref, mref, tref = st0, 0.0, p.t0
+    drift = []
+    for blk in range(10):
+        f.step(state, mean, t, 100)
+        ref, mref, tref = orc.step(p, ref, mref, tref, 100)
+        drift.append(_box_err(state.cpu().numpy(), ref, f.K1))
+        assert t.item() == tref
+    print(f"\nFP32 1024x2048 one-step rel L2 {e1:.3e}; drift every 100 steps: "
+          + " ".join(f"{d:.2e}" for d in drift))
+    assert max(drift) < 1e-4
+    f.close()
+
+
+@pytest.mark.gpu
+def test_fp32_full_size_one_step(fl, orc):
+    # 4096 x 8192, the large memory-bound configuration: one full step from
+    # identical input against the oracle (full comparison, every mode)
+    f, st0, state, mean, t = _setup(fl, 4096, 8192, "fp32", 256, 0)
+    f.step(state, mean, t, 1)
+    ref, mref, tref = orc.step(_oparams(orc, f), st0, 0.0, 200.0, 1)
+    assert _box_err(state.cpu().numpy(), ref, f.K1) < 2e-5
+    assert t.item() == tref
+    assert abs(mean.item() - mref) <= 1e-6 * mref
+    f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_replay_equals_single_steps(fl, prec):
+    f, st0, state, mean, t = _setup(fl, 64, 128, prec, 30, 9, amp=1e-2)
+    s2, m2, t2 = state.clone(), mean.clone(), t.clone()
+    f.step(state, mean, t, 300)            # one 256-step graph + one 44-step graph
+    for _ in range(300):
+        f.step(s2, m2, t2, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(state, s2) and torch.equal(mean, m2) and torch.equal(t, t2)
+    f.step(state, mean, t, 0)              # no-op
+    assert torch.equal(state, s2)
+    # per-pass entry equals one step
+    s3, m3, t3 = s2.clone(), m2.clone(), t2.clone()
+    for ps in range(3):
+        fl.flame_step_pass(f.h, ps, s3, m3, t3)
+    f.step(s2, m2, t2, 1)
+    assert torch.equal(s3, s2) and torch.equal(m3, m2) and torch.equal(t3, t2)
+    f.close()
+
+
+@pytest.mark.gpu
+def test_nonfinite_detected(fl):
+    f, st0, state, mean, t = _setup(fl, 32, 64, "fp32", 8, 1)
+    state[3, 2] = complex(float("nan"), 0.0)
+    f.step(state, mean, t, 1)
+    with pytest.raises(fl.FlameError) as ei:
+        f.sync_status()
+    assert ei.value.status == fl.FLAME_ENONFINITE
+    f.sync_status()  # cleared
+    f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_equals_individual(fl, prec):
+    shapes = [(64, 128), (32, 64), (64, 128), (128, 256), (32, 64)]
+    fs, ss, ms, ts, ref = [], [], [], [], []
+    for i, (n1, n2) in enumerate(shapes):
+        f, st0, state, mean, t = _setup(fl, n1, n2, prec, 10, 100 + i, amp=1e-2, gamma=0.6 + 0.05 * i)
+        fs.append(f)
+        ss.append(state)
+        ms.append(mean)
+        ts.append(t)
+        ref.append((state.clone(), mean.clone(), t.clone()))
+    fl.flame_step_batch([f.h for f in fs], ss, ms, ts, nsteps=7)
+    for f, (s, m, t) in zip(fs, ref):
+        f.step(s, m, t, 7)
+    torch.cuda.synchronize()
+    for i in range(len(fs)):
+        assert torch.equal(ss[i], ref[i][0]), i
+        assert torch.equal(ms[i], ref[i][1]) and torch.equal(ts[i], ref[i][2])
+    # a second call with the same binding replays the cached graph
+    fl.flame_step_batch([f.h for f in fs], ss, ms, ts, nsteps=7)
+    for f, (s, m, t) in zip(fs, ref):
+        f.step(s, m, t, 7)
+    torch.cuda.synchronize()
+    for i in range(len(fs)):
+        assert torch.equal(ss[i], ref[i][0]), i
+    for f in fs:
+        f.close()
