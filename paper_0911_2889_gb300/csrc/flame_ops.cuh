@@ -6,7 +6,6 @@
 
 namespace flame {
 
-constexpr size_t kMaxSmem = 227 * 1024;     // opt-in limit per CTA on sm_103a
 constexpr size_t kSmemBudget = 200 * 1024;  // what one CTA may take here
 constexpr int kThreadsTarget = 256;
 constexpr int kMaxThreads = 256;  // launch bound of every line-FFT kernel
@@ -31,12 +30,20 @@ template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { retu
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
 template <class R> cudaError_t Ops<R>::prepare() {
-    static bool done = false;  // per process; all devices of one process share the attribute
-    if (done) return cudaSuccess;
-    const int b = (int)kMaxSmem;
-    cudaError_t e = cudaSuccess;
+    static int done_dev = -1;  // the attribute is per function; set once per process
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (done_dev >= 0) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
     auto set = [&](const void *f) {
-        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, f);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
         if (r != cudaSuccess) e = r;
     };
     set((const void *)k_rows_r2c<R>);
@@ -49,7 +56,7 @@ template <class R> cudaError_t Ops<R>::prepare() {
     set((const void *)k_passA_n<R>);
     set((const void *)k_passB_n<R>);
     set((const void *)k_passC_n<R>);
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) done_dev = dev;
     return e;
 }
 
