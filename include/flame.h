@@ -178,6 +178,30 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0,
                            void *grad_state0, double *grad_mean0,
                            double *grad_gamma, void *stream);
 
+/* flame_step without any allocation (the paper has no counterpart: this is
+ * for callers of this library that cannot allocate device memory -- code
+ * running inside a host callback or a hook that forbids cudaMalloc, under a
+ * memory manager that owns the whole device, or anywhere the allocator must
+ * not be re-entered).  No handle is needed: params are validated as in
+ * flame_create, and state, mean_mode and t are the caller's buffers exactly
+ * as for flame_step, advanced by nsteps explicit Euler steps with the same
+ * kernels and the same results.  The twiddle tables, both step workspaces
+ * and the status word live in one static device array of 8 MiB that the
+ * library image reserves on every GPU that loads it, until the process exits.
+ * Grids whose scratch does not fit (roughly N1 x (K2+1) above 170k entries in
+ * FP64, 340k in FP32, e.g. 512 x 1024 FP64 fits, 4096 x 8192 does not) are
+ * rejected with FLAME_EUNSUPPORTED and a message giving the bytes needed.
+ * The function calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents; each call rewrites the tables and
+ * workspaces it reads and clears the status word, but calls whose work
+ * overlaps on the GPU (unordered streams) race on the array.  Non-finite
+ * values are not reported (there is no handle to read them from). */
+flame_status flame_step_noalloc(const flame_params *params, void *state, double *mean_mode,
+                                double *t, int nsteps, void *stream);
+
 /* Synchronises the handle's device status word and returns it
  * (FLAME_OK, FLAME_ENONFINITE or FLAME_ETIMEOUT); clears it. */
 flame_status flame_sync_status(flame_t h);

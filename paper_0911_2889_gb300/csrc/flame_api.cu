@@ -59,6 +59,8 @@ constexpr int kGraphCache = 8;
 
 }  // namespace
 
+void flame::set_last_error(const char *msg) { g_err = msg; }
+
 struct GraphEntry {
     const void *state;
     const double *mean, *t;

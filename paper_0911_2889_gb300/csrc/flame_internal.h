@@ -47,6 +47,9 @@ struct Geom {
     size_t smem;       // dynamic shared memory bytes
 };
 
+// Sets the thread-local message returned by flame_last_error().
+void set_last_error(const char *msg);
+
 // Per-precision launchers (defined in flame_f32.cu / flame_f64.cu).
 template <class R> struct Ops {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;

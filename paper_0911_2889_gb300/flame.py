@@ -60,6 +60,7 @@ SIGNATURES = {
     "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
     "flame_area": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "flame_adjoint": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "flame_step_noalloc": (_i, [ctypes.POINTER(flame_params), _vp, _vp, _vp, _i, _vp]),
     "flame_sync_status": (_i, [_vp]),
     "flame_status_str": (ctypes.c_char_p, [_i]),
     "flame_last_error": (ctypes.c_char_p, []),
@@ -182,6 +183,14 @@ def flame_adjoint(h, state0, mean0, t_start, nsteps, ckpt_every, lambda_T, lambd
                                 _ptr(lambda_T, name="lambda_T"), _ptr(lambda0_T, f64, "lambda0_T"),
                                 _ptr(grad_state0, name="grad_state0"), _ptr(grad_mean0, f64, "grad_mean0"),
                                 _ptr(grad_gamma, f64, "grad_gamma"), _stream(stream)))
+
+
+def flame_step_noalloc(params: flame_params, state, mean_mode, t, nsteps=1, stream=None):
+    """flame_step for callers that cannot allocate: scratch is the library's
+    static device array (see include/flame.h)."""
+    _check(load().flame_step_noalloc(ctypes.byref(params), _ptr(state, name="state"),
+                                     _ptr(mean_mode, torch.float64, "mean_mode"),
+                                     _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
 
 
 def flame_sync_status(h):
