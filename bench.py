@@ -274,6 +274,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """Deterministic launch sequence for ncu: two twiddle-table launches at
+    creation, then `--profile N` plain steps (passes A, B, C each), nothing else."""
+    import torch
+
+    from paper_0911_2889_gb300 import flame, inputs
+    w = WORKLOAD
+    n1, n2 = args.grid if args.grid else (w["n1"], w["n2"])
+    f = flame.Flame(n1, n2, gamma=w["gamma"], t0=w["t0"], dt=w["dt"], prec=args.prec)
+    st = torch.from_numpy(inputs.spectrum_ic(n1, n2, w["kmax"], w["seed"], K1=f.K1, K2=f.K2)).cuda().to(f.cdtype)
+    mean = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), w["t0"], dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(args.profile):
+        f.step(st, mean, t, 1)
+    torch.cuda.synchronize()
+    f.sync_status()
+    print(json.dumps({"profile_steps": args.profile, "grid": [n1, n2], "prec": args.prec}))
+    f.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -281,8 +302,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=0, help="run N plain steps for ncu and exit")
+    ap.add_argument("--grid", type=int, nargs=2, default=None, help="grid for --profile")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="precision for --profile")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
