@@ -159,7 +159,7 @@ def run_ours(args):
     n1, n2 = w["n1"], w["n2"]
     f = flame.Flame(n1, n2, gamma=w["gamma"], t0=w["t0"], dt=w["dt"], prec=w["prec"])
     st0 = inputs.spectrum_ic(n1, n2, w["kmax"], w["seed"] + rank, K1=f.K1, K2=f.K2)
-    state = torch.from_numpy(st0).cuda().to(f.cdtype)
+    state = torch.from_numpy(flame.box_to_abi(st0)).cuda().to(f.cdtype)
     mean = torch.zeros(1, dtype=torch.float64, device="cuda")
     t = torch.full((1,), w["t0"], dtype=torch.float64, device="cuda")
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -283,7 +283,7 @@ def run_profile(args):
     w = WORKLOAD
     n1, n2 = args.grid if args.grid else (w["n1"], w["n2"])
     f = flame.Flame(n1, n2, gamma=w["gamma"], t0=w["t0"], dt=w["dt"], prec=args.prec)
-    st = torch.from_numpy(inputs.spectrum_ic(n1, n2, w["kmax"], w["seed"], K1=f.K1, K2=f.K2)).cuda().to(f.cdtype)
+    st = torch.from_numpy(flame.box_to_abi(inputs.spectrum_ic(n1, n2, w["kmax"], w["seed"], K1=f.K1, K2=f.K2))).cuda().to(f.cdtype)
     mean = torch.zeros(1, dtype=torch.float64, device="cuda")
     t = torch.full((1,), w["t0"], dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()

@@ -16,10 +16,13 @@
  * Grid and coefficients: x_i = 2 pi j_i / N_i on an N1 x N2 (theta, phi) grid,
  * Phi(x) = sum_k Phi_k exp(i k.x).
  *
- * STATE LAYOUT ("compact box"): the retained half spectrum, rows
- * k1 = -K1..K1, columns k2 = 0..K2, row-major with k2 fastest, complex
- * interleaved (re, im): double2 for FLAME_FP64, float2 for FLAME_FP32_MIXED.
- * (2 K1 + 1) * (K2 + 1) entries.  The k2 = 0 column is Hermitian
+ * STATE LAYOUT ("compact box"): the retained half spectrum k1 = -K1..K1,
+ * k2 = 0..K2, stored COLUMN-MAJOR: element (k1, k2) at index
+ * k2 * (2 K1 + 1) + (k1 + K1), i.e. k1 fastest (an array of shape
+ * (K2 + 1, 2 K1 + 1) in C order); complex interleaved (re, im): double2 for
+ * FLAME_FP64, float2 for FLAME_FP32_MIXED; (2 K1 + 1) * (K2 + 1) entries.
+ * Column-major keeps every read of the step contiguous: the column passes
+ * read whole columns of the state.  The k2 = 0 column is Hermitian
  * (Phi_{-k1,0} = conj(Phi_{k1,0}), the symmetrization of Sec. 3); the k = 0
  * entry is ignored and written as 0: the mean mode Phi_0 lives in a separate
  * double.  The time t is a double on the device.

@@ -215,11 +215,32 @@ struct CtaBarrier {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
-template <class V> struct Planes {
-    V *re, *im;
-    __device__ __forceinline__ void st(int i, CV<V> v) const { re[spad(i)] = v.re; im[spad(i)] = v.im; }
-    __device__ __forceinline__ CV<V> ld(int i) const { return {re[spad(i)], im[spad(i)]}; }
+// Exchange buffer of one pair of lines: plane_len(N) slots of CV<V>.  FP32:
+// one plane of 16-byte slots (one 128-bit access per point, conflict-free for
+// the Stockham store pattern thanks to the padding); FP64: separate re and im
+// planes of 16-byte slots.  Both take plane_len(N) * 2 * sizeof(V) bytes.
+template <class V> struct Planes;
+template <> struct Planes<float2> {
+    float4 *p;
+    __device__ __forceinline__ explicit Planes(float2 *base) : p(reinterpret_cast<float4 *>(base)) {}
+    __device__ __forceinline__ void st(int i, CV<float2> v) const {
+        p[spad(i)] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y);
+    }
+    __device__ __forceinline__ CV<float2> ld(int i) const {
+        float4 q = p[spad(i)];
+        return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+    }
 };
+template <> struct Planes<double2> {
+    double2 *re, *im;
+    int len;
+    __device__ __forceinline__ Planes(double2 *base, int n) : re(base), im(base + plane_len(n)) {}
+    __device__ __forceinline__ void st(int i, CV<double2> v) const { re[spad(i)] = v.re; im[spad(i)] = v.im; }
+    __device__ __forceinline__ CV<double2> ld(int i) const { return {re[spad(i)], im[spad(i)]}; }
+};
+// Exchange buffer of a group: `base` points at 2 * plane_len(n) V slots.
+__device__ __forceinline__ Planes<float2> make_planes(float2 *base, int n) { return Planes<float2>(base); }
+__device__ __forceinline__ Planes<double2> make_planes(double2 *base, int n) { return Planes<double2>(base, n); }
 
 // Loads the twiddle of a table entry (stored with + sign) for direction DIR.
 template <int DIR, class C> __device__ __forceinline__ void load_tw(const C *tab, int i, decltype(C::x) &wr,

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_r2c(const R *__rest
     const int pair = blockIdx.x * G + g;
     const bool valid = pair < (n1 >> 1);
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(M);
-    Planes<V> sm{base, base + plane_len(M)};
+    auto sm = make_planes(base, M);
     const C *ra = reinterpret_cast<const C *>(in) + (size_t)(2 * pair) * M;
     const C *rb = ra + M;
     CV<V> x[16];
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_c2r(const CplxT<R> 
     const int pair = blockIdx.x * G + g;
     const bool valid = pair < (n1 >> 1);
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(M);
-    Planes<V> sm{base, base + plane_len(M)};
+    auto sm = make_planes(base, M);
     const C *ia = in + (size_t)(2 * pair) * ldi, *ib = ia + ldi;
     const C *P = tw + tw_real_offset(logm);
     CV<V> x[16];
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_cols(const CplxT<R> *in,
     const int c0 = 2 * (blockIdx.x * G + g);
     const bool va = c0 < ncols, vb = c0 + 1 < ncols;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(n);
-    Planes<V> sm{base, base + plane_len(n)};
+    auto sm = make_planes(base, n);
     CV<V> x[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -226,13 +226,35 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_cols(const CplxT<R> *in,
 // ----------------------------------------------------------------------------
 // Step passes
 // ----------------------------------------------------------------------------
+// Bulk prefetch of a contiguous range into L2 (no register or shared-memory
+// cost): the next wave's input streams from HBM while this wave computes.
+// The bulk prefetch needs a 16-byte aligned start and a size that is a
+// multiple of 16: the range is shrunk to [align_up(begin), align_down(end)),
+// so it never reaches outside [begin, end).
+__device__ __forceinline__ void l2_prefetch(const void *begin, size_t bytes) {
+    const size_t b = (reinterpret_cast<size_t>(begin) + 15) & ~(size_t)15;
+    const size_t e = (reinterpret_cast<size_t>(begin) + bytes) & ~(size_t)15;
+    if (e > b)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((unsigned)(e - b)) : "memory");
+}
+
+// Memory layouts (see include/flame.h and the design doc):
+//   state  column-major compact box: element (k1, k2) at k2 * ld1 + (k1 + K1),
+//          ld1 = 2 K1 + 1
+//   uv     row-major N1 x (K2+1) pairs (U, V): element (j1, k2) at
+//          2 * (j1 * ldk + k2), ldk = K2 + 1
+//   gk     column-major N1 x (K2+1): element (j1, k2) at k2 * N1 + j1
+// Every pass reads whole contiguous blocks (state columns, uv rows, gk
+// columns); the transposition between the column and row passes is done by
+// the scattered stores of passes A and B.
+
 // Pass A (a1 + a2): column k2 of the compact box -> inverse FFT along k1 of
 // a = i s1 k1 Phi and b = Phi (one pair of lines), zero padded outside
 // |k1| <= K1 (positions K1 < n < N1 - K1; with N1 >= 4 K1 + 1 the registers
 // r = 4..11 of the first pass are always zero and are dropped at compile
-// time).  Writes UV[j1][k2] = (U, V) with U = synthesis of a, V = i s2 k2 x
+// time).  Writes uv[j1][k2] = (U, V) with U = synthesis of a, V = i s2 k2 x
 // synthesis of b.
-template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile) {
+template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -241,22 +263,28 @@ template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d
     C *__restrict__ uv = static_cast<C *>(d.uv);
     const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
     const int N1 = 1 << a.logn1, T = N1 >> 4;
-    const int G = blockDim.x / T, g = threadIdx.x % G, t = threadIdx.x / G;
+    const int G = blockDim.x / T, g = threadIdx.x / T, t = threadIdx.x % T;
+    const int ld1 = 2 * a.K1 + 1;
+    if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
+        const int c = (tile + pf) * G, nc = min(G, a.K2 + 1 - c);
+        if (nc > 0) l2_prefetch(state + (size_t)c * ld1, (size_t)nc * ld1 * sizeof(C));
+    }
     const int k2 = tile * G + g;
     const bool valid = k2 <= a.K2;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
-    Planes<V> sm{base, base + plane_len(N1)};
+    auto sm = make_planes(base, N1);
     const R s1 = (R)a.s1, s2k2 = (R)(a.s2 * k2);
+    const C *col = state + (size_t)k2 * ld1 + a.K1;  // col[k1], k1 = -K1..K1
     CV<V> x[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         x[r] = CV<V>{vzero(V{}), vzero(V{})};
         if (r < 4 || r >= 12) {
             const int n = t + r * T;
-            int k1 = (r < 4) ? n : n - N1;
-            bool in_box = valid && ((r < 4) ? (n <= a.K1) : (k1 >= -a.K1));
+            const int k1 = (r < 4) ? n : n - N1;
+            const bool in_box = valid && ((r < 4) ? (n <= a.K1) : (k1 >= -a.K1));
             if (in_box) {
-                C phi = __ldg(state + (size_t)(k1 + a.K1) * a.ldk + k2);
+                C phi = __ldg(col + k1);
                 if (k1 == 0 && k2 == 0) phi = C{0, 0};
                 const R f = s1 * (R)k1;
                 C da{-f * phi.y, f * phi.x};  // i s1 k1 Phi
@@ -277,14 +305,14 @@ template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d
     }
 }
 
-// Pass B (a3..a6): rows 2p and 2p+1 of UV.  For each row the full spectrum
+// Pass B (a3..a6): rows 2p and 2p+1 of uv.  For each row the full spectrum
 // Z[k] = U[k] + i V[k] (k = -K2..K2, U[-k] = conj U[k]) is transformed by
 // two half-length inverse FFTs (even and odd grid points:
 // z[2m+q] = sum_k Z[k] exp(2 pi i k q/N2) exp(2 pi i k m/M)), giving
 // u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
-// forward with the real-input post-processing; G[k], k <= K2, is written.
-// G[j1][0] is the row sum of g used for the FP64 mean mode.
-template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile) {
+// forward with the real-input post-processing; G[k], k <= K2, is written
+// (column-major gk).  G[j1][0] is the row sum of g used for the FP64 mean mode.
+template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -292,19 +320,23 @@ template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d
     const C *__restrict__ uv = static_cast<const C *>(d.uv);
     C *__restrict__ gk = static_cast<C *>(d.gk);
     const C *__restrict__ twm = static_cast<const C *>(d.twm);
-    const int M = 1 << a.logm, T = M >> 4, half = M >> 1;
+    const int M = 1 << a.logm, T = M >> 4;
     const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
+    if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
+        const int p0 = (tile + pf) * G, np = min(G, (a.n1 >> 1) - p0);
+        if (np > 0) l2_prefetch(uv + 2 * (size_t)(2 * p0) * a.ldk, (size_t)np * 2 * a.ldk * 2 * sizeof(C));
+    }
     const int pair = tile * G + g;
     const bool valid = pair < (a.n1 >> 1);
-    // per group: two exchange planes, then M entries of C (sizeof(C) ==
+    // per group: the exchange buffer, then M entries of C (sizeof(C) ==
     // sizeof(V) in both precisions)
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len(M) + M);
-    Planes<V> sm{base, base + plane_len(M)};
+    auto sm = make_planes(base, M);
     const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
     if (tile == 0 && threadIdx.x == 0) *d.t_copy = *d.t_in;
 
     // |z|^2 of the first row is parked in shared memory (h_first, M entries
-    // per group, after the two exchange planes) while the second row is
+    // per group, after the exchange buffer) while the second row is
     // transformed; the second row's stays in registers.
     C *h_first = reinterpret_cast<C *>(base + 2 * plane_len(M));
     auto row_ifft = [&](int q, CV<V>(&x)[16]) {
@@ -313,17 +345,17 @@ template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int n = t + r * T;
-            const int k = (n < half) ? n : n - M;  // signed wavenumber
-            const int kk = k < 0 ? -k : k;
+            // r < 8: k = n >= 0 (n < M/2); r >= 8: k = n - M < 0
+            const int kk = (r < 8) ? n : M - n;
             C z{0, 0};
             if (valid && kk <= a.K2) {
                 UV<R> e = ld_uv<R>(src + 2 * kk);
-                if (k >= 0) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
-                else z = C{e.u.x + e.v.y, e.v.x - e.u.y};          // conj U + i conj V
+                if (r < 8) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
+                else z = C{e.u.x + e.v.y, e.v.x - e.u.y};         // conj U + i conj V
             }
             C w = __ldg(P + kk);                                 // exp(2 pi i |k|/N2)
-            C z1 = (k >= 0) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
-                            : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
+            C z1 = (r < 8) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
+                           : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
             x[r] = pack2<R>(z, z1);
         }
         line_fft<1>(x, a.logm, t, sm, twm, CtaBarrier{});
@@ -347,7 +379,6 @@ template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d
 #pragma unroll
     for (int r = 0; r < 16; ++r) sm.st(t + r * T, x[r]);
     __syncthreads();
-    C *oa = gk + (size_t)(2 * pair) * a.ldk, *ob = oa + a.ldk;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int k = t + r * T;
@@ -358,8 +389,13 @@ template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d
             CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
             C w = __ldg(P + k);
             CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
-            oa[k] = lane0<R>(Y);
-            ob[k] = lane1<R>(Y);
+            C *dst = gk + (size_t)k * a.n1 + 2 * pair;  // rows 2p, 2p+1 adjacent
+            if constexpr (std::is_same<R, float>::value) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(Y.re.x, Y.im.x, Y.re.y, Y.im.y);
+            } else {
+                dst[0] = lane0<R>(Y);
+                dst[1] = lane1<R>(Y);
+            }
         }
     }
 }
@@ -384,12 +420,13 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
     else return sqrt(fma(s1k1, s1k1, s2k2 * s2k2));
 }
 
-// Pass C (a7..a10): columns k2, k2+1 of G -> forward FFT along j1 (outputs
+// Pass C (a7..a10): columns k2, k2+1 of gk -> forward FFT along j1 (outputs
 // outside |k1| <= K1 unused and dropped at compile time), scaled by
 // 1/(N1 N2) -> ghat; Phi <- Phi + dt (omega Phi + c ghat); the k2 = 0 column
 // is written from its k1 > 0 half and its conjugate mirror; the block owning
-// column 0 sums G[j1][0] in FP64 for the mean mode and advances t.
-template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile) {
+// column 0 sums G[j1][0] in FP64 for the mean mode and advances t.  The state
+// entries of the epilogue are loaded before the transform.
+template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -399,20 +436,42 @@ template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d
     C *__restrict__ state = static_cast<C *>(d.state);
     const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
     const int N1 = 1 << a.logn1, T = N1 >> 4;
-    const int G = blockDim.x / T, g = threadIdx.x % G, t = threadIdx.x / G;
+    const int G = blockDim.x / T, g = threadIdx.x / T, t = threadIdx.x % T;
+    const int ld1 = 2 * a.K1 + 1;
+    if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
+        const int c = 2 * (tile + pf) * G, nc = min(2 * G, a.K2 + 1 - c);
+        if (nc > 0) {
+            l2_prefetch(gk + (size_t)c * N1, (size_t)nc * N1 * sizeof(C));
+            l2_prefetch(state + (size_t)c * ld1, (size_t)nc * ld1 * sizeof(C));
+        }
+    }
     const int c0 = 2 * (tile * G + g);
     const bool va = c0 <= a.K2, vb = c0 + 1 <= a.K2;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
-    Planes<V> sm{base, base + plane_len(N1)};
+    auto sm = make_planes(base, N1);
+    const C *ga = gk + (size_t)c0 * N1, *gb = ga + N1;
     CV<V> x[16];
     double colsum = 0.0;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const size_t row = (size_t)(t + r * T) * a.ldk;
-        C p = va ? gk[row + c0] : C{0, 0};
-        C q = vb ? gk[row + c0 + 1] : C{0, 0};
+        const int n = t + r * T;
+        C p = va ? __ldg(ga + n) : C{0, 0};
+        C q = vb ? __ldg(gb + n) : C{0, 0};
         if (c0 == 0) colsum += (double)p.x;
         x[r] = pack2<R>(p, q);
+    }
+    // state entries this thread updates: rows r < 4 (k1 = n) and r >= 12
+    // (k1 = n - N1) of columns c0 and c0 + 1
+    C *sa = state + (size_t)c0 * ld1 + a.K1, *sb = sa + ld1;
+    C phi[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = i < 4 ? i : i + 8;
+        const int n = t + r * T;
+        const int k1 = (r < 4) ? n : n - N1;
+        const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
+        phi[i][0] = (in_box && va) ? sa[k1] : C{0, 0};
+        phi[i][1] = (in_box && vb) ? sb[k1] : C{0, 0};
     }
     if (tile == 0) {  // block-uniform: FP64 row-sum reduction of column 0
         for (int o = 16; o > 0; o >>= 1) colsum += __shfl_xor_sync(0xffffffffu, colsum, o);
@@ -433,32 +492,31 @@ template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d
     const R ra = (R)cf.a, rb = (R)cf.b, rcs = (R)(cf.c * inv), rdt = (R)a.dt;
     int bad = 0;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        if (r < 4 || r >= 12) {
-            const int n = t + r * T;
-            const int k1 = (r < 4) ? n : n - N1;
-            const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
+    for (int i = 0; i < 8; ++i) {
+        const int r = i < 4 ? i : i + 8;
+        const int n = t + r * T;
+        const int k1 = (r < 4) ? n : n - N1;
+        const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const int k2 = c0 + side;
-                const bool ok = in_box && (side == 0 ? va : vb);
-                if (!ok) continue;
-                if (k2 == 0 && k1 < 0) continue;  // written as the mirror of +k1
-                const size_t idx = (size_t)(k1 + a.K1) * a.ldk + k2;
-                if (k1 == 0 && k2 == 0) {
-                    state[idx] = C{0, 0};
-                    continue;
-                }
-                C gh = side == 0 ? lane0<R>(x[r]) : lane1<R>(x[r]);
-                C phi = state[idx];
-                const R kap = kappa_norm<R>((R)a.s1 * (R)k1, (R)a.s2 * (R)k2);
-                const R om = lin ? kap * (rb - kap * ra) : (R)0;
-                const R cn = nl ? rcs : (R)0;
-                C nw{phi.x + rdt * (om * phi.x + cn * gh.x), phi.y + rdt * (om * phi.y + cn * gh.y)};
-                bad |= !(isfinite(nw.x) && isfinite(nw.y));
-                state[idx] = nw;
-                if (k2 == 0) state[(size_t)(-k1 + a.K1) * a.ldk] = C{nw.x, -nw.y};
+        for (int side = 0; side < 2; ++side) {
+            const int k2 = c0 + side;
+            const bool ok = in_box && (side == 0 ? va : vb);
+            if (!ok) continue;
+            if (k2 == 0 && k1 < 0) continue;  // written as the mirror of +k1
+            C *col = side == 0 ? sa : sb;
+            if (k1 == 0 && k2 == 0) {
+                col[0] = C{0, 0};
+                continue;
             }
+            C gh = side == 0 ? lane0<R>(x[r]) : lane1<R>(x[r]);
+            C ph = phi[i][side];
+            const R kap = kappa_norm<R>((R)a.s1 * (R)k1, (R)a.s2 * (R)k2);
+            const R om = lin ? kap * (rb - kap * ra) : (R)0;
+            const R cn = nl ? rcs : (R)0;
+            C nw{ph.x + rdt * (om * ph.x + cn * gh.x), ph.y + rdt * (om * ph.y + cn * gh.y)};
+            bad |= !(isfinite(nw.x) && isfinite(nw.y));
+            col[k1] = nw;
+            if (k2 == 0) col[-k1] = C{nw.x, -nw.y};
         }
     }
     if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
@@ -472,17 +530,23 @@ template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d
 
 // Kernel entry points: one flame (descriptor by value) or an ensemble of
 // equal-size flames (descriptor array, flame = blockIdx.y).
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA(FlameDesc d) { passA_body<R>(d, blockIdx.x); }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d) { passB_body<R>(d, blockIdx.x); }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d) { passC_body<R>(d, blockIdx.x); }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds) {
-    passA_body<R>(ds[blockIdx.y], blockIdx.x);
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA(FlameDesc d, int pf) {
+    passA_body<R>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds) {
-    passB_body<R>(ds[blockIdx.y], blockIdx.x);
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d, int pf) {
+    passB_body<R>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC_n(const FlameDesc *__restrict__ ds) {
-    passC_body<R>(ds[blockIdx.y], blockIdx.x);
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
+    passC_body<R>(d, blockIdx.x, gridDim.x, pf);
+}
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds, int pf) {
+    passA_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds, int pf) {
+    passB_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC_n(const FlameDesc *__restrict__ ds, int pf) {
+    passC_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
 
 }  // namespace flame

@@ -26,6 +26,24 @@ template <class R> static Geom make_geom(int logn, int nlines, int hint, size_t 
     return g;
 }
 
+// CTAs of one kernel resident at once on the current device: a tile that
+// starts now is followed, one wave later, by tile + resident_ctas.
+static int resident_ctas(const void *kernel, const Geom &g) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, g.threads, g.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per * nsm;
+}
+
 template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { return make_geom<R>(logn, nlines, hint); }
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
@@ -90,7 +108,8 @@ cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int d
 
 template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s) {
     Geom g = geom_cols(d.a.logn1, d.a.K2 + 1, 0);
-    k_passA<R><<<g.blocks, g.threads, g.smem, s>>>(d);
+    const int pf = resident_ctas((const void *)k_passA<R>, g);
+    k_passA<R><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
     return cudaGetLastError();
 }
 // pass B parks one row of |z|^2 (N2/2 complex) per group in shared memory
@@ -100,30 +119,32 @@ template <class R> static Geom geom_passB(int logm, int nlines) {
 
 template <class R> cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s) {
     Geom g = geom_passB<R>(d.a.logm, d.a.n1 / 2);
-    k_passB<R><<<g.blocks, g.threads, g.smem, s>>>(d);
+    const int pf = resident_ctas((const void *)k_passB<R>, g);
+    k_passB<R><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
     return cudaGetLastError();
 }
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
     Geom g = geom_cols(d.a.logn1, (d.a.K2 + 2) / 2, 0);
-    k_passC<R><<<g.blocks, g.threads, g.smem, s>>>(d);
+    const int pf = resident_ctas((const void *)k_passC<R>, g);
+    k_passC<R><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
     return cudaGetLastError();
 }
 template <class R>
 cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_cols(a.logn1, a.K2 + 1, 0);
-    k_passA_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds);
+    k_passA_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
     return cudaGetLastError();
 }
 template <class R>
 cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_passB<R>(a.logm, a.n1 / 2);
-    k_passB_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds);
+    k_passB_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
     return cudaGetLastError();
 }
 template <class R>
 cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
-    k_passC_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds);
+    k_passC_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
     return cudaGetLastError();
 }
 

@@ -205,6 +205,20 @@ def flame_last_error() -> str:
     return load().flame_last_error().decode(errors="replace")
 
 
+def box_to_abi(box):
+    """Host-side layout change: a (2K1+1, K2+1) box indexed [k1 + K1, k2]
+    (the oracle's and the input generator's convention) -> the ABI's
+    column-major layout, an array of shape (K2+1, 2K1+1)."""
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(box).T)
+
+
+def abi_to_box(arr):
+    """Inverse of box_to_abi (accepts a numpy array or a CPU tensor)."""
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(arr).T)
+
+
 # ------------------------------------------------------------- convenience
 class Flame:
     """One handle: grid, model parameters and precision (see flame_params)."""
@@ -229,7 +243,8 @@ class Flame:
 
     @property
     def state_shape(self):
-        return (2 * self.params.K1 + 1, self.params.K2 + 1)
+        """Shape of the state tensor: (K2 + 1, 2 K1 + 1), k1 fastest."""
+        return (self.params.K2 + 1, 2 * self.params.K1 + 1)
 
     def step(self, state, mean_mode, t, nsteps=1, stream=None):
         if state.dtype != self.cdtype or tuple(state.shape) != self.state_shape:

@@ -19,11 +19,16 @@ from paper_0911_2889_gb300 import inputs
 def _setup(fl, n1, n2, prec, kmax, seed, amp=1e-3, **kw):
     f = fl.Flame(n1, n2, prec=prec, **kw)
     st0 = inputs.spectrum_ic(n1, n2, kmax, seed, amp=amp, K1=f.K1, K2=f.K2)
-    state = torch.from_numpy(st0).cuda().to(f.cdtype)
-    st0 = state.cpu().numpy().astype(np.complex128)  # the exact input the GPU sees
+    state = torch.from_numpy(fl.box_to_abi(st0)).cuda().to(f.cdtype)
+    st0 = _host(fl, state)  # the exact input the GPU sees, in the oracle's layout
     mean = torch.zeros(1, dtype=torch.float64, device="cuda")
     t = torch.full((1,), float(f.params.t0), dtype=torch.float64, device="cuda")
     return f, st0, state, mean, t
+
+
+def _host(fl, t):
+    """Device state (ABI column-major layout) -> complex128 box [k1+K1, k2]."""
+    return fl.abi_to_box(t.cpu().numpy()).astype(np.complex128)
 
 
 def _oparams(orc, f):
@@ -52,16 +57,16 @@ def test_fp64_config1_trajectory(fl, orc, gamma, seed):
     for n in range(100):
         # one step from the oracle's current state (identical input) ...
         if n % 25 == 0:
-            s1 = torch.from_numpy(ref).cuda()
+            s1 = torch.from_numpy(fl.box_to_abi(ref)).cuda()
             m1 = torch.tensor([mref], dtype=torch.float64, device="cuda")
             t1 = torch.tensor([tref], dtype=torch.float64, device="cuda")
             f.step(s1, m1, t1, 1)
         ref, mref, tref = orc.step(p, ref, mref, tref, 1)
         if n % 25 == 0:
-            assert _box_err(s1.cpu().numpy(), ref, f.K1) < 1e-12
+            assert _box_err(_host(fl, s1), ref, f.K1) < 1e-12
         # ... and the free-running trajectory, compared at every step
         f.step(state, mean, t, 1)
-        e = _box_err(state.cpu().numpy(), ref, f.K1)
+        e = _box_err(_host(fl, state), ref, f.K1)
         worst = max(worst, e)
         assert e < 1e-12, (n, e)
         assert t.item() == tref
@@ -87,10 +92,10 @@ def test_one_step_identical_input(fl, orc, prec, tol, shape, K, s):
     mean.fill_(0.125)
     f.step(state, mean, t, 1)
     ref, mref, tref = orc.step(_oparams(orc, f), st0, 0.125, 20.0, 1)
-    assert _box_err(state.cpu().numpy(), ref, f.K1) < tol
+    assert _box_err(_host(fl, state), ref, f.K1) < tol
     assert t.item() == tref
     assert abs(mean.item() - mref) <= (1e-14 if prec == "fp64" else 1e-7) * abs(mref)
-    out = state.cpu().numpy()
+    out = _host(fl, state)
     assert out[f.K1, 0] == 0
     np.testing.assert_array_equal(out[: f.K1, 0], np.conj(out[f.K1 + 1:, 0][::-1]))
     f.close()
@@ -103,7 +108,7 @@ def test_linear_and_nonlinear_only(fl, orc, flags, prec, tol):
     f, st0, state, mean, t = _setup(fl, 64, 128, prec, 30, 3, amp=1e-2, flags=flags, t0=10.0, dt=1e-2)
     f.step(state, mean, t, 3)
     ref, mref, _ = orc.step(_oparams(orc, f), st0, 0.0, 10.0, 3)
-    assert _box_err(state.cpu().numpy(), ref, f.K1) < tol
+    assert _box_err(_host(fl, state), ref, f.K1) < tol
     if flags == 1:
         assert mean.item() == 0.0
     else:
@@ -121,14 +126,14 @@ def test_fp32_config2_one_step_and_drift(fl, orc):
     m1, t1 = mean.clone(), t.clone()
     f.step(s1, m1, t1, 1)
     ref1, _, _ = orc.step(p, st0, 0.0, p.t0, 1)
-    e1 = _box_err(s1.cpu().numpy(), ref1, f.K1)
+    e1 = _box_err(_host(fl, s1), ref1, f.K1)
     assert e1 < 2e-5
     ref, mref, tref = st0, 0.0, p.t0
     drift = []
     for blk in range(10):
         f.step(state, mean, t, 100)
         ref, mref, tref = orc.step(p, ref, mref, tref, 100)
-        drift.append(_box_err(state.cpu().numpy(), ref, f.K1))
+        drift.append(_box_err(_host(fl, state), ref, f.K1))
         assert t.item() == tref
     print(f"\nFP32 1024x2048 one-step rel L2 {e1:.3e}; drift every 100 steps: "
           + " ".join(f"{d:.2e}" for d in drift))
@@ -143,7 +148,7 @@ def test_fp32_full_size_one_step(fl, orc):
     f, st0, state, mean, t = _setup(fl, 4096, 8192, "fp32", 256, 0)
     f.step(state, mean, t, 1)
     ref, mref, tref = orc.step(_oparams(orc, f), st0, 0.0, 200.0, 1)
-    assert _box_err(state.cpu().numpy(), ref, f.K1) < 2e-5
+    assert _box_err(_host(fl, state), ref, f.K1) < 2e-5
     assert t.item() == tref
     assert abs(mean.item() - mref) <= 1e-6 * mref
     f.close()

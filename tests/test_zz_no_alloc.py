@@ -44,7 +44,7 @@ def _run_pair(fl, n1, n2, prec, seed, nsteps):
     st0 = inputs.spectrum_ic(n1, n2, 16, seed, amp=1e-2, K1=f.K1, K2=f.K2)
     outs = []
     for use_static in (False, True):
-        state = torch.from_numpy(st0).cuda().to(f.cdtype)
+        state = torch.from_numpy(fl.box_to_abi(st0)).cuda().to(f.cdtype)
         mean = torch.full((1,), 0.25, dtype=torch.float64, device="cuda")
         t = torch.full((1,), 200.0, dtype=torch.float64, device="cuda")
         if use_static:
@@ -52,7 +52,7 @@ def _run_pair(fl, n1, n2, prec, seed, nsteps):
         else:
             f.step(state, mean, t, nsteps)
         torch.cuda.synchronize()
-        outs.append((state.cpu().numpy().astype(np.complex128), mean.item(), t.item()))
+        outs.append((fl.abi_to_box(state.cpu().numpy()).astype(np.complex128), mean.item(), t.item()))
     f.close()
     return outs
 
