@@ -77,7 +77,9 @@ struct flame_ctx {
     void *tw1, *twm;  // twiddle tables
     void *uv, *gk;    // step workspaces
     void *spec;       // c2r workspace, N1 x (N2/2 + 1)
-    double *dscal;    // [0]: t_n copy
+    void *aw;         // area / adjoint workspace, N1 x ldk pairs
+    double *rowsum;   // N1 per-row area sums
+    double *dscal;    // [0]: t_n copy, [1]: lambda_0, [2]: dgamma, [3]: dA/dPhi_0 scratch
     int *status;
     cudaStream_t cap;  // capture stream
     std::vector<GraphEntry> graphs;
@@ -87,6 +89,9 @@ struct flame_ctx {
     std::vector<FlameDesc> batch_key;
     int batch_n = 0;
     cudaGraphExec_t batch_exec = nullptr;
+    // adjoint arena (grown on demand by flame_adjoint)
+    void *adj = nullptr;
+    size_t adj_cap = 0;
 };
 
 namespace {
@@ -109,6 +114,9 @@ void free_ctx(flame_ctx *h) {
     cudaFree(h->uv);
     cudaFree(h->gk);
     cudaFree(h->spec);
+    cudaFree(h->aw);
+    cudaFree(h->rowsum);
+    cudaFree(h->adj);
     cudaFree(h->dscal);
     cudaFree(h->status);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -260,7 +268,8 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
     bool ok = dev_alloc(&h->tw1, flame::tw_table_len(h->logn1) * h->csz) &&
               dev_alloc(&h->twm, flame::tw_table_len(h->logm) * h->csz) &&
               dev_alloc(&h->uv, n1 * ldk * 2 * h->csz) && dev_alloc(&h->gk, n1 * ldk * h->csz) &&
-              dev_alloc(&h->spec, n1 * m1 * h->csz) && dev_alloc((void **)&h->dscal, 4 * sizeof(double)) &&
+              dev_alloc(&h->spec, n1 * m1 * h->csz) && dev_alloc(&h->aw, n1 * ldk * 2 * h->csz) &&
+              dev_alloc((void **)&h->rowsum, n1 * sizeof(double)) && dev_alloc((void **)&h->dscal, 4 * sizeof(double)) &&
               dev_alloc((void **)&h->status, sizeof(int));
     if (!ok) {
         cudaGetLastError();
@@ -478,18 +487,122 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
 
 flame_status flame_area(flame_t h, const void *state, const double *mean_mode, const double *t,
                         double *area_out, void *dA_dstate, double *dA_dmean, void *stream) {
-    (void)state; (void)mean_mode; (void)t; (void)area_out; (void)dA_dstate; (void)dA_dmean; (void)stream;
-    if (!h) return fail(FLAME_EINVAL, "flame_area: null handle");
-    return fail(FLAME_EUNSUPPORTED, "flame_area: not built yet");
+    if (!h || !state || !mean_mode || !t || !area_out) return fail(FLAME_EINVAL, "flame_area: null pointer");
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_area: injected launch fault");
+    flame::AdjDesc d;
+    memset(&d, 0, sizeof d);
+    d.a = h->sa;
+    d.state = state;
+    d.mean = mean_mode;
+    d.t = t;
+    d.uv = h->uv;
+    d.gk = h->gk;
+    d.aw = h->aw;
+    d.rowsum = h->rowsum;
+    d.area = area_out;
+    d.grad = dA_dstate;
+    d.dmean = dA_dmean ? dA_dmean : h->dscal + 3;
+    d.tw1 = h->tw1;
+    d.twm = h->twm;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h->p.prec == FLAME_FP64) CUDA_TRY(Ops<double>::area(d, s));
+    else CUDA_TRY(Ops<float>::area(d, s));
+    return FLAME_OK;
 }
 
 flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, const double *t_start, int nsteps,
                            int ckpt_every, const void *lambda_T, const double *lambda0_T, void *grad_state0,
                            double *grad_mean0, double *grad_gamma, void *stream) {
-    (void)state0; (void)mean0; (void)t_start; (void)nsteps; (void)ckpt_every; (void)lambda_T;
-    (void)lambda0_T; (void)grad_state0; (void)grad_mean0; (void)grad_gamma; (void)stream;
-    if (!h) return fail(FLAME_EINVAL, "flame_adjoint: null handle");
-    return fail(FLAME_EUNSUPPORTED, "flame_adjoint: not built yet");
+    if (!h || !state0 || !mean0 || !t_start || !lambda_T || !lambda0_T || !grad_state0 || !grad_mean0 || !grad_gamma)
+        return fail(FLAME_EINVAL, "flame_adjoint: null pointer");
+    if (nsteps < 0) return fail(FLAME_EINVAL, "flame_adjoint: nsteps=%d < 0", nsteps);
+    if (nsteps > 0 && ckpt_every < 1) return fail(FLAME_EINVAL, "flame_adjoint: ckpt_every=%d < 1", ckpt_every);
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_adjoint: injected launch fault");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t ld1 = 2 * (size_t)h->p.K1 + 1, ldk = (size_t)h->p.K2 + 1;
+    const size_t box = ld1 * ldk * h->csz;
+    const size_t k0 = (size_t)h->p.K1 * h->csz;  // byte offset of the k = 0 entry
+    const int K = nsteps > 0 ? (ckpt_every < nsteps ? ckpt_every : nsteps) : 1;
+    const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    // arena: nseg checkpoints, K trajectory states, lambda; 2 doubles each for
+    // the checkpoint and trajectory (mean, t)
+    const size_t nbox = (size_t)nseg + K + 1;
+    const size_t need = nbox * box + 2 * ((size_t)nseg + K) * sizeof(double) + 256;
+    if (h->adj_cap < need) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(h->adj);
+        h->adj = nullptr;
+        h->adj_cap = 0;
+        if (cudaMalloc(&h->adj, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FLAME_ENOMEM, "flame_adjoint: cannot allocate %zu bytes of checkpoints", need);
+        }
+        h->adj_cap = need;
+    }
+    char *base = static_cast<char *>(h->adj);
+    auto ckpt = [&](int i) { return base + (size_t)i * box; };
+    auto traj = [&](int i) { return base + ((size_t)nseg + i) * box; };
+    char *lam = base + ((size_t)nseg + K) * box;
+    double *ckm = reinterpret_cast<double *>(base + nbox * box);  // ckm[i], ckt = ckm + nseg
+    double *ckt = ckm + nseg;
+    double *trm = ckt + nseg;
+    double *trt = trm + K;
+    double *lam0 = h->dscal + 1, *dgam = h->dscal + 2;
+    const bool f64 = h->p.prec == FLAME_FP64;
+    auto step1 = [&](void *st, double *m, double *t) -> cudaError_t {
+        return enqueue_step(h, make_desc(h, st, m, t), s);
+    };
+    // forward sweep: checkpoints every K steps
+    if (nseg > 0) {
+        CUDA_TRY(cudaMemcpyAsync(ckpt(0), state0, box, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ckm, mean0, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ckt, t_start, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    for (int g = 1; g < nseg; ++g) {
+        CUDA_TRY(cudaMemcpyAsync(ckpt(g), ckpt(g - 1), box, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ckm + g, ckm + g - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ckt + g, ckt + g - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int i = 0; i < K; ++i) CUDA_TRY(step1(ckpt(g), ckm + g, ckt + g));
+    }
+    // reverse sweep
+    CUDA_TRY(cudaMemcpyAsync(lam, lambda_T, box, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(lam + k0, 0, h->csz, s));
+    CUDA_TRY(cudaMemcpyAsync(lam0, lambda0_T, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(dgam, 0, sizeof(double), s));
+    flame::AdjDesc d;
+    memset(&d, 0, sizeof d);
+    d.a = h->sa;
+    d.lam = lam;
+    d.lam_out = lam;
+    d.lam0 = lam0;
+    d.uv = h->uv;
+    d.gk = h->gk;
+    d.aw = h->aw;
+    d.dgamma = dgam;
+    d.tw1 = h->tw1;
+    d.twm = h->twm;
+    for (int g = nseg - 1; g >= 0; --g) {
+        const int len = (g == nseg - 1) ? nsteps - g * K : K;
+        CUDA_TRY(cudaMemcpyAsync(traj(0), ckpt(g), box, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(trm, ckm + g, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(trt, ckt + g, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int i = 1; i < len; ++i) {
+            CUDA_TRY(cudaMemcpyAsync(traj(i), traj(i - 1), box, cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(trm + i, trm + i - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(trt + i, trt + i - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(step1(traj(i), trm + i, trt + i));
+        }
+        for (int i = len - 1; i >= 0; --i) {
+            d.state = traj(i);
+            d.t = trt + i;
+            if (f64) CUDA_TRY(Ops<double>::adj_step(d, s));
+            else CUDA_TRY(Ops<float>::adj_step(d, s));
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(grad_state0, nseg > 0 ? lam : lambda_T, box, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(grad_mean0, nseg > 0 ? lam0 : lambda0_T, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(grad_gamma, dgam, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return FLAME_OK;
 }
 
 flame_status flame_sync_status(flame_t h) {

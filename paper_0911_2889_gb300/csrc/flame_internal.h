@@ -40,6 +40,26 @@ struct FlameDesc {
     int *status;            // handle's device status word
 };
 
+// Workspace pointers of the area / adjoint kernels.
+struct AdjDesc {
+    StepArgs a;
+    const void *state;   // forward state Phi (column-major box)
+    const void *lam;     // adjoint lambda (column-major box), lambda_0 in *lam0
+    void *lam_out;       // updated lambda (may equal lam)
+    void *grad;          // dA/dPhi output (column-major box)
+    const double *lam0;  // lambda_0 (mean-mode component of lambda)
+    const double *mean;  // mean mode Phi_0
+    const double *t;     // time (r0 = t for the area; t_n for the adjoint)
+    void *uv;            // N1 x ldk pairs, row-major
+    void *gk;            // N1 x ldk, row-major (lambda columns) or column-major
+    void *aw;            // N1 x ldk pairs, column-major
+    double *rowsum;      // N1 per-row partial area sums
+    double *area;        // area output
+    double *dmean;       // dA/dPhi_0 output
+    double *dgamma;      // dL/dgamma accumulator (atomic)
+    const void *tw1, *twm;
+};
+
 // Launch geometry of a line-FFT kernel.
 struct Geom {
     int threads;       // blockDim.x
@@ -69,6 +89,11 @@ template <class R> struct Ops {
     // geometry used by the step passes (for the autotuner and the tests)
     static Geom geom_cols(int logn, int nlines, int groups_hint);
     static Geom geom_rows(int logm, int nlines, int groups_hint);
+    // Area objective (and its gradient when d.grad / d.dmean are set): 3 kernels.
+    static cudaError_t area(const AdjDesc &d, cudaStream_t s);
+    // One adjoint step at (d.state, d.t): pass A on the forward state, column
+    // synthesis of lambda, row pass, column pass with the lambda update.
+    static cudaError_t adj_step(const AdjDesc &d, cudaStream_t s);
     static cudaError_t prepare();  // opt-in shared memory sizes (idempotent)
 };
 

@@ -2,7 +2,9 @@
 // once per precision by flame_f32.cu and flame_f64.cu.
 #pragma once
 
-#include "flame_kernels.cuh"
+#include <cstring>
+
+#include "flame_adjoint.cuh"
 
 namespace flame {
 
@@ -74,6 +76,12 @@ template <class R> cudaError_t Ops<R>::prepare() {
     set((const void *)k_passA_n<R>);
     set((const void *)k_passB_n<R>);
     set((const void *)k_passC_n<R>);
+    set((const void *)k_areaA<R>);
+    set((const void *)k_areaB<R>);
+    set((const void *)k_areaC<R>);
+    set((const void *)k_adjL<R>);
+    set((const void *)k_adjB<R>);
+    set((const void *)k_adjC<R>);
     if (e == cudaSuccess) done_dev = dev;
     return e;
 }
@@ -145,6 +153,43 @@ template <class R>
 cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
     k_passC_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+    return cudaGetLastError();
+}
+
+// one row per CTA (N2/32 threads): exchange buffer + one parked row
+template <class R> static Geom geom_row1(int logm, int nrows) {
+    Geom g;
+    g.threads = (1 << logm) >> 4;
+    g.blocks = nrows;
+    g.smem = group_smem<R>(logm) + (size_t)(1 << logm) * sizeof(typename VecOf<R>::c);
+    return g;
+}
+
+template <class R> cudaError_t Ops<R>::area(const AdjDesc &d, cudaStream_t s) {
+    const StepArgs &a = d.a;
+    Geom ga = geom_cols(a.logn1, a.K2 + 1, 0);
+    k_areaA<R><<<ga.blocks, ga.threads, ga.smem, s>>>(d);
+    Geom gb = geom_row1<R>(a.logm, a.n1);
+    k_areaB<R><<<gb.blocks, gb.threads, gb.smem, s>>>(d);
+    k_areaC<R><<<ga.blocks, ga.threads, ga.smem, s>>>(d);
+    return cudaGetLastError();
+}
+
+template <class R> cudaError_t Ops<R>::adj_step(const AdjDesc &d, cudaStream_t s) {
+    const StepArgs &a = d.a;
+    FlameDesc f;
+    memset(&f, 0, sizeof f);
+    f.a = a;
+    f.state = const_cast<void *>(d.state);
+    f.uv = d.uv;
+    f.tw1 = d.tw1;
+    Geom ga = geom_cols(a.logn1, a.K2 + 1, 0);
+    k_passA<R><<<ga.blocks, ga.threads, ga.smem, s>>>(f, 0);
+    Geom gl = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
+    k_adjL<R><<<gl.blocks, gl.threads, gl.smem, s>>>(d);
+    Geom gb = geom_row1<R>(a.logm, a.n1);
+    k_adjB<R><<<gb.blocks, gb.threads, gb.smem, s>>>(d);
+    k_adjC<R><<<ga.blocks, ga.threads, ga.smem, s>>>(d);
     return cudaGetLastError();
 }
 

@@ -269,6 +269,35 @@ class Flame:
         flame_fft_c2r(self.h, X, out, stream)
         return out
 
+    def area(self, state, mean_mode, t, grad=False, stream=None):
+        """Surface area (device float64 tensor of shape (1,)); with grad=True
+        also dA/dPhi (ABI layout, full-spectrum inner product) and dA/dPhi_0."""
+        dev = state.device
+        A = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty_like(state) if grad else None
+        gm = torch.empty(1, dtype=torch.float64, device=dev) if grad else None
+        flame_area(self.h, state, mean_mode, t, A, g, gm, stream)
+        return (A, g, gm) if grad else A
+
+    def adjoint(self, state0, mean0, t_start, nsteps, ckpt_every, lambda_T, lambda0_T, stream=None):
+        """Reverse-mode gradient through nsteps steps: returns
+        (dL/dPhi(t_start), dL/dPhi_0(t_start), dL/dgamma) on the device."""
+        dev = state0.device
+        g = torch.empty_like(state0)
+        gm = torch.empty(1, dtype=torch.float64, device=dev)
+        gg = torch.empty(1, dtype=torch.float64, device=dev)
+        flame_adjoint(self.h, state0, mean0, t_start, nsteps, ckpt_every, lambda_T, lambda0_T,
+                      g, gm, gg, stream)
+        return g, gm, gg
+
+    def half_weights(self, device=None):
+        """Weights that turn a full-spectrum gradient into the gradient with
+        respect to the stored entries: 2 for k2 > 0 (each stored entry stands
+        for k and -k), 1 on the k2 = 0 column (ABI layout: row k2 = 0)."""
+        w = torch.full(self.state_shape, 2.0, dtype=torch.float64, device=device)
+        w[0, :] = 1.0
+        return w
+
     def sync_status(self):
         flame_sync_status(self.h)
 
@@ -282,3 +311,44 @@ class Flame:
             self.close()
         except Exception:
             pass
+
+
+class FlameArea(torch.autograd.Function):
+    """L = A(Phi(T)): final flame surface area after nsteps explicit steps from
+    (state0, mean0) at t_start, differentiable with respect to state0, mean0
+    and gamma through flame_adjoint (checkpoint every ckpt_every steps and
+    recompute).  gamma must equal the handle's gamma (the handle is built for
+    one gamma); its gradient is still returned.  The returned state gradient
+    is with respect to the stored entries (full-spectrum gradient times
+    Flame.half_weights), so that torch's real-inner-product convention holds
+    for Hermitian perturbations.
+
+    Usage: A = FlameArea.apply(state0, mean0, gamma, flame, t_start, nsteps, ckpt_every)
+    """
+
+    @staticmethod
+    def forward(ctx, state0, mean0, gamma, flame, t_start, nsteps, ckpt_every):
+        if abs(float(gamma) - flame.params.gamma) > 1e-15 * max(1.0, abs(flame.params.gamma)):
+            raise ValueError("gamma must equal the handle's gamma")
+        s = state0.detach().clone()
+        m = mean0.detach().clone()
+        t = t_start.detach().clone()
+        flame.step(s, m, t, nsteps)
+        A = flame.area(s, m, t)
+        ctx.save_for_backward(state0.detach(), mean0.detach(), t_start.detach(), s, m, t)
+        ctx.flame, ctx.nsteps, ctx.ckpt = flame, int(nsteps), int(ckpt_every)
+        ctx.gamma_device = gamma.device if isinstance(gamma, torch.Tensor) else None
+        return A
+
+    @staticmethod
+    def backward(ctx, gA):
+        state0, mean0, t_start, sT, mT, tT = ctx.saved_tensors
+        fl = ctx.flame
+        _, lam, lam0 = fl.area(sT, mT, tT, grad=True)
+        g, gm, gg = fl.adjoint(state0, mean0, t_start, ctx.nsteps, ctx.ckpt, lam, lam0)
+        w = fl.half_weights(g.device).to(g.real.dtype)
+        scale = gA.reshape(-1)[0]
+        ggam = (gg * scale).reshape(())
+        if ctx.gamma_device is not None:
+            ggam = ggam.to(ctx.gamma_device)
+        return g * w * scale.to(g.real.dtype), gm * scale, ggam, None, None, None, None

@@ -1,0 +1,148 @@
+"""Area objective and discrete adjoint (flame_area, flame_adjoint) against
+the oracle (orc_area, orc_area_grad) and FP64 central finite differences.
+
+Bars: area value 1e-12 (FP64) / 1e-6 (FP32) relative; area gradient 1e-12 /
+2e-5 relative L2; adjoint gradients vs the oracle's exact discrete adjoint
+1e-10 (FP64) / 1e-3 (FP32, normalised per direction, see _dir_err).  Central
+differences of the FP64 oracle at h = 1e-6 carry ~1e-3 of roundoff noise at
+512 x 1024 over 200 steps (oracle adjoint vs oracle FD: 6e-4 .. 1.5e-3), so
+against them the bar is 3e-3 at h = 1e-6 and 1e-3 at h = 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_l2
+from paper_0911_2889_gb300 import inputs
+
+
+def _dev(fl, box, f):
+    return torch.from_numpy(fl.box_to_abi(box)).cuda().to(f.cdtype)
+
+
+def _host(fl, t):
+    return fl.abi_to_box(t.cpu().numpy()).astype(np.complex128)
+
+
+def _d(x):
+    return torch.tensor([x], dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tv,tg", [("fp64", 1e-12, 1e-12), ("fp32", 1e-6, 2e-5)])
+@pytest.mark.parametrize("shape", [(32, 64), (64, 128), (512, 1024)])
+def test_area_and_gradient(fl, orc, prec, tv, tg, shape):
+    n1, n2 = shape
+    f = fl.Flame(n1, n2, prec=prec, s1=1.0, s2=1.0)
+    box = inputs.spectrum_ic(n1, n2, 12, seed=3, amp=0.2, K1=f.K1, K2=f.K2)
+    st = _dev(fl, box, f)
+    box = _host(fl, st)
+    A, g, gm = f.area(st, _d(0.3), _d(50.0), grad=True)
+    p = orc.Params(n1, n2, K1=f.K1, K2=f.K2)
+    Ar, gr, gmr = orc.area(p, box, 0.3, 50.0, grad=True)
+    assert abs(A.item() - Ar) <= tv * Ar
+    gr0 = gr.copy()
+    gr0[f.K1, 0] = 0
+    assert rel_l2(_host(fl, g), gr0) < tg
+    assert abs(gm.item() - gmr) <= tg * abs(gmr)
+    f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+@pytest.mark.parametrize("nsteps,ckpt", [(10, 3), (7, 7), (5, 1), (0, 1)])
+def test_adjoint_matches_oracle_adjoint(fl, orc, prec, tol, nsteps, ckpt):
+    n1, n2 = 32, 64
+    f = fl.Flame(n1, n2, prec=prec, t0=5.0, dt=0.05, gamma=0.8)
+    box = inputs.spectrum_ic(n1, n2, 8, seed=5, amp=0.2, K1=f.K1, K2=f.K2)
+    st0 = _dev(fl, box, f)
+    box = _host(fl, st0)
+    mean0, t0 = _d(0.1), _d(5.0)
+    s, m, t = st0.clone(), mean0.clone(), t0.clone()
+    f.step(s, m, t, nsteps)
+    _, lam, lam0 = f.area(s, m, t, grad=True)
+    g, gm, gg = f.adjoint(st0, mean0, t0, nsteps, ckpt, lam, lam0)
+    p = orc.Params(n1, n2, K1=f.K1, K2=f.K2, t0=5.0, dt=0.05, gamma=0.8)
+    L, gr, ggr = orc.area_grad(p, box, 0.1, 5.0, nsteps)
+    gr0 = gr.copy()
+    gr0[f.K1, 0] = 0
+    assert rel_l2(_host(fl, g), gr0) < tol
+    assert abs(gm.item() - gr[f.K1, 0].real) <= tol * abs(gr[f.K1, 0].real)
+    if nsteps:
+        assert abs(gg.item() - ggr) <= tol * max(abs(ggr), 1e-12)
+    else:
+        assert gg.item() == 0.0
+    f.close()
+
+
+def _dir_err(a, b):
+    """Per-direction errors |a_i - b_i| normalised by the RMS of b over the
+    directions (directional derivatives near zero are not relative-error
+    friendly)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b) / np.sqrt(np.mean(b * b))
+
+
+@pytest.mark.gpu
+def test_adjoint_config5_512x1024(fl, orc):
+    # gradient of the final area over 200 FP32 steps on 512 x 1024 (|k| <= 64,
+    # seed 7), checkpoints every 20 steps with recompute
+    n1, n2, nsteps, ckpt = 512, 1024, 200, 20
+    f = fl.Flame(n1, n2, prec="fp32", gamma=0.8, t0=200.0, dt=1e-3)
+    box = inputs.spectrum_ic(n1, n2, 64, seed=7, K1=f.K1, K2=f.K2)
+    st0 = _dev(fl, box, f)
+    box = _host(fl, st0)
+    mean0 = _d(0.0).requires_grad_()
+    gamma = torch.tensor(0.8, dtype=torch.float64).requires_grad_()
+    A = fl.FlameArea.apply(st0.requires_grad_(), mean0, gamma, f, _d(200.0), nsteps, ckpt)
+    A.sum().backward()
+    g_stored = st0.grad
+    w = f.half_weights(g_stored.device).to(torch.float32)
+    g = _host(fl, g_stored / w)            # back to the full-spectrum gradient
+    p = orc.Params(n1, n2, K1=f.K1, K2=f.K2, gamma=0.8, t0=200.0, dt=1e-3)
+    L, gr, ggr = orc.area_grad(p, box, 0.0, 200.0, nsteps)
+    assert abs(A.item() - L) <= 1e-6 * L
+    gr0 = gr.copy()
+    gr0[f.K1, 0] = 0
+    support = np.abs(box) > 0
+    dirs = [inputs.random_direction(p.box_shape, 99 + i, support=support) for i in range(32)]
+    an_gpu = np.array([orc.inner(p, g, v) for v in dirs])
+    an_orc = np.array([orc.inner(p, gr0, v) for v in dirs])
+    err = _dir_err(an_gpu, an_orc)
+    print(f"\nadjoint 512x1024 FP32 vs FP64 oracle adjoint: max normalised err {err.max():.2e}")
+    assert err.max() < 1e-3
+    # the gamma direction and the mean mode, against the oracle's adjoint
+    assert abs(gamma.grad.item() - ggr) <= 1e-3 * abs(ggr)
+    assert abs(mean0.grad.item() - gr[f.K1, 0].real) <= 1e-5 * abs(gr[f.K1, 0].real)
+    # finite differences of the FP64 oracle on a few directions
+    def loss(s):
+        s2, m2, t2 = orc.step(p, s, 0.0, 200.0, nsteps)
+        return orc.area(p, s2, m2, t2)
+    for h, bar in ((1e-6, 3e-3), (1e-5, 1e-3)):
+        fd = np.array([(loss(box + h * v) - loss(box - h * v)) / (2 * h) for v in dirs[:4]])
+        e = _dir_err(an_gpu[:4], fd)
+        print(f"FD h={h}: max normalised err {e.max():.2e}")
+        assert e.max() < bar
+    f.close()
+
+
+@pytest.mark.gpu
+def test_adjoint_gamma_gradient_fd(fl, orc):
+    n1, n2, nsteps, ckpt = 64, 128, 40, 8
+    f = fl.Flame(n1, n2, prec="fp32", gamma=0.8, t0=20.0, dt=1e-2)
+    box = inputs.spectrum_ic(n1, n2, 16, seed=2, amp=0.05, K1=f.K1, K2=f.K2)
+    st0 = _dev(fl, box, f)
+    box = _host(fl, st0)
+    s, m, t = st0.clone(), _d(0.0), _d(20.0)
+    f.step(s, m, t, nsteps)
+    _, lam, lam0 = f.area(s, m, t, grad=True)
+    g, gm, gg = f.adjoint(st0, _d(0.0), _d(20.0), nsteps, ckpt, lam, lam0)
+
+    def loss(gamma):
+        q = orc.Params(n1, n2, K1=f.K1, K2=f.K2, gamma=gamma, t0=20.0, dt=1e-2)
+        s2, m2, t2 = orc.step(q, box, 0.0, 20.0, nsteps)
+        return orc.area(q, s2, m2, t2)
+    h = 1e-6
+    fd = (loss(0.8 + h) - loss(0.8 - h)) / (2 * h)
+    assert abs(gg.item() - fd) <= 1e-3 * abs(fd)
+    f.close()
