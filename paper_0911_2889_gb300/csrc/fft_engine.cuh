@@ -79,7 +79,7 @@ template <class V, class R> __device__ __forceinline__ CV<V> cscale(CV<V> a, R s
 }
 
 // compile-time loop
-template <int B, int E, class F> __device__ __forceinline__ void static_for(F &&f) {
+template <int B, int E, class F> __host__ __device__ __forceinline__ void static_for(F &&f) {
     if constexpr (B < E) {
         f(std::integral_constant<int, B>{});
         static_for<B + 1, E>(f);
@@ -191,13 +191,13 @@ template <int R, int DIR, class V> __device__ __forceinline__ void dft(CV<V> *x)
 //       w[k] = exp(2 pi i k / (2N)),                  k < N
 // Stored with the + sign; forward transforms use the conjugate.
 // ----------------------------------------------------------------------------
-__host__ __device__ inline int tw_pass_offset(int s) {  // offset of pass s >= 1
+__host__ __device__ constexpr int tw_pass_offset(int s) {  // offset of pass s >= 1
     int off = 0, ns = 16;
     for (int q = 1; q < s; ++q) { off += 15 * ns; ns <<= 4; }
     return off;
 }
-__host__ __device__ inline int tw_final_offset(int logN) { return tw_pass_offset(logN >> 2); }
-__host__ __device__ inline int tw_real_offset(int logN) {
+__host__ __device__ constexpr int tw_final_offset(int logN) { return tw_pass_offset(logN >> 2); }
+__host__ __device__ constexpr int tw_real_offset(int logN) {
     int rho = 1 << (logN & 3);
     int N = 1 << logN;
     return tw_final_offset(logN) + (rho - 1) * (N / rho);
@@ -207,8 +207,8 @@ __host__ __device__ inline int tw_table_len(int logN) { return tw_real_offset(lo
 // ----------------------------------------------------------------------------
 // Shared-memory exchange
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
-__host__ __device__ inline int plane_len(int N) { return N + (N >> 4); }
+__host__ __device__ constexpr int spad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int plane_len(int N) { return N + (N >> 4); }
 
 // Barrier over the threads that share the exchange buffers.
 struct CtaBarrier {
@@ -230,6 +230,14 @@ template <> struct Planes<float2> {
         float4 q = p[spad(i)];
         return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
     }
+    // slot index already padded
+    __device__ __forceinline__ void st_raw(int j, CV<float2> v) const {
+        p[j] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y);
+    }
+    __device__ __forceinline__ CV<float2> ld_raw(int j) const {
+        float4 q = p[j];
+        return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+    }
 };
 template <> struct Planes<double2> {
     double2 *re, *im;
@@ -237,6 +245,8 @@ template <> struct Planes<double2> {
     __device__ __forceinline__ Planes(double2 *base, int n) : re(base), im(base + plane_len(n)) {}
     __device__ __forceinline__ void st(int i, CV<double2> v) const { re[spad(i)] = v.re; im[spad(i)] = v.im; }
     __device__ __forceinline__ CV<double2> ld(int i) const { return {re[spad(i)], im[spad(i)]}; }
+    __device__ __forceinline__ void st_raw(int j, CV<double2> v) const { re[j] = v.re; im[j] = v.im; }
+    __device__ __forceinline__ CV<double2> ld_raw(int j) const { return {re[j], im[j]}; }
 };
 // Exchange buffer of a group: `base` points at 2 * plane_len(n) V slots.
 __device__ __forceinline__ Planes<float2> make_planes(float2 *base, int n) { return Planes<float2>(base); }
@@ -316,6 +326,80 @@ __device__ __forceinline__ void line_fft(CV<V> (&x)[16], int logN, int t, const 
         else if (lr == 2) final_pass(std::integral_constant<int, 4>{});
         else final_pass(std::integral_constant<int, 8>{});
     }
+}
+
+// Same transform with the length known at compile time (LOGN): pass
+// strides, twiddle-table offsets and padded exchange addresses fold into
+// immediates.  Padded addresses are base + r * stride because the strides are
+// multiples of 16 (spad(a + 16 b) = spad(a) + 17 b):
+//   store of pass s:  spad(idxD + r Ns) = spad(idxD) + r (Ns == 1 ? 1 : Ns + Ns/16)
+//   load:             spad(t + r T)     = spad(t) + r (T + T/16)      (T >= 16)
+template <int DIR, int LOGN, class V, class C, class Bar>
+__device__ __forceinline__ void line_fft_ct(CV<V> (&x)[16], int t, const Planes<V> &sm,
+                                            const C *__restrict__ tw, Bar bar) {
+    using Real = decltype(C::x);
+    constexpr int N = 1 << LOGN, T = N >> 4, P16 = LOGN >> 2, LR = LOGN & 3;
+    static_for<0, P16>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        constexpr int Ns = 1 << (4 * s);
+        if constexpr (s > 0) {
+            const C *tp = tw + tw_pass_offset(s) + (t & (Ns - 1));
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                Real wr, wi;
+                load_tw<DIR>(tp, (r - 1) * Ns, wr, wi);
+                x[r] = cmul_s(x[r], wr, wi);
+            }
+        }
+        dft<16, DIR>(x);
+        constexpr bool last = (s == P16 - 1) && (LR == 0);
+        if constexpr (!last) {
+            const int idxD = ((t >> (4 * s)) << (4 * s + 4)) + (t & (Ns - 1));
+            const int wb = spad(idxD);
+            constexpr int ws = (Ns == 1) ? 1 : Ns + Ns / 16;
+            bar();
+#pragma unroll
+            for (int r = 0; r < 16; ++r) sm.st_raw(wb + r * ws, x[r]);
+            bar();
+            if constexpr (T >= 16) {
+                const int rb = spad(t);
+                constexpr int rs = T + T / 16;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) x[r] = sm.ld_raw(rb + r * rs);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) x[r] = sm.ld(t + r * T);
+            }
+        }
+    });
+    if constexpr (LR > 0) {
+        constexpr int rho = 1 << LR, B = 16 / rho, Ns = N / rho;
+        const C *twf = tw + tw_final_offset(LOGN);
+#pragma unroll
+        for (int mm = 0; mm < B; ++mm) {
+            const int j = t + mm * T;
+            CV<V> y[rho];
+#pragma unroll
+            for (int q = 0; q < rho; ++q) y[q] = x[mm + q * B];
+#pragma unroll
+            for (int q = 1; q < rho; ++q) {
+                Real wr, wi;
+                load_tw<DIR>(twf, (q - 1) * Ns + j, wr, wi);
+                y[q] = cmul_s(y[q], wr, wi);
+            }
+            dft<rho, DIR>(y);
+#pragma unroll
+            for (int q = 0; q < rho; ++q) x[mm + q * B] = y[q];
+        }
+    }
+}
+
+// Compile-time length when LOG > 0, runtime length otherwise.
+template <int DIR, int LOG, class V, class C>
+__device__ __forceinline__ void fft_line(CV<V> (&x)[16], int logn, int t, const Planes<V> &sm,
+                                         const C *__restrict__ tw) {
+    if constexpr (LOG > 0) line_fft_ct<DIR, LOG>(x, t, sm, tw, CtaBarrier{});
+    else line_fft<DIR>(x, logn, t, sm, tw, CtaBarrier{});
 }
 
 }  // namespace flame

@@ -254,7 +254,7 @@ __device__ __forceinline__ void l2_prefetch(const void *begin, size_t bytes) {
 // r = 4..11 of the first pass are always zero and are dropped at compile
 // time).  Writes uv[j1][k2] = (U, V) with U = synthesis of a, V = i s2 k2 x
 // synthesis of b.
-template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+template <class R, int LOG> __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -262,7 +262,7 @@ template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d
     const C *__restrict__ state = static_cast<const C *>(d.state);
     C *__restrict__ uv = static_cast<C *>(d.uv);
     const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
-    const int N1 = 1 << a.logn1, T = N1 >> 4;
+    const int N1 = LOG > 0 ? (1 << LOG) : (1 << a.logn1), T = N1 >> 4;
     const int G = blockDim.x / T, g = threadIdx.x / T, t = threadIdx.x % T;
     const int ld1 = 2 * a.K1 + 1;
     if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
@@ -292,7 +292,7 @@ template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d
             }
         }
     }
-    line_fft<1>(x, a.logn1, t, sm, tw1, CtaBarrier{});
+    fft_line<1, LOG>(x, a.logn1, t, sm, tw1);
     if (valid) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -312,7 +312,7 @@ template <class R> __device__ __forceinline__ void passA_body(const FlameDesc &d
 // u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
 // forward with the real-input post-processing; G[k], k <= K2, is written
 // (column-major gk).  G[j1][0] is the row sum of g used for the FP64 mean mode.
-template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+template <class R, int LOG> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -320,7 +320,7 @@ template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d
     const C *__restrict__ uv = static_cast<const C *>(d.uv);
     C *__restrict__ gk = static_cast<C *>(d.gk);
     const C *__restrict__ twm = static_cast<const C *>(d.twm);
-    const int M = 1 << a.logm, T = M >> 4;
+    const int M = LOG > 0 ? (1 << LOG) : (1 << a.logm), T = M >> 4;
     const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
     if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
         const int p0 = (tile + pf) * G, np = min(G, (a.n1 >> 1) - p0);
@@ -358,7 +358,7 @@ template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d
                            : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
             x[r] = pack2<R>(z, z1);
         }
-        line_fft<1>(x, a.logm, t, sm, twm, CtaBarrier{});
+        fft_line<1, LOG>(x, a.logm, t, sm, twm);
     };
     CV<V> x[16];
     row_ifft(0, x);
@@ -374,7 +374,7 @@ template <class R> __device__ __forceinline__ void passB_body(const FlameDesc &d
         V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
         x[r] = pack2<R>(h_first[t + r * T], C{sq.x, sq.y});
     }
-    line_fft<-1>(x, a.logm, t, sm, twm, CtaBarrier{});
+    fft_line<-1, LOG>(x, a.logm, t, sm, twm);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 16; ++r) sm.st(t + r * T, x[r]);
@@ -426,7 +426,7 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
 // is written from its k1 > 0 half and its conjugate mirror; the block owning
 // column 0 sums G[j1][0] in FP64 for the mean mode and advances t.  The state
 // entries of the epilogue are loaded before the transform.
-template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+template <class R, int LOG> __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -435,7 +435,7 @@ template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d
     const C *__restrict__ gk = static_cast<const C *>(d.gk);
     C *__restrict__ state = static_cast<C *>(d.state);
     const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
-    const int N1 = 1 << a.logn1, T = N1 >> 4;
+    const int N1 = LOG > 0 ? (1 << LOG) : (1 << a.logn1), T = N1 >> 4;
     const int G = blockDim.x / T, g = threadIdx.x / T, t = threadIdx.x % T;
     const int ld1 = 2 * a.K1 + 1;
     if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
@@ -484,7 +484,7 @@ template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d
         }
         // red[0] is read after the transform's barriers
     }
-    line_fft<-1>(x, a.logn1, t, sm, tw1, CtaBarrier{});
+    fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
 
     const Coef cf = step_coef(a, *d.t_copy);
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
@@ -529,24 +529,28 @@ template <class R> __device__ __forceinline__ void passC_body(const FlameDesc &d
 }
 
 // Kernel entry points: one flame (descriptor by value) or an ensemble of
-// equal-size flames (descriptor array, flame = blockIdx.y).
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA(FlameDesc d, int pf) {
-    passA_body<R>(d, blockIdx.x, gridDim.x, pf);
+// equal-size flames (descriptor array, flame = blockIdx.y).  LOG > 0: line
+// length 2^LOG fixed at compile time; LOG = 0: any length.
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA(FlameDesc d, int pf) {
+    passA_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d, int pf) {
-    passB_body<R>(d, blockIdx.x, gridDim.x, pf);
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d, int pf) {
+    passB_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
-    passC_body<R>(d, blockIdx.x, gridDim.x, pf);
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
+    passC_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds, int pf) {
-    passA_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds, int pf) {
+    passA_body<R, LOG>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds, int pf) {
-    passB_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds, int pf) {
+    passB_body<R, LOG>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC_n(const FlameDesc *__restrict__ ds, int pf) {
-    passC_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC_n(const FlameDesc *__restrict__ ds, int pf) {
+    passC_body<R, LOG>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
 
 }  // namespace flame

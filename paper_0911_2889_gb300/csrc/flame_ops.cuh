@@ -46,6 +46,26 @@ static int resident_ctas(const void *kernel, const Geom &g) {
     return per * nsm;
 }
 
+// Line lengths with compile-time step kernels: FP32 2^8 .. 2^12 (the
+// benchmark, ensemble and adjoint grids); everything else (and FP64) runs the
+// runtime-length kernels (LOG = 0).
+template <class R, class F> static void for_each_log(F &&f) {
+    f(std::integral_constant<int, 0>{});
+    if constexpr (sizeof(R) == 4) static_for<8, 13>(f);
+}
+template <class R, class F> static void with_log(int logn, F &&f) {
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        static_for<8, 13>([&](auto lc) {
+            if (!done && logn == decltype(lc)::value) {
+                f(lc);
+                done = true;
+            }
+        });
+    }
+    if (!done) f(std::integral_constant<int, 0>{});
+}
+
 template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { return make_geom<R>(logn, nlines, hint); }
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
@@ -70,12 +90,15 @@ template <class R> cudaError_t Ops<R>::prepare() {
     set((const void *)k_rows_c2r<R>);
     set((const void *)k_cols<R, -1>);
     set((const void *)k_cols<R, 1>);
-    set((const void *)k_passA<R>);
-    set((const void *)k_passB<R>);
-    set((const void *)k_passC<R>);
-    set((const void *)k_passA_n<R>);
-    set((const void *)k_passB_n<R>);
-    set((const void *)k_passC_n<R>);
+    for_each_log<R>([&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        set((const void *)k_passA<R, L>);
+        set((const void *)k_passB<R, L>);
+        set((const void *)k_passC<R, L>);
+        set((const void *)k_passA_n<R, L>);
+        set((const void *)k_passB_n<R, L>);
+        set((const void *)k_passC_n<R, L>);
+    });
     set((const void *)k_areaA<R>);
     set((const void *)k_areaB<R>);
     set((const void *)k_areaC<R>);
@@ -116,8 +139,11 @@ cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int d
 
 template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s) {
     Geom g = geom_cols(d.a.logn1, d.a.K2 + 1, 0);
-    const int pf = resident_ctas((const void *)k_passA<R>, g);
-    k_passA<R><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+    with_log<R>(d.a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        const int pf = resident_ctas((const void *)k_passA<R, L>, g);
+        k_passA<R, L><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+    });
     return cudaGetLastError();
 }
 // pass B parks one row of |z|^2 (N2/2 complex) per group in shared memory
@@ -127,32 +153,47 @@ template <class R> static Geom geom_passB(int logm, int nlines) {
 
 template <class R> cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s) {
     Geom g = geom_passB<R>(d.a.logm, d.a.n1 / 2);
-    const int pf = resident_ctas((const void *)k_passB<R>, g);
-    k_passB<R><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+    with_log<R>(d.a.logm, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        const int pf = resident_ctas((const void *)k_passB<R, L>, g);
+        k_passB<R, L><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+    });
     return cudaGetLastError();
 }
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
     Geom g = geom_cols(d.a.logn1, (d.a.K2 + 2) / 2, 0);
-    const int pf = resident_ctas((const void *)k_passC<R>, g);
-    k_passC<R><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+    with_log<R>(d.a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        const int pf = resident_ctas((const void *)k_passC<R, L>, g);
+        k_passC<R, L><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+    });
     return cudaGetLastError();
 }
 template <class R>
 cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_cols(a.logn1, a.K2 + 1, 0);
-    k_passA_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+    with_log<R>(a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        k_passA_n<R, L><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+    });
     return cudaGetLastError();
 }
 template <class R>
 cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_passB<R>(a.logm, a.n1 / 2);
-    k_passB_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+    with_log<R>(a.logm, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        k_passB_n<R, L><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+    });
     return cudaGetLastError();
 }
 template <class R>
 cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
-    k_passC_n<R><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+    with_log<R>(a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        k_passC_n<R, L><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+    });
     return cudaGetLastError();
 }
 
@@ -184,7 +225,7 @@ template <class R> cudaError_t Ops<R>::adj_step(const AdjDesc &d, cudaStream_t s
     f.uv = d.uv;
     f.tw1 = d.tw1;
     Geom ga = geom_cols(a.logn1, a.K2 + 1, 0);
-    k_passA<R><<<ga.blocks, ga.threads, ga.smem, s>>>(f, 0);
+    k_passA<R, 0><<<ga.blocks, ga.threads, ga.smem, s>>>(f, 0);
     Geom gl = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
     k_adjL<R><<<gl.blocks, gl.threads, gl.smem, s>>>(d);
     Geom gb = geom_row1<R>(a.logm, a.n1);
