@@ -264,6 +264,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
             "gpu_launches": 3 * args.steps,
+            "tuning": dict(zip(("passA", "passB"), flame.flame_tuning(f.h))),
             "clocks": clk.summary(),
             "wall_s": wall,
             "cpu_baseline": cpu,

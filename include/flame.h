@@ -99,6 +99,13 @@ flame_status flame_destroy(flame_t h);
 /* Copies the resolved parameters (K1, K2, s1, s2 filled in) into *out. */
 flame_status flame_get_params(flame_t h, flame_params *out);
 
+/* Kernel variants the autotuner chose for this handle (FP32 grids with
+ * N1, N2/2 in 256..4096 are timed once per grid, precision and device at
+ * creation, FLAME_AUTOTUNE=0 disables it): pass A 0 = cluster write-out
+ * through distributed shared memory, 1 = direct stores; pass B 0 = 16 points
+ * per thread, 1 = 8 points per thread.  EINVAL on null pointers. */
+flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant);
+
 /* Number of complex entries of the compact box, (2 K1 + 1) * (K2 + 1). */
 size_t flame_state_len(flame_t h);
 

@@ -191,24 +191,28 @@ template <int R, int DIR, class V> __device__ __forceinline__ void dft(CV<V> *x)
 //       w[k] = exp(2 pi i k / (2N)),                  k < N
 // Stored with the + sign; forward transforms use the conjugate.
 // ----------------------------------------------------------------------------
-__host__ __device__ constexpr int tw_pass_offset(int s) {  // offset of pass s >= 1
-    int off = 0, ns = 16;
-    for (int q = 1; q < s; ++q) { off += 15 * ns; ns <<= 4; }
+__host__ __device__ constexpr int tw_pass_offset(int s, int LE = 4) {  // offset of pass s >= 1
+    int off = 0, ns = 1 << LE;
+    for (int q = 1; q < s; ++q) { off += ((1 << LE) - 1) * ns; ns <<= LE; }
     return off;
 }
-__host__ __device__ constexpr int tw_final_offset(int logN) { return tw_pass_offset(logN >> 2); }
-__host__ __device__ constexpr int tw_real_offset(int logN) {
-    int rho = 1 << (logN & 3);
-    int N = 1 << logN;
-    return tw_final_offset(logN) + (rho - 1) * (N / rho);
+__host__ __device__ constexpr int tw_final_offset(int logN, int LE = 4) { return tw_pass_offset(logN / LE, LE); }
+__host__ __device__ constexpr int tw_real_offset(int logN, int LE = 4) {
+    return tw_final_offset(logN, LE) + ((1 << (logN % LE)) - 1) * ((1 << logN) >> (logN % LE));
 }
-__host__ __device__ inline int tw_table_len(int logN) { return tw_real_offset(logN) + (1 << logN); }
+__host__ __device__ constexpr int tw_table_len(int logN, int LE = 4) { return tw_real_offset(logN, LE) + (1 << logN); }
+// A line's twiddle allocation: the radix-16 table followed by the radix-8
+// table (used by the 8-point-per-thread kernels).
+__host__ __device__ constexpr int tw_alloc_len(int logN) { return tw_table_len(logN, 4) + tw_table_len(logN, 3); }
 
 // ----------------------------------------------------------------------------
 // Shared-memory exchange
 // ----------------------------------------------------------------------------
 __host__ __device__ constexpr int spad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int plane_len(int N) { return N + (N >> 4); }
+// radix-E exchanges pad one slot every E (E = 8 or 16)
+template <int E> __host__ __device__ constexpr int spad_e(int i) { return i + (i >> (E == 16 ? 4 : 3)); }
+template <int E> __host__ __device__ constexpr int plane_len_e(int N) { return N + (N >> (E == 16 ? 4 : 3)); }
 
 // Barrier over the threads that share the exchange buffers.
 struct CtaBarrier {
@@ -328,53 +332,56 @@ __device__ __forceinline__ void line_fft(CV<V> (&x)[16], int logN, int t, const 
     }
 }
 
-// Same transform with the length known at compile time (LOGN): pass
+// Same transform with the length known at compile time (LOGN) and E points
+// per thread (radix-E passes, E = 16 or 8; T = N/E threads per line): pass
 // strides, twiddle-table offsets and padded exchange addresses fold into
-// immediates.  Padded addresses are base + r * stride because the strides are
-// multiples of 16 (spad(a + 16 b) = spad(a) + 17 b):
-//   store of pass s:  spad(idxD + r Ns) = spad(idxD) + r (Ns == 1 ? 1 : Ns + Ns/16)
-//   load:             spad(t + r T)     = spad(t) + r (T + T/16)      (T >= 16)
-template <int DIR, int LOGN, class V, class C, class Bar>
-__device__ __forceinline__ void line_fft_ct(CV<V> (&x)[16], int t, const Planes<V> &sm,
+// immediates.  With one pad slot every E slots, padded addresses are
+// base + r * stride because the strides are multiples of E:
+//   store of pass s:  spad(idxD + r Ns) = spad(idxD) + r (Ns == 1 ? 1 : Ns + Ns/E)
+//   load:             spad(t + r T)     = spad(t) + r (T + T/E)      (T >= E)
+// `tw` is the radix-E table of this length.
+template <int DIR, int LOGN, int E, class V, class C, class Bar>
+__device__ __forceinline__ void line_fft_ct(CV<V> (&x)[E], int t, const Planes<V> &sm,
                                             const C *__restrict__ tw, Bar bar) {
     using Real = decltype(C::x);
-    constexpr int N = 1 << LOGN, T = N >> 4, P16 = LOGN >> 2, LR = LOGN & 3;
-    static_for<0, P16>([&](auto sc) {
+    constexpr int LE = E == 16 ? 4 : 3;
+    constexpr int N = 1 << LOGN, T = N / E, P = LOGN / LE, LR = LOGN % LE;
+    static_for<0, P>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        constexpr int Ns = 1 << (4 * s);
+        constexpr int Ns = 1 << (LE * s);
         if constexpr (s > 0) {
-            const C *tp = tw + tw_pass_offset(s) + (t & (Ns - 1));
+            const C *tp = tw + tw_pass_offset(s, LE) + (t & (Ns - 1));
 #pragma unroll
-            for (int r = 1; r < 16; ++r) {
+            for (int r = 1; r < E; ++r) {
                 Real wr, wi;
                 load_tw<DIR>(tp, (r - 1) * Ns, wr, wi);
                 x[r] = cmul_s(x[r], wr, wi);
             }
         }
-        dft<16, DIR>(x);
-        constexpr bool last = (s == P16 - 1) && (LR == 0);
+        dft<E, DIR>(x);
+        constexpr bool last = (s == P - 1) && (LR == 0);
         if constexpr (!last) {
-            const int idxD = ((t >> (4 * s)) << (4 * s + 4)) + (t & (Ns - 1));
-            const int wb = spad(idxD);
-            constexpr int ws = (Ns == 1) ? 1 : Ns + Ns / 16;
+            const int idxD = ((t >> (LE * s)) << (LE * s + LE)) + (t & (Ns - 1));
+            const int wb = spad_e<E>(idxD);
+            constexpr int ws = (Ns == 1) ? 1 : Ns + Ns / E;
             bar();
 #pragma unroll
-            for (int r = 0; r < 16; ++r) sm.st_raw(wb + r * ws, x[r]);
+            for (int r = 0; r < E; ++r) sm.st_raw(wb + r * ws, x[r]);
             bar();
-            if constexpr (T >= 16) {
-                const int rb = spad(t);
-                constexpr int rs = T + T / 16;
+            if constexpr (T >= E) {
+                const int rb = spad_e<E>(t);
+                constexpr int rs = T + T / E;
 #pragma unroll
-                for (int r = 0; r < 16; ++r) x[r] = sm.ld_raw(rb + r * rs);
+                for (int r = 0; r < E; ++r) x[r] = sm.ld_raw(rb + r * rs);
             } else {
 #pragma unroll
-                for (int r = 0; r < 16; ++r) x[r] = sm.ld(t + r * T);
+                for (int r = 0; r < E; ++r) x[r] = sm.ld_raw(spad_e<E>(t + r * T));
             }
         }
     });
     if constexpr (LR > 0) {
-        constexpr int rho = 1 << LR, B = 16 / rho, Ns = N / rho;
-        const C *twf = tw + tw_final_offset(LOGN);
+        constexpr int rho = 1 << LR, B = E / rho, Ns = N / rho;
+        const C *twf = tw + tw_final_offset(LOGN, LE);
 #pragma unroll
         for (int mm = 0; mm < B; ++mm) {
             const int j = t + mm * T;
@@ -398,7 +405,7 @@ __device__ __forceinline__ void line_fft_ct(CV<V> (&x)[16], int t, const Planes<
 template <int DIR, int LOG, class V, class C>
 __device__ __forceinline__ void fft_line(CV<V> (&x)[16], int logn, int t, const Planes<V> &sm,
                                          const C *__restrict__ tw) {
-    if constexpr (LOG > 0) line_fft_ct<DIR, LOG>(x, t, sm, tw, CtaBarrier{});
+    if constexpr (LOG > 0) line_fft_ct<DIR, LOG, 16>(x, t, sm, tw, CtaBarrier{});
     else line_fft<DIR>(x, logn, t, sm, tw, CtaBarrier{});
 }
 

@@ -8,6 +8,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -92,6 +94,8 @@ struct flame_ctx {
     // adjoint arena (grown on demand by flame_adjoint)
     void *adj = nullptr;
     size_t adj_cap = 0;
+    // kernel variants picked by the autotuner for passes A and B
+    int var_a = 0, var_b = 0;
 };
 
 namespace {
@@ -143,13 +147,98 @@ FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
 cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
     cudaError_t e;
     if (h->p.prec == FLAME_FP64) {
-        if ((e = Ops<double>::passA(d, s)) != cudaSuccess) return e;
-        if ((e = Ops<double>::passB(d, s)) != cudaSuccess) return e;
+        if ((e = Ops<double>::passA(d, s, h->var_a)) != cudaSuccess) return e;
+        if ((e = Ops<double>::passB(d, s, h->var_b)) != cudaSuccess) return e;
         return Ops<double>::passC(d, s);
     }
-    if ((e = Ops<float>::passA(d, s)) != cudaSuccess) return e;
-    if ((e = Ops<float>::passB(d, s)) != cudaSuccess) return e;
+    if ((e = Ops<float>::passA(d, s, h->var_a)) != cudaSuccess) return e;
+    if ((e = Ops<float>::passB(d, s, h->var_b)) != cudaSuccess) return e;
     return Ops<float>::passC(d, s);
+}
+
+// ---------------------------------------------------------------- autotuner
+// For FP32 grids with compile-time kernels (N1, N2/2 in 256..4096) the
+// alternative shapes of passes A and B are timed once per (grid, K,
+// precision, device) on scratch buffers, and the fastest is kept for the
+// process.  FLAME_AUTOTUNE=0 keeps the default shapes.
+using TuneKey = std::tuple<int, int, int, int, int, int>;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+std::mutex g_tune_mu;
+
+flame_status autotune(flame_ctx *h) {
+    // FLAME_FORCE_VARIANTS=a,b fixes the variants (tests exercise each one)
+    const char *force = getenv("FLAME_FORCE_VARIANTS");
+    if (force) {
+        int va = 0, vb = 0;
+        if (sscanf(force, "%d,%d", &va, &vb) == 2) {
+            h->var_a = va ? flame::kVariantDirect : flame::kVariantDefault;
+            h->var_b = vb ? flame::kVariantRadix8 : flame::kVariantDefault;
+            return FLAME_OK;
+        }
+    }
+    const char *env = getenv("FLAME_AUTOTUNE");
+    if (env && strcmp(env, "0") == 0) return FLAME_OK;
+    if (h->p.prec != FLAME_FP32_MIXED || h->logn1 < 8 || h->logn1 > 12 || h->logm < 8 || h->logm > 12)
+        return FLAME_OK;
+    const TuneKey key{h->p.n_theta, h->p.n_phi, h->p.K1, h->p.K2, (int)h->p.prec, h->device};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            h->var_a = it->second.first;
+            h->var_b = it->second.second;
+            return FLAME_OK;
+        }
+    }
+    const size_t box = (2 * (size_t)h->p.K1 + 1) * ((size_t)h->p.K2 + 1) * h->csz;
+    void *st = nullptr;
+    double *sc = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(st);
+        cudaFree(sc);
+    };
+    if (cudaMalloc(&st, box) != cudaSuccess || cudaMalloc((void **)&sc, 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return FLAME_OK;  // tuning is optional: keep the defaults
+    }
+    double init[2] = {0.0, h->p.t0};
+    cudaError_t e = cudaMemsetAsync(st, 0, box, h->cap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc, init, sizeof init, cudaMemcpyHostToDevice, h->cap);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const FlameDesc d = make_desc(h, st, sc, sc + 1);
+    auto time_it = [&](int pass, int variant, float *ms) -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        float total = 0.f;
+        for (int rep = 0; rep < 4 && r == cudaSuccess; ++rep) {
+            r = cudaEventRecord(e0, h->cap);
+            if (r == cudaSuccess)
+                r = pass == 0 ? Ops<float>::passA(d, h->cap, variant) : Ops<float>::passB(d, h->cap, variant);
+            if (r == cudaSuccess) r = cudaEventRecord(e1, h->cap);
+            if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (r == cudaSuccess) r = cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) total += t;  // the first run is the warm-up
+        }
+        *ms = total / 3.f;
+        return r;
+    };
+    float a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    if (e == cudaSuccess) e = time_it(0, flame::kVariantDefault, &a0);
+    if (e == cudaSuccess) e = time_it(0, flame::kVariantDirect, &a1);
+    if (e == cudaSuccess) e = time_it(1, flame::kVariantDefault, &b0);
+    if (e == cudaSuccess) e = time_it(1, flame::kVariantRadix8, &b1);
+    cleanup();
+    if (e != cudaSuccess) return fail(FLAME_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    h->var_a = a1 < a0 ? flame::kVariantDirect : flame::kVariantDefault;
+    h->var_b = b1 < b0 ? flame::kVariantRadix8 : flame::kVariantDefault;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {h->var_a, h->var_b};
+    return FLAME_OK;
 }
 
 // Captures n steps of one flame on the handle's capture stream.
@@ -265,8 +354,8 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
         return fail(FLAME_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ge));
     }
     const size_t n1 = p.n_theta, ldk = a.ldk, m1 = p.n_phi / 2 + 1;
-    bool ok = dev_alloc(&h->tw1, flame::tw_table_len(h->logn1) * h->csz) &&
-              dev_alloc(&h->twm, flame::tw_table_len(h->logm) * h->csz) &&
+    bool ok = dev_alloc(&h->tw1, flame::tw_alloc_len(h->logn1) * h->csz) &&
+              dev_alloc(&h->twm, flame::tw_alloc_len(h->logm) * h->csz) &&
               dev_alloc(&h->uv, n1 * ldk * 2 * h->csz) && dev_alloc(&h->gk, n1 * ldk * h->csz) &&
               dev_alloc(&h->spec, n1 * m1 * h->csz) && dev_alloc(&h->aw, n1 * ldk * 2 * h->csz) &&
               dev_alloc((void **)&h->rowsum, n1 * sizeof(double)) && dev_alloc((void **)&h->dscal, 4 * sizeof(double)) &&
@@ -289,11 +378,19 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap);
         if (e != cudaSuccess) st = fail(FLAME_ECUDA, "flame_create: %s", cudaGetErrorString(e));
     }
+    if (st == FLAME_OK) st = autotune(h);
     if (st != FLAME_OK) {
         free_ctx(h);
         return st;
     }
     *out = h;
+    return FLAME_OK;
+}
+
+flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant) {
+    if (!h || !pass_a_variant || !pass_b_variant) return fail(FLAME_EINVAL, "flame_tuning: null pointer");
+    *pass_a_variant = h->var_a;
+    *pass_b_variant = h->var_b;
     return FLAME_OK;
 }
 
@@ -412,14 +509,19 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
     }
     // group by grid: one launch per pass and size class
     std::map<std::vector<int>, std::vector<FlameDesc>> classes;
+    std::map<std::vector<int>, const flame_ctx *> first;
     for (int i = 0; i < nflames; ++i) {
         const StepArgs &a = hs[i]->sa;
-        classes[{a.n1, a.n2, a.K1, a.K2}].push_back(make_desc(hs[i], states[i], mean_modes[i], ts[i]));
+        std::vector<int> key{a.n1, a.n2, a.K1, a.K2};
+        classes[key].push_back(make_desc(hs[i], states[i], mean_modes[i], ts[i]));
+        if (!first.count(key)) first[key] = hs[i];
     }
     std::vector<FlameDesc> flat;
     std::vector<std::pair<size_t, size_t>> ranges;  // (offset, count) per class
+    std::vector<const flame_ctx *> class_handle;
     for (auto &kv : classes) {
         ranges.emplace_back(flat.size(), kv.second.size());
+        class_handle.push_back(first[kv.first]);
         flat.insert(flat.end(), kv.second.begin(), kv.second.end());
     }
     const size_t bytes = flat.size() * sizeof(FlameDesc);
@@ -454,13 +556,14 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
                     const StepArgs &a = flat[rg.first].a;
                     const FlameDesc *d = dev + rg.first;
                     const int n = (int)rg.second;
+                    const flame_ctx *hc = class_handle[&rg - &ranges[0]];
                     if (h0->p.prec == FLAME_FP64)
-                        le = pass == 0 ? Ops<double>::passA_batch(d, n, a, h0->cap)
-                           : pass == 1 ? Ops<double>::passB_batch(d, n, a, h0->cap)
+                        le = pass == 0 ? Ops<double>::passA_batch(d, n, a, h0->cap, hc->var_a)
+                           : pass == 1 ? Ops<double>::passB_batch(d, n, a, h0->cap, hc->var_b)
                                        : Ops<double>::passC_batch(d, n, a, h0->cap);
                     else
-                        le = pass == 0 ? Ops<float>::passA_batch(d, n, a, h0->cap)
-                           : pass == 1 ? Ops<float>::passB_batch(d, n, a, h0->cap)
+                        le = pass == 0 ? Ops<float>::passA_batch(d, n, a, h0->cap, hc->var_a)
+                           : pass == 1 ? Ops<float>::passB_batch(d, n, a, h0->cap, hc->var_b)
                                        : Ops<float>::passC_batch(d, n, a, h0->cap);
                     if (le != cudaSuccess) break;
                 }

@@ -12,6 +12,11 @@ constexpr unsigned kNonlinearOnly = 2u;
 constexpr int kStatusNonfinite = 0;
 constexpr int kStatusTimeout = 1;
 
+// Kernel variants chosen by the autotuner (0 = default shape).
+constexpr int kVariantDefault = 0;
+constexpr int kVariantDirect = 1;   // pass A: direct scattered stores (no cluster write-out)
+constexpr int kVariantRadix8 = 1;   // pass B: 8 points per thread, 512-thread CTAs
+
 // Plain-old-data arguments of the step kernels.
 struct StepArgs {
     int n1, n2;        // grid
@@ -80,11 +85,15 @@ template <class R> struct Ops {
                             cudaStream_t s);
     // One step pass for one flame (desc by value) or for nflames flames of
     // the same grid (descs: device array of nflames entries, shape from a).
-    static cudaError_t passA(const FlameDesc &d, cudaStream_t s);
-    static cudaError_t passB(const FlameDesc &d, cudaStream_t s);
+    // variant: kVariantDefault, or a tuned alternative (pass A: kVariantDirect
+    // = no cluster write-out; pass B: kVariantRadix8 = 8 points per thread)
+    static cudaError_t passA(const FlameDesc &d, cudaStream_t s, int variant = 0);
+    static cudaError_t passB(const FlameDesc &d, cudaStream_t s, int variant = 0);
     static cudaError_t passC(const FlameDesc &d, cudaStream_t s);
-    static cudaError_t passA_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
-    static cudaError_t passB_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
+    static cudaError_t passA_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
+                                   int variant = 0);
+    static cudaError_t passB_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
+                                   int variant = 0);
     static cudaError_t passC_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
     // geometry used by the step passes (for the autotuner and the tests)
     static Geom geom_cols(int logn, int nlines, int groups_hint);

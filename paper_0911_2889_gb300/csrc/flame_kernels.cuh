@@ -17,6 +17,8 @@
 // transform goes through shared memory.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "fft_engine.cuh"
 #include "flame_internal.h"
 
@@ -63,21 +65,21 @@ template <class R> __device__ __forceinline__ CplxT<R> lane1(CV<typename VecOf<R
 // ----------------------------------------------------------------------------
 // Twiddle table generation (FP64 sincospi, rounded once)
 // ----------------------------------------------------------------------------
-template <class R> __global__ void k_twiddles(CplxT<R> *tab, int logN) {
-    const int N = 1 << logN;
-    const int len = tw_table_len(logN);
-    const int fin = tw_final_offset(logN);
-    const int real = tw_real_offset(logN);
+template <class R> __global__ void k_twiddles(CplxT<R> *tab, int logN, int LE) {
+    const int N = 1 << logN, E = 1 << LE;
+    const int len = tw_table_len(logN, LE);
+    const int fin = tw_final_offset(logN, LE);
+    const int real = tw_real_offset(logN, LE);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
         long num, den;  // angle = 2 pi num / den
         if (i < fin) {
-            int s = 1, off = 0, ns = 16;
-            while (i >= off + 15 * ns) { off += 15 * ns; ns <<= 4; ++s; }
+            int off = 0, ns = E;
+            while (i >= off + (E - 1) * ns) { off += (E - 1) * ns; ns <<= LE; }
             int r = (i - off) / ns + 1, m = (i - off) % ns;
             num = (long)r * m;
-            den = 16L * ns;
+            den = (long)E * ns;
         } else if (i < real) {
-            int rho = 1 << (logN & 3), ns = N / rho;
+            int rho = 1 << (logN % LE), ns = N / rho;
             int q = (i - fin) / ns + 1, m = (i - fin) % ns;
             num = (long)q * m;
             den = N;
@@ -238,6 +240,19 @@ __device__ __forceinline__ void l2_prefetch(const void *begin, size_t bytes) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((unsigned)(e - b)) : "memory");
 }
 
+// Compile-time CTA shape of the FP32 step kernels (LOG > 0): G line groups of
+// T = 2^LOG / 16 threads, and, for pass A, clusters of CL CTAs (CL G = 8
+// columns) that write their transposed output cooperatively through
+// distributed shared memory, one 128-byte line per row.
+template <int LOG> struct Shape {
+    static constexpr int T = (1 << LOG) >> 4;
+    static constexpr int G = T >= 256 ? 1 : 256 / T;
+    static constexpr int CL = (LOG > 0 && G <= 8) ? 8 / G : 1;
+};
+template <> struct Shape<0> {
+    static constexpr int T = 0, G = 0, CL = 1;
+};
+
 // Memory layouts (see include/flame.h and the design doc):
 //   state  column-major compact box: element (k1, k2) at k2 * ld1 + (k1 + K1),
 //          ld1 = 2 K1 + 1
@@ -293,7 +308,41 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
         }
     }
     fft_line<1, LOG>(x, a.logn1, t, sm, tw1);
-    if (valid) {
+    constexpr int CL = Shape<LOG>::CL;
+    if constexpr (CL > 1 && std::is_same<R, float>::value) {
+        // Park (U, V) of this column at its natural row index, then the CL
+        // CTAs of the cluster (CL G adjacent columns) write rows: CTA q takes
+        // rows [q N1/CL, (q+1) N1/CL), consecutive threads consecutive columns
+        // of one row (CL G x 16 bytes = 128 contiguous bytes per row).
+        namespace cg = cooperative_groups;
+        cg::cluster_group cluster = cg::this_cluster();
+        constexpr int GG = Shape<LOG>::G, NC = CL * GG, NN = 1 << LOG, ROWS = NN / CL;
+        float4 *park = reinterpret_cast<float4 *>(base);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int n = t + r * T;
+            C U = lane0<R>(x[r]);
+            C Vb = lane1<R>(x[r]);
+            park[spad(n)] = make_float4(U.x, U.y, -s2k2 * Vb.y, s2k2 * Vb.x);
+        }
+        cluster.sync();
+        const int q = (int)cluster.block_rank();
+        const int col0 = (tile / CL) * NC;
+        static_assert((ROWS * NC) % 256 == 0, "256 threads per CTA");
+#pragma unroll
+        for (int i = 0; i < ROWS * NC / 256; ++i) {
+            const int e = (int)threadIdx.x + 256 * i;
+            const int c = e % NC, n = q * ROWS + e / NC;
+            const int kc = col0 + c;
+            const float4 *rb = cluster.map_shared_rank(
+                reinterpret_cast<const float4 *>(reinterpret_cast<V *>(smraw) + (size_t)(c % GG) * 2 * plane_len(NN)),
+                c / GG);
+            const float4 v = rb[spad(n)];
+            if (kc <= a.K2) *reinterpret_cast<float4 *>(uv + 2 * ((size_t)n * a.ldk + kc)) = v;
+        }
+        cluster.sync();
+    } else if (valid) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int n = t + r * T;
@@ -312,7 +361,15 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
 // u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
 // forward with the real-input post-processing; G[k], k <= K2, is written
 // (column-major gk).  G[j1][0] is the row sum of g used for the FP64 mean mode.
-template <class R, int LOG> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+// E points per thread: 16 (runtime-length kernels, FP64) or 8 (compile-time
+// FP32 kernels: 512-thread CTAs at 64 registers, two CTAs per SM).
+template <int DIR, int LOG, int E, class V, class C>
+__device__ __forceinline__ void fft_line_e(CV<V> (&x)[E], int logn, int t, const Planes<V> &sm, const C *tw) {
+    if constexpr (E == 8) line_fft_ct<DIR, LOG, 8>(x, t, sm, tw + tw_table_len(LOG, 4), CtaBarrier{});
+    else fft_line<DIR, LOG>(x, logn, t, sm, tw);
+}
+
+template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -320,7 +377,7 @@ template <class R, int LOG> __device__ __forceinline__ void passB_body(const Fla
     const C *__restrict__ uv = static_cast<const C *>(d.uv);
     C *__restrict__ gk = static_cast<C *>(d.gk);
     const C *__restrict__ twm = static_cast<const C *>(d.twm);
-    const int M = LOG > 0 ? (1 << LOG) : (1 << a.logm), T = M >> 4;
+    const int M = LOG > 0 ? (1 << LOG) : (1 << a.logm), T = M / E;
     const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
     if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
         const int p0 = (tile + pf) * G, np = min(G, (a.n1 >> 1) - p0);
@@ -330,60 +387,60 @@ template <class R, int LOG> __device__ __forceinline__ void passB_body(const Fla
     const bool valid = pair < (a.n1 >> 1);
     // per group: the exchange buffer, then M entries of C (sizeof(C) ==
     // sizeof(V) in both precisions)
-    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len(M) + M);
-    auto sm = make_planes(base, M);
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len_e<E>(M) + M);
+    auto sm = make_planes(base, M);  // (E = 8 uses its own padding: st_raw/ld_raw)
     const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
     if (tile == 0 && threadIdx.x == 0) *d.t_copy = *d.t_in;
 
     // |z|^2 of the first row is parked in shared memory (h_first, M entries
     // per group, after the exchange buffer) while the second row is
     // transformed; the second row's stays in registers.
-    C *h_first = reinterpret_cast<C *>(base + 2 * plane_len(M));
-    auto row_ifft = [&](int q, CV<V>(&x)[16]) {
+    C *h_first = reinterpret_cast<C *>(base + 2 * plane_len_e<E>(M));
+    auto row_ifft = [&](int q, CV<V>(&x)[E]) {
         const int row = 2 * pair + q;
         const C *src = uv + 2 * (size_t)row * a.ldk;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
+        for (int r = 0; r < E; ++r) {
             const int n = t + r * T;
-            // r < 8: k = n >= 0 (n < M/2); r >= 8: k = n - M < 0
-            const int kk = (r < 8) ? n : M - n;
+            // r < E/2: k = n >= 0 (n < M/2); r >= E/2: k = n - M < 0
+            const int kk = (r < E / 2) ? n : M - n;
             C z{0, 0};
             if (valid && kk <= a.K2) {
                 UV<R> e = ld_uv<R>(src + 2 * kk);
-                if (r < 8) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
+                if (r < E / 2) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
                 else z = C{e.u.x + e.v.y, e.v.x - e.u.y};         // conj U + i conj V
             }
             C w = __ldg(P + kk);                                 // exp(2 pi i |k|/N2)
-            C z1 = (r < 8) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
+            C z1 = (r < E / 2) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
                            : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
             x[r] = pack2<R>(z, z1);
         }
-        fft_line<1, LOG>(x, a.logm, t, sm, twm);
+        fft_line_e<1, LOG, E>(x, a.logm, t, sm, twm);
     };
-    CV<V> x[16];
+    CV<V> x[E];
     row_ifft(0, x);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < E; ++r) {
         // g at grid points 2m and 2m+1: |z_0|^2, |z_1|^2
         V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
         h_first[t + r * T] = C{sq.x, sq.y};
     }
     row_ifft(1, x);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < E; ++r) {
         V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
         x[r] = pack2<R>(h_first[t + r * T], C{sq.x, sq.y});
     }
-    fft_line<-1, LOG>(x, a.logm, t, sm, twm);
+    fft_line_e<-1, LOG, E>(x, a.logm, t, sm, twm);
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 16; ++r) sm.st(t + r * T, x[r]);
+    for (int r = 0; r < E; ++r) sm.st_raw(spad_e<E>(t + r * T), x[r]);
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < E / 2; ++r) {
         const int k = t + r * T;
         if (valid && k <= a.K2) {
-            CV<V> h = x[r], hc = sm.ld((M - k) & (M - 1));
+            CV<V> h = x[r], hc = sm.ld_raw(spad_e<E>((M - k) & (M - 1)));
             const R hf = (R)0.5;
             CV<V> E{vmul(vadd(h.re, hc.re), vbc(hf)), vmul(vsub(h.im, hc.im), vbc(hf))};
             CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
@@ -535,7 +592,11 @@ template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>
     passA_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
 }
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d, int pf) {
-    passB_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
+    passB_body<R, LOG, 16>(d, blockIdx.x, gridDim.x, pf);
+}
+// 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
+template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passB8(FlameDesc d, int pf) {
+    passB_body<R, LOG, 8>(d, blockIdx.x, gridDim.x, pf);
 }
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
     passC_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
@@ -546,7 +607,11 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc 
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds, int pf) {
-    passB_body<R, LOG>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+    passB_body<R, LOG, 16>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG>
+__global__ void __launch_bounds__(512, 2) k_passB8_n(const FlameDesc *__restrict__ ds, int pf) {
+    passB_body<R, LOG, 8>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC_n(const FlameDesc *__restrict__ ds, int pf) {

@@ -153,8 +153,8 @@ flame_status flame_step_noalloc(const flame_params *params, void *state, double 
     // scratch layout: twiddles (N1), twiddles (N2/2), (U,V), G, scalars
     const size_t csz = p.prec == FLAME_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t off_tw1 = 0;
-    const size_t off_twm = off_tw1 + align256(flame::tw_table_len(a.logn1) * csz);
-    const size_t off_uv = off_twm + align256(flame::tw_table_len(a.logm) * csz);
+    const size_t off_twm = off_tw1 + align256(flame::tw_alloc_len(a.logn1) * csz);
+    const size_t off_uv = off_twm + align256(flame::tw_alloc_len(a.logm) * csz);
     const size_t off_gk = off_uv + align256((size_t)a.n1 * a.ldk * 2 * csz);
     const size_t off_sc = off_gk + align256((size_t)a.n1 * a.ldk * csz);
     const size_t need = off_sc + 256;

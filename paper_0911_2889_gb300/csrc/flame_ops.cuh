@@ -66,6 +66,34 @@ template <class R, class F> static void with_log(int logn, F &&f) {
     if (!done) f(std::integral_constant<int, 0>{});
 }
 
+// Launch with a thread-block cluster of `cl` CTAs along x (grid.x must be a
+// multiple of cl); cl <= 1 is a plain launch.
+template <class... KArgs, class... Args>
+static cudaError_t launch_cl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t s, int cl,
+                             Args... args) {
+    if (cl <= 1) {
+        kernel<<<grid, threads, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <class R, int L> static constexpr int cluster_of() {
+    return (sizeof(R) == 4 && L > 0) ? Shape<L>::CL : 1;
+}
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
 template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { return make_geom<R>(logn, nlines, hint); }
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
@@ -97,6 +125,8 @@ template <class R> cudaError_t Ops<R>::prepare() {
         set((const void *)k_passC<R, L>);
         set((const void *)k_passA_n<R, L>);
         set((const void *)k_passB_n<R, L>);
+        set((const void *)k_passB8<R, L>);
+        set((const void *)k_passB8_n<R, L>);
         set((const void *)k_passC_n<R, L>);
     });
     set((const void *)k_areaA<R>);
@@ -110,8 +140,10 @@ template <class R> cudaError_t Ops<R>::prepare() {
 }
 
 template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStream_t s) {
-    const int len = tw_table_len(logN);
-    k_twiddles<R><<<(len + 255) / 256, 256, 0, s>>>(tab, logN);
+    // radix-16 table, then the radix-8 table (tw_alloc_len entries in all)
+    const int len16 = tw_table_len(logN, 4), len8 = tw_table_len(logN, 3);
+    k_twiddles<R><<<(len16 + 255) / 256, 256, 0, s>>>(tab, logN, 4);
+    k_twiddles<R><<<(len8 + 255) / 256, 256, 0, s>>>(tab + len16, logN, 3);
     return cudaGetLastError();
 }
 
@@ -137,13 +169,21 @@ cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int d
     return cudaGetLastError();
 }
 
-template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s) {
+template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant) {
     Geom g = geom_cols(d.a.logn1, d.a.K2 + 1, 0);
+    cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        const int pf = resident_ctas((const void *)k_passA<R, L>, g);
-        k_passA<R, L><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+        constexpr int cl = cluster_of<R, L>();
+        if (cl > 1 && variant == kVariantDirect) {  // same kernel shape without the cluster write-out
+            const int pf = resident_ctas((const void *)k_passA<R, 0>, g);
+            err = launch_cl(k_passA<R, 0>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+        } else {
+            const int pf = resident_ctas((const void *)k_passA<R, L>, g);
+            err = launch_cl(k_passA<R, L>, dim3(round_up(g.blocks, cl)), g.threads, g.smem, s, cl, d, pf);
+        }
     });
+    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 // pass B parks one row of |z|^2 (N2/2 complex) per group in shared memory
@@ -151,13 +191,33 @@ template <class R> static Geom geom_passB(int logm, int nlines) {
     return make_geom<R>(logm, nlines, 0, (size_t)(1 << logm) * sizeof(typename VecOf<R>::c));
 }
 
-template <class R> cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s) {
+// pass B with 8 points per thread: 512-thread CTAs, padding every 8 slots
+template <class R> static Geom geom_passB8(int logm, int nlines) {
+    const int T = (1 << logm) >> 3;
+    const int G = T >= 512 ? 1 : 512 / T;
+    Geom g;
+    g.threads = G * T;
+    g.blocks = (nlines + G - 1) / G;
+    g.smem = (size_t)G * (2 * (size_t)plane_len_e<8>(1 << logm) * sizeof(typename VecOf<R>::type) +
+                          (size_t)(1 << logm) * sizeof(typename VecOf<R>::c));
+    return g;
+}
+
+template <class R> cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant) {
     Geom g = geom_passB<R>(d.a.logm, d.a.n1 / 2);
+    cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        const int pf = resident_ctas((const void *)k_passB<R, L>, g);
-        k_passB<R, L><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+        if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {
+            const Geom g8 = geom_passB8<R>(L, d.a.n1 / 2);
+            const int pf = resident_ctas((const void *)k_passB8<R, L>, g8);
+            err = launch_cl(k_passB8<R, L>, dim3(g8.blocks), g8.threads, g8.smem, s, 1, d, pf);
+        } else {
+            const int pf = resident_ctas((const void *)k_passB<R, L>, g);
+            err = launch_cl(k_passB<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+        }
     });
+    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
@@ -170,21 +230,34 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
     return cudaGetLastError();
 }
 template <class R>
-cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
+cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant) {
     Geom g = geom_cols(a.logn1, a.K2 + 1, 0);
+    cudaError_t err = cudaSuccess;
     with_log<R>(a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        k_passA_n<R, L><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+        constexpr int cl = cluster_of<R, L>();
+        if (cl > 1 && variant == kVariantDirect)
+            err = launch_cl(k_passA_n<R, 0>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        else
+            err = launch_cl(k_passA_n<R, L>, dim3(round_up(g.blocks, cl), n), g.threads, g.smem, s, cl, ds, 0);
     });
+    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 template <class R>
-cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
+cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant) {
     Geom g = geom_passB<R>(a.logm, a.n1 / 2);
+    cudaError_t err = cudaSuccess;
     with_log<R>(a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        k_passB_n<R, L><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+        if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {
+            const Geom g8 = geom_passB8<R>(L, a.n1 / 2);
+            err = launch_cl(k_passB8_n<R, L>, dim3(g8.blocks, n), g8.threads, g8.smem, s, 1, ds, 0);
+        } else {
+            err = launch_cl(k_passB_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        }
     });
+    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 template <class R>

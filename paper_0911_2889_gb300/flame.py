@@ -53,6 +53,7 @@ SIGNATURES = {
     "flame_destroy": (_i, [_vp]),
     "flame_get_params": (_i, [_vp, ctypes.POINTER(flame_params)]),
     "flame_state_len": (_sz, [_vp]),
+    "flame_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "flame_fft_r2c": (_i, [_vp, _vp, _vp, _vp]),
     "flame_fft_c2r": (_i, [_vp, _vp, _vp, _vp]),
     "flame_step": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
@@ -131,6 +132,13 @@ def flame_get_params(h: int) -> flame_params:
     p = flame_params()
     _check(load().flame_get_params(ctypes.c_void_p(h), ctypes.byref(p)))
     return p
+
+
+def flame_tuning(h):
+    """(pass A variant, pass B variant) chosen by the autotuner."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().flame_tuning(ctypes.c_void_p(h), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def flame_fft_r2c(h, real_in, spec_out, stream=None):

@@ -215,3 +215,30 @@ def test_batch_equals_individual(fl, prec):
         assert torch.equal(ss[i], ref[i][0]), i
     for f in fs:
         f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("variants", ["0,0", "1,0", "0,1", "1,1"])
+@pytest.mark.parametrize("shape", [(256, 512), (1024, 2048), (4096, 8192)])
+def test_every_tuned_variant_matches_oracle(fl, orc, monkeypatch, variants, shape):
+    # the autotuner may pick either shape of passes A and B; each must be exact
+    monkeypatch.setenv("FLAME_FORCE_VARIANTS", variants)
+    n1, n2 = shape
+    f, st0, state, mean, t = _setup(fl, n1, n2, "fp32", 64, 11, amp=1e-2)
+    assert fl.flame_tuning(f.h) == tuple(int(v) for v in variants.split(","))
+    f.step(state, mean, t, 1)
+    ref, mref, tref = orc.step(_oparams(orc, f), st0, 0.0, f.params.t0, 1)
+    assert _box_err(_host(fl, state), ref, f.K1) < 2e-5
+    assert t.item() == tref
+    f.close()
+
+
+@pytest.mark.gpu
+def test_autotuner_choice_is_valid_and_cached(fl, monkeypatch):
+    monkeypatch.delenv("FLAME_FORCE_VARIANTS", raising=False)
+    f1 = fl.Flame(512, 1024, prec="fp32")
+    f2 = fl.Flame(512, 1024, prec="fp32")
+    v1, v2 = fl.flame_tuning(f1.h), fl.flame_tuning(f2.h)
+    assert v1 == v2 and all(v in (0, 1) for v in v1)
+    f1.close()
+    f2.close()
