@@ -55,7 +55,7 @@ class ClockSampler:
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, index):
         self.index = index
@@ -65,7 +65,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -81,24 +81,30 @@ class ClockSampler:
             self.lines = [l for l in out.splitlines() if l.strip()]
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        """Median SM clock over the samples taken with the GPU busy (>= 50 %
+        utilisation); the throttle reasons seen in those samples."""
+        sm, mx, reasons, total = [], None, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in getattr(self, "lines", []):
             parts = [p.strip() for p in l.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                clk, mxc, util = float(parts[0]), float(parts[1]), float(parts[7])
             except ValueError:
                 continue
+            total += 1
+            mx = mxc
+            if util < 50:
+                continue
+            sm.append(clk)
             for n, v in zip(names, parts[3:7]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples under load"], "samples": total}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples_under_load": len(sm), "samples": total}
 
 
 def cpu_oracle_step_time(w, nsteps=1):
@@ -143,6 +149,97 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def reduce_max(x, device="cpu"):
+    """Max of a per-rank float over all ranks (identity without a process
+    group); the device follows the backend (cuda for nccl, cpu for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank, steps, world, max_ms):
+    """Grid-point updates per second of all ranks together (replicas: every
+    rank steps its own flame), timed by the slowest rank."""
+    return points_per_rank * steps * world / (max_ms * 1e-3)
+
+
+def _ev_time(fn, stream, reps=1):
+    """Device time (ms) of fn() on `stream`, averaged over reps."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_batched(flame, inputs, nflames=256, steps=20, warmup=3):
+    """Ensemble of uneven FP32 flames (grids uniform over 256x512, 512x1024,
+    1024x2048, size seed 1234, spectrum seeds 1000+i): one graph of grouped
+    launches per call, against the same flames stepped one by one."""
+    import torch
+    grids = inputs.batch_grids(nflames)
+    fl, ss, ms, ts = [], [], [], []
+    for i, (n1, n2) in enumerate(grids):
+        f = flame.Flame(n1, n2, prec="fp32", gamma=0.8, t0=200.0, dt=1e-3)
+        st = inputs.spectrum_ic(n1, n2, inputs.batch_kmax(n1), 1000 + i, K1=f.K1, K2=f.K2)
+        fl.append(f)
+        ss.append(torch.from_numpy(flame.box_to_abi(st)).cuda().to(f.cdtype))
+        ms.append(torch.zeros(1, dtype=torch.float64, device="cuda"))
+        ts.append(torch.full((1,), 200.0, dtype=torch.float64, device="cuda"))
+    hs = [f.h for f in fl]
+    s = torch.cuda.current_stream()
+    flame.flame_step_batch(hs, ss, ms, ts, nsteps=steps)  # capture + warm-up
+    torch.cuda.synchronize()
+    t_batch = _ev_time(lambda: flame.flame_step_batch(hs, ss, ms, ts, nsteps=steps), s)
+    for f, st, m, t in zip(fl, ss, ms, ts):
+        f.step(st, m, t, steps)  # capture each flame's graph
+    torch.cuda.synchronize()
+    t_plain = _ev_time(lambda: [f.step(st, m, t, steps) for f, st, m, t in zip(fl, ss, ms, ts)], s)
+    for f in fl:
+        f.sync_status()
+    pts = sum(n1 * n2 for n1, n2 in grids) * steps
+    for f in fl:
+        f.close()
+    return {"workload": f"ensemble-{nflames}-uneven-fp32mixed", "steps": steps,
+            "value": pts / (t_batch * 1e-3), "unit": "points/s",
+            "plain_value": pts / (t_plain * 1e-3), "vs_plain": t_plain / t_batch,
+            "ms_per_step": t_batch / steps}
+
+
+def measure_adjoint(flame, inputs, nsteps=200, ckpt=20, reps=2):
+    """Gradient of the final area over nsteps FP32 steps on 512x1024 (|k| <= 64,
+    seed 7), checkpoints every ckpt steps, against plain forward stepping."""
+    import torch
+    n1, n2 = 512, 1024
+    f = flame.Flame(n1, n2, prec="fp32", gamma=0.8, t0=200.0, dt=1e-3)
+    st0 = torch.from_numpy(flame.box_to_abi(inputs.spectrum_ic(n1, n2, 64, 7, K1=f.K1, K2=f.K2))).cuda().to(f.cdtype)
+    m0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t0 = torch.full((1,), 200.0, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    sT, mT, tT = st0.clone(), m0.clone(), t0.clone()
+    f.step(sT, mT, tT, nsteps)
+    _, lam, lam0 = f.area(sT, mT, tT, grad=True)
+    f.adjoint(st0, m0, t0, nsteps, ckpt, lam, lam0)  # warm-up (allocates the checkpoint arena)
+    torch.cuda.synchronize()
+    t_adj = _ev_time(lambda: f.adjoint(st0, m0, t0, nsteps, ckpt, lam, lam0), s, reps)
+    x, m, t = st0.clone(), m0.clone(), t0.clone()
+    t_fwd = _ev_time(lambda: f.step(x, m, t, nsteps), s, reps)
+    f.sync_status()
+    f.close()
+    pts = n1 * n2 * nsteps
+    return {"workload": "adjoint-512x1024-200steps-ckpt20-fp32mixed", "value": pts / (t_adj * 1e-3),
+            "unit": "points/s", "plain_value": pts / (t_fwd * 1e-3), "vs_plain": t_fwd / t_adj,
+            "ms": t_adj, "note": "working set fits in L2"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -184,25 +281,27 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()  # > L2, outside the timed interval of the step
-            one_step(evs[k])
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
+    clk = ClockSampler(local)
+    clk.__enter__()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # > L2, outside the timed interval of the step
+        one_step(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    # keep the GPU busy with more steps of the same workload so the clock
+    # samples see it under load (not timed)
+    for k in range(max(200, args.steps)):
+        one_step()
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     f.sync_status()
     per_pass = [[evs[k][ps].elapsed_time(evs[k][ps + 1]) for k in range(args.steps)] for ps in range(3)]
     step_ms = [sum(per_pass[ps][k] for ps in range(3)) for k in range(args.steps)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = reduce_max(sum(step_ms), device="cuda")
     pts = n1 * n2
-    value = pts * args.steps * world / (total_ms * 1e-3)
+    value = whole_job_rate(pts, args.steps, world, total_ms)
     avg = [sum(v) / len(v) for v in per_pass]
     dom = max(range(3), key=lambda i: avg[i])
     peak, peak_kind = _peaks()
@@ -243,6 +342,12 @@ def run_ours(args):
         except Exception:
             traffic = None
 
+    batched = adjoint = None
+    if not args.no_extras:
+        batched = measure_batched(flame, inputs)
+        adjoint = measure_adjoint(flame, inputs)
+    clk.__exit__(None, None, None)
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -268,11 +373,59 @@ def run_ours(args):
             "clocks": clk.summary(),
             "wall_s": wall,
             "cpu_baseline": cpu,
+            "batched": batched,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     f.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_suite(args):
+    """Secondary configurations (one JSON line each): the FP64 128x256 and
+    FP32 1024x2048 trajectories' step rates and the 2-D real FFT pair sweep."""
+    import torch
+
+    from paper_0911_2889_gb300 import flame, inputs
+    s = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    peak, kind = _peaks()
+    for (n1, n2, prec, kmax, nsteps) in ((128, 256, "fp64", 16, 100), (1024, 2048, "fp32", 256, 1000)):
+        f = flame.Flame(n1, n2, prec=prec, gamma=0.8, t0=200.0, dt=1e-3)
+        st = torch.from_numpy(flame.box_to_abi(inputs.spectrum_ic(n1, n2, kmax, 0, K1=f.K1, K2=f.K2))).cuda().to(f.cdtype)
+        m = torch.zeros(1, dtype=torch.float64, device="cuda")
+        t = torch.full((1,), 200.0, dtype=torch.float64, device="cuda")
+        f.step(st, m, t, nsteps)  # capture the graphs
+        torch.cuda.synchronize()
+        ms = _ev_time(lambda: f.step(st, m, t, nsteps), s)
+        f.sync_status()
+        esz = 16 if prec == "fp64" else 8
+        gbs = sum(pass_bytes(n1, n2, f.K1, f.K2, esz)) / (ms * 1e-3 / nsteps) / 1e9
+        print(json.dumps({"suite": f"trajectory-{n1}x{n2}-{prec}", "steps": nsteps, "ms_per_step": ms / nsteps,
+                          "points_per_s": n1 * n2 * nsteps / (ms * 1e-3), "effective_gbs": gbs,
+                          "note": "graph-captured; L2-resident" if n1 * n2 <= 2 ** 21 else "graph-captured"}),
+              flush=True)
+        f.close()
+    sizes = [(256, 256), (256, 512), (512, 512), (512, 1024), (1024, 1024), (1024, 2048), (2048, 2048),
+             (2048, 4096), (4096, 4096), (4096, 8192)]
+    for prec in ("fp32", "fp64"):
+        for n1, n2 in sizes:
+            f = flame.Flame(n1, n2, prec=prec)
+            x = torch.from_numpy(inputs.real_field(n1, n2, 1)).cuda().to(f.rdtype)
+            X = f.fft_r2c(x)
+            y = f.fft_c2r(X)
+            reps, tot = 5, 0.0
+            for _ in range(reps):
+                flush.zero_()
+                tot += _ev_time(lambda: (f.fft_r2c(x, X), f.fft_c2r(X, y)), s)
+            ms = tot / reps
+            rsz = 4 if prec == "fp32" else 8
+            alg = 8 * rsz * n1 * n2  # 32 B/pt FP32, 64 B/pt FP64 (4 passes, each read + write)
+            gbs = alg / (ms * 1e-3) / 1e9
+            print(json.dumps({"suite": f"fft-pair-{n1}x{n2}-{prec}", "ms": ms, "alg_bytes": alg,
+                              "effective_gbs": gbs, "frac_of_hbm": gbs / peak, "peak_kind": kind}), flush=True)
+            f.close()
 
 
 def run_profile(args):
@@ -303,12 +456,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble and adjoint measurements")
+    ap.add_argument("--suite", action="store_true", help="print one line per secondary configuration and exit")
     ap.add_argument("--profile", type=int, default=0, help="run N plain steps for ncu and exit")
     ap.add_argument("--grid", type=int, nargs=2, default=None, help="grid for --profile")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="precision for --profile")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.suite:
+        run_suite(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -375,7 +375,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[32];
+    __shared__ double red[256];  // one per thread (blockDim <= 256)
     const StepArgs &a = d.a;
     const int N1 = 1 << a.logn1, T = N1 >> 4;
     const int G = blockDim.x / T, g = threadIdx.x / T, t = threadIdx.x % T;
@@ -428,12 +428,11 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(
             if (k2 == 0) lout[-k1] = C{nw.x, -nw.y};
         }
     }
-    for (int o = 16; o > 0; o >>= 1) dg += __shfl_xor_sync(0xffffffffu, dg, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dg;
+    red[threadIdx.x] = dg;  // any block size
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        for (int i = 0; i < (int)blockDim.x; ++i) s += red[i];
         if (s != 0.0) atomicAdd(d.dgamma, s);
     }
 }

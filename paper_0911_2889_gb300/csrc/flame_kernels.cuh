@@ -487,7 +487,7 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[32];
+    __shared__ double red[256];  // one per thread (blockDim <= 256)
     const StepArgs &a = d.a;
     const C *__restrict__ gk = static_cast<const C *>(d.gk);
     C *__restrict__ state = static_cast<C *>(d.state);
@@ -530,16 +530,15 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
         phi[i][0] = (in_box && va) ? sa[k1] : C{0, 0};
         phi[i][1] = (in_box && vb) ? sb[k1] : C{0, 0};
     }
-    if (tile == 0) {  // block-uniform: FP64 row-sum reduction of column 0
-        for (int o = 16; o > 0; o >>= 1) colsum += __shfl_xor_sync(0xffffffffu, colsum, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = colsum;
+    if (tile == 0) {  // block-uniform: FP64 row-sum reduction of column 0 (any block size)
+        red[threadIdx.x] = colsum;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            for (int w = 0; w < (int)blockDim.x; ++w) s += red[w];
             red[0] = s;
         }
-        // red[0] is read after the transform's barriers
+        // red[0] is read by thread 0 after the transform's barriers
     }
     fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
 

@@ -16,11 +16,27 @@ template <class R> static size_t group_smem(int logn) {
     return 2 * (size_t)plane_len(1 << logn) * sizeof(typename VecOf<R>::type);
 }
 
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 148;
+    }
+    return n;
+}
+
+// G line groups of T = 2^logn / 16 threads per CTA: up to 256 threads and
+// the shared-memory budget, but no more groups than keep at least two CTAs
+// per SM busy (small grids spread over the whole GPU).  hint > 0 fixes G.
 template <class R> static Geom make_geom(int logn, int nlines, int hint, size_t extra = 0) {
     const int T = (1 << logn) >> 4;
     int G = hint > 0 ? hint : (T >= kThreadsTarget ? 1 : kThreadsTarget / T);
     const size_t per = group_smem<R>(logn) + extra;
     while (G > 1 && (G * per > kSmemBudget || G * T > kMaxThreads)) G >>= 1;
+    if (hint <= 0)
+        while (G > 1 && (nlines + G - 1) / G < 2 * sm_count()) G >>= 1;
+
     Geom g;
     g.threads = G * T;
     g.blocks = (nlines + G - 1) / G;
@@ -31,13 +47,7 @@ template <class R> static Geom make_geom(int logn, int nlines, int hint, size_t 
 // CTAs of one kernel resident at once on the current device: a tile that
 // starts now is followed, one wave later, by tile + resident_ctas.
 static int resident_ctas(const void *kernel, const Geom &g) {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return 0;
-    }
+    const int nsm = sm_count();
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, g.threads, g.smem) != cudaSuccess) {
         cudaGetLastError();
@@ -175,12 +185,14 @@ template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s,
     with_log<R>(d.a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
-        if (cl > 1 && variant == kVariantDirect) {  // same kernel shape without the cluster write-out
+        if (cl > 1 && variant == kVariantDirect) {  // runtime-length kernel, direct stores
             const int pf = resident_ctas((const void *)k_passA<R, 0>, g);
             err = launch_cl(k_passA<R, 0>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
         } else {
-            const int pf = resident_ctas((const void *)k_passA<R, L>, g);
-            err = launch_cl(k_passA<R, L>, dim3(round_up(g.blocks, cl)), g.threads, g.smem, s, cl, d, pf);
+            // the compile-time kernels assume Shape<L>::G groups per CTA
+            const Geom gl = cl > 1 ? geom_cols(d.a.logn1, d.a.K2 + 1, Shape<L>::G) : g;
+            const int pf = resident_ctas((const void *)k_passA<R, L>, gl);
+            err = launch_cl(k_passA<R, L>, dim3(round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
         }
     });
     if (err != cudaSuccess) return err;
@@ -236,10 +248,12 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
     with_log<R>(a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
-        if (cl > 1 && variant == kVariantDirect)
+        if (cl > 1 && variant == kVariantDirect) {
             err = launch_cl(k_passA_n<R, 0>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
-        else
-            err = launch_cl(k_passA_n<R, L>, dim3(round_up(g.blocks, cl), n), g.threads, g.smem, s, cl, ds, 0);
+        } else {
+            const Geom gl = cl > 1 ? geom_cols(a.logn1, a.K2 + 1, Shape<L>::G) : g;
+            err = launch_cl(k_passA_n<R, L>, dim3(round_up(gl.blocks, cl), n), gl.threads, gl.smem, s, cl, ds, 0);
+        }
     });
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
