@@ -102,8 +102,9 @@ flame_status flame_get_params(flame_t h, flame_params *out);
 /* Kernel variants the autotuner chose for this handle (FP32 grids with
  * N1, N2/2 in 256..4096 are timed once per grid, precision and device at
  * creation, FLAME_AUTOTUNE=0 disables it): pass A 0 = cluster write-out
- * through distributed shared memory, 1 = direct stores; pass B 0 = 16 points
- * per thread, 1 = 8 points per thread.  EINVAL on null pointers. */
+ * through distributed shared memory, 1 = direct stores, 2 = 8 points per
+ * thread with the cluster write-out; pass B 0 = 16 points per thread, 1 = 8
+ * points per thread.  EINVAL on null pointers. */
 flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant);
 
 /* Number of complex entries of the compact box, (2 K1 + 1) * (K2 + 1). */

@@ -64,7 +64,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaA
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int n = t + r * T;
-            st_uv<R>(uv + 2 * ((size_t)n * a.ldk + k2), lane0<R>(x[r]), lane1<R>(x[r]));
+            st_uv<R>(uv + uv_index(n, k2, a.ldk), lane0<R>(x[r]), lane1<R>(x[r]));
         }
     }
 }
@@ -144,13 +144,13 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB
     V *base = reinterpret_cast<V *>(smraw);
     C *park = reinterpret_cast<C *>(base + 2 * plane_len(M));  // M entries
     const C *P = twm + tw_real_offset(a.logm);
-    const C *src = uv + 2 * (size_t)(valid ? row : 0) * a.ldk;
+    const C *src = uv + uv_index(valid ? row : 0, 0, a.ldk);  // element kk at src + 4 kk
     const R s2 = (R)a.s2;
     // phi at 2m, 2m+1 (real parts of the two lanes), parked
     CV<V> x[16];
     halfband_ifft<R>(x, a, t, P, twm,
                      [&](int kk, bool pos) {
-                         UV<R> e = ld_uv<R>(src + 2 * kk);
+                         UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
                          return pos ? e.v : C{e.v.x, -e.v.y};
                      },
                      valid, base);
@@ -159,7 +159,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB
     // u + iv at 2m, 2m+1
     halfband_ifft<R>(x, a, t, P, twm,
                      [&](int kk, bool pos) {
-                         UV<R> e = ld_uv<R>(src + 2 * kk);
+                         UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
                          const R f = s2 * (R)kk;
                          C Vv{-f * e.v.y, f * e.v.x};  // i s2 k2 P
                          if (pos) return C{e.u.x - Vv.y, e.u.y + Vv.x};
@@ -331,7 +331,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(
     V *base = reinterpret_cast<V *>(smraw);
     C *park = reinterpret_cast<C *>(base + 2 * plane_len(M));
     const C *P = twm + tw_real_offset(a.logm);
-    const C *src = uv + 2 * (size_t)(valid ? row : 0) * a.ldk;
+    const C *src = uv + uv_index(valid ? row : 0, 0, a.ldk);  // element kk at src + 4 kk
     const C *lsrc = lrow + (size_t)(valid ? row : 0) * a.ldk;
     CV<V> x[16];
     halfband_ifft<R>(x, a, t, P, twm,
@@ -344,7 +344,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(
     for (int r = 0; r < 16; ++r) park[t + r * T] = C{x[r].re.x, x[r].re.y};  // ell(2m), ell(2m+1)
     halfband_ifft<R>(x, a, t, P, twm,
                      [&](int kk, bool pos) {
-                         UV<R> e = ld_uv<R>(src + 2 * kk);
+                         UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
                          if (pos) return C{e.u.x - e.v.y, e.u.y + e.v.x};
                          return C{e.u.x + e.v.y, e.v.x - e.u.y};
                      },

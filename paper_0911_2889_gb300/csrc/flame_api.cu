@@ -171,7 +171,7 @@ flame_status autotune(flame_ctx *h) {
     if (force) {
         int va = 0, vb = 0;
         if (sscanf(force, "%d,%d", &va, &vb) == 2) {
-            h->var_a = va ? flame::kVariantDirect : flame::kVariantDefault;
+            h->var_a = va == 2 ? flame::kVariantRadix8A : va ? flame::kVariantDirect : flame::kVariantDefault;
             h->var_b = vb ? flame::kVariantRadix8 : flame::kVariantDefault;
             return FLAME_OK;
         }
@@ -227,15 +227,27 @@ flame_status autotune(flame_ctx *h) {
         *ms = total / 3.f;
         return r;
     };
-    float a0 = 0, a1 = 0, b0 = 0, b1 = 0;
-    if (e == cudaSuccess) e = time_it(0, flame::kVariantDefault, &a0);
-    if (e == cudaSuccess) e = time_it(0, flame::kVariantDirect, &a1);
-    if (e == cudaSuccess) e = time_it(1, flame::kVariantDefault, &b0);
-    if (e == cudaSuccess) e = time_it(1, flame::kVariantRadix8, &b1);
+    const int avars[3] = {flame::kVariantDefault, flame::kVariantDirect, flame::kVariantRadix8A};
+    const int bvars[2] = {flame::kVariantDefault, flame::kVariantRadix8};
+    float best_a = 1e30f, best_b = 1e30f;
+    for (int v : avars) {
+        float ms = 0;
+        if (e == cudaSuccess) e = time_it(0, v, &ms);
+        if (e == cudaSuccess && ms < best_a) {
+            best_a = ms;
+            h->var_a = v;
+        }
+    }
+    for (int v : bvars) {
+        float ms = 0;
+        if (e == cudaSuccess) e = time_it(1, v, &ms);
+        if (e == cudaSuccess && ms < best_b) {
+            best_b = ms;
+            h->var_b = v;
+        }
+    }
     cleanup();
     if (e != cudaSuccess) return fail(FLAME_ECUDA, "autotune: %s", cudaGetErrorString(e));
-    h->var_a = a1 < a0 ? flame::kVariantDirect : flame::kVariantDefault;
-    h->var_b = b1 < b0 ? flame::kVariantRadix8 : flame::kVariantDefault;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = {h->var_a, h->var_b};
     return FLAME_OK;
@@ -356,7 +368,7 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
     const size_t n1 = p.n_theta, ldk = a.ldk, m1 = p.n_phi / 2 + 1;
     bool ok = dev_alloc(&h->tw1, flame::tw_alloc_len(h->logn1) * h->csz) &&
               dev_alloc(&h->twm, flame::tw_alloc_len(h->logm) * h->csz) &&
-              dev_alloc(&h->uv, n1 * ldk * 2 * h->csz) && dev_alloc(&h->gk, n1 * ldk * h->csz) &&
+              dev_alloc(&h->uv, n1 * ldk * 2 * h->csz) && dev_alloc(&h->gk, n1 * ((ldk + 1) & ~(size_t)1) * h->csz) &&
               dev_alloc(&h->spec, n1 * m1 * h->csz) && dev_alloc(&h->aw, n1 * ldk * 2 * h->csz) &&
               dev_alloc((void **)&h->rowsum, n1 * sizeof(double)) && dev_alloc((void **)&h->dscal, 4 * sizeof(double)) &&
               dev_alloc((void **)&h->status, sizeof(int));
@@ -485,9 +497,11 @@ flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const FlameDesc d = make_desc(h, state, mean_mode, t);
     if (h->p.prec == FLAME_FP64)
-        CUDA_TRY(pass == 0 ? Ops<double>::passA(d, s) : pass == 1 ? Ops<double>::passB(d, s) : Ops<double>::passC(d, s));
+        CUDA_TRY(pass == 0 ? Ops<double>::passA(d, s, h->var_a)
+                 : pass == 1 ? Ops<double>::passB(d, s, h->var_b) : Ops<double>::passC(d, s));
     else
-        CUDA_TRY(pass == 0 ? Ops<float>::passA(d, s) : pass == 1 ? Ops<float>::passB(d, s) : Ops<float>::passC(d, s));
+        CUDA_TRY(pass == 0 ? Ops<float>::passA(d, s, h->var_a)
+                 : pass == 1 ? Ops<float>::passB(d, s, h->var_b) : Ops<float>::passC(d, s));
     return FLAME_OK;
 }
 

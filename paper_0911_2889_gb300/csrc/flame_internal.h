@@ -14,8 +14,9 @@ constexpr int kStatusTimeout = 1;
 
 // Kernel variants chosen by the autotuner (0 = default shape).
 constexpr int kVariantDefault = 0;
-constexpr int kVariantDirect = 1;   // pass A: direct scattered stores (no cluster write-out)
+constexpr int kVariantDirect = 1;   // pass A: direct stores (no cluster write-out)
 constexpr int kVariantRadix8 = 1;   // pass B: 8 points per thread, 512-thread CTAs
+constexpr int kVariantRadix8A = 2;  // pass A: 8 points per thread, cluster write-out
 
 // Plain-old-data arguments of the step kernels.
 struct StepArgs {

@@ -34,6 +34,22 @@ template <class R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
 // Element of the interleaved (U, V) workspace: two complex numbers.
 template <class R> struct UV { CplxT<R> u, v; };
 
+// Index (in complex units) of element (j1, k2) of the gk workspace: column
+// pairs interleaved, ((k2/2) N1 + j1) * 2 + k2 % 2, so that a column pair is
+// one contiguous block read 16 bytes per row (pass C) and the two rows of a
+// row pair at two adjacent k2 fill one 32-byte sector (pass B).
+__host__ __device__ __forceinline__ size_t gk_index(int j1, int k2, int n1) {
+    return (((size_t)(k2 >> 1) * n1 + j1) << 1) + (k2 & 1);
+}
+
+// Index (in complex units) of element (j1, k2) of the uv workspace: row pairs
+// are interleaved, ((j1/2) ldk + k2) * 2 + j1 % 2 pairs of (U, V), so that a
+// row pair is one contiguous block (pass B) and a column's row pair is one
+// 32-byte sector (pass A).
+__host__ __device__ __forceinline__ size_t uv_index(int j1, int k2, int ldk) {
+    return 2 * ((((size_t)(j1 >> 1) * ldk + k2) << 1) + (j1 & 1));
+}
+
 template <class R> __device__ __forceinline__ UV<R> ld_uv(const CplxT<R> *p) {
     if constexpr (std::is_same<R, float>::value) {
         float4 q = __ldg(reinterpret_cast<const float4 *>(p));
@@ -253,12 +269,34 @@ template <> struct Shape<0> {
     static constexpr int T = 0, G = 0, CL = 1;
 };
 
+// E points per thread: 16 (runtime-length kernels, FP64) or 8 (compile-time
+// FP32 kernels: 512-thread CTAs at 64 registers, two CTAs per SM).
+template <int DIR, int LOG, int E, class V, class C>
+__device__ __forceinline__ void fft_line_e(CV<V> (&x)[E], int logn, int t, const Planes<V> &sm, const C *tw) {
+    if constexpr (E == 8) line_fft_ct<DIR, LOG, 8>(x, t, sm, tw + tw_table_len(LOG, 4), CtaBarrier{});
+    else fft_line<DIR, LOG>(x, logn, t, sm, tw);
+}
+
+// CTA shape of the compile-time kernels with E points per thread: G line
+// groups of T = 2^LOG / E threads (256 threads for E = 16, 512 for E = 8) and
+// clusters of CL CTAs holding 8 line groups (pass A's write-out).
+template <int LOG, int E> struct ShapeE {
+    static constexpr int T = (1 << LOG) / E;
+    static constexpr int THREADS = E == 16 ? 256 : 512;
+    static constexpr int G = T >= THREADS ? 1 : THREADS / T;
+    static constexpr int CL = (G <= 8) ? 8 / G : 1;
+};
+template <int E> struct ShapeE<0, E> {  // runtime-length kernels: no clusters
+    static constexpr int T = 0, THREADS = 256, G = 0, CL = 1;
+};
+
 // Memory layouts (see include/flame.h and the design doc):
 //   state  column-major compact box: element (k1, k2) at k2 * ld1 + (k1 + K1),
 //          ld1 = 2 K1 + 1
-//   uv     row-major N1 x (K2+1) pairs (U, V): element (j1, k2) at
-//          2 * (j1 * ldk + k2), ldk = K2 + 1
-//   gk     column-major N1 x (K2+1): element (j1, k2) at k2 * N1 + j1
+//   uv     N1 x (K2+1) pairs (U, V), row pairs interleaved: element (j1, k2)
+//          at uv_index(j1, k2, ldk) = 2 (((j1/2) ldk + k2) 2 + j1 % 2), ldk = K2 + 1
+//   gk     N1 x (K2+1), column pairs interleaved: element (j1, k2) at
+//          gk_index(j1, k2, N1) = ((k2/2) N1 + j1) 2 + k2 % 2
 // Every pass reads whole contiguous blocks (state columns, uv rows, gk
 // columns); the transposition between the column and row passes is done by
 // the scattered stores of passes A and B.
@@ -269,7 +307,8 @@ template <> struct Shape<0> {
 // r = 4..11 of the first pass are always zero and are dropped at compile
 // time).  Writes uv[j1][k2] = (U, V) with U = synthesis of a, V = i s2 k2 x
 // synthesis of b.
-template <class R, int LOG> __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+template <class R, int LOG, int E, bool CLU = true>
+__device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -277,7 +316,7 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
     const C *__restrict__ state = static_cast<const C *>(d.state);
     C *__restrict__ uv = static_cast<C *>(d.uv);
     const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
-    const int N1 = LOG > 0 ? (1 << LOG) : (1 << a.logn1), T = N1 >> 4;
+    const int N1 = LOG > 0 ? (1 << LOG) : (1 << a.logn1), T = N1 / E;
     const int G = blockDim.x / T, g = threadIdx.x / T, t = threadIdx.x % T;
     const int ld1 = 2 * a.K1 + 1;
     if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
@@ -286,18 +325,20 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
     }
     const int k2 = tile * G + g;
     const bool valid = k2 <= a.K2;
-    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len_e<E>(N1);
     auto sm = make_planes(base, N1);
     const R s1 = (R)a.s1, s2k2 = (R)(a.s2 * k2);
     const C *col = state + (size_t)k2 * ld1 + a.K1;  // col[k1], k1 = -K1..K1
-    CV<V> x[16];
+    // band rows: r < E/4 (k1 = n <= K1) and r >= 3E/4 (k1 = n - N1 >= -K1);
+    // the middle half of the registers is zero padding, dropped at compile time
+    CV<V> x[E];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < E; ++r) {
         x[r] = CV<V>{vzero(V{}), vzero(V{})};
-        if (r < 4 || r >= 12) {
+        if (r < E / 4 || r >= 3 * E / 4) {
             const int n = t + r * T;
-            const int k1 = (r < 4) ? n : n - N1;
-            const bool in_box = valid && ((r < 4) ? (n <= a.K1) : (k1 >= -a.K1));
+            const int k1 = (r < E / 4) ? n : n - N1;
+            const bool in_box = valid && ((r < E / 4) ? (n <= a.K1) : (k1 >= -a.K1));
             if (in_box) {
                 C phi = __ldg(col + k1);
                 if (k1 == 0 && k2 == 0) phi = C{0, 0};
@@ -307,8 +348,8 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
             }
         }
     }
-    fft_line<1, LOG>(x, a.logn1, t, sm, tw1);
-    constexpr int CL = Shape<LOG>::CL;
+    fft_line_e<1, LOG, E>(x, a.logn1, t, sm, tw1);
+    constexpr int CL = CLU ? ShapeE<LOG, E>::CL : 1;
     if constexpr (CL > 1 && std::is_same<R, float>::value) {
         // Park (U, V) of this column at its natural row index, then the CL
         // CTAs of the cluster (CL G adjacent columns) write rows: CTA q takes
@@ -316,11 +357,12 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
         // of one row (CL G x 16 bytes = 128 contiguous bytes per row).
         namespace cg = cooperative_groups;
         cg::cluster_group cluster = cg::this_cluster();
-        constexpr int GG = Shape<LOG>::G, NC = CL * GG, NN = 1 << LOG, ROWS = NN / CL;
+        constexpr int GG = ShapeE<LOG, E>::G, NC = CL * GG, NN = 1 << LOG, ROWS = NN / CL;
+        constexpr int NT = ShapeE<LOG, E>::THREADS;
         float4 *park = reinterpret_cast<float4 *>(base);
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
+        for (int r = 0; r < E; ++r) {
             const int n = t + r * T;
             C U = lane0<R>(x[r]);
             C Vb = lane1<R>(x[r]);
@@ -329,27 +371,30 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
         cluster.sync();
         const int q = (int)cluster.block_rank();
         const int col0 = (tile / CL) * NC;
-        static_assert((ROWS * NC) % 256 == 0, "256 threads per CTA");
+        static_assert((ROWS * NC) % NT == 0, "threads per CTA");
+        // element e: row parity e % 2, column (e / 2) % NC, row pair e / (2 NC);
+        // consecutive threads cover one row pair's NC columns x 2 rows
+        // (NC x 32 contiguous bytes of the interleaved uv)
 #pragma unroll
-        for (int i = 0; i < ROWS * NC / 256; ++i) {
-            const int e = (int)threadIdx.x + 256 * i;
-            const int c = e % NC, n = q * ROWS + e / NC;
+        for (int i = 0; i < ROWS * NC / NT; ++i) {
+            const int e = (int)threadIdx.x + NT * i;
+            const int c = (e >> 1) % NC, n = q * ROWS + 2 * (e / (2 * NC)) + (e & 1);
             const int kc = col0 + c;
             const float4 *rb = cluster.map_shared_rank(
-                reinterpret_cast<const float4 *>(reinterpret_cast<V *>(smraw) + (size_t)(c % GG) * 2 * plane_len(NN)),
+                reinterpret_cast<const float4 *>(reinterpret_cast<V *>(smraw) + (size_t)(c % GG) * 2 * plane_len_e<E>(NN)),
                 c / GG);
             const float4 v = rb[spad(n)];
-            if (kc <= a.K2) *reinterpret_cast<float4 *>(uv + 2 * ((size_t)n * a.ldk + kc)) = v;
+            if (kc <= a.K2) *reinterpret_cast<float4 *>(uv + uv_index(n, kc, a.ldk)) = v;
         }
         cluster.sync();
     } else if (valid) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
+        for (int r = 0; r < E; ++r) {
             const int n = t + r * T;
             C U = lane0<R>(x[r]);
             C Vb = lane1<R>(x[r]);
             C Vv{-s2k2 * Vb.y, s2k2 * Vb.x};  // i s2 k2 (synthesis of Phi)
-            st_uv<R>(uv + 2 * ((size_t)n * a.ldk + k2), U, Vv);
+            st_uv<R>(uv + uv_index(n, k2, a.ldk), U, Vv);
         }
     }
 }
@@ -361,14 +406,6 @@ template <class R, int LOG> __device__ __forceinline__ void passA_body(const Fla
 // u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
 // forward with the real-input post-processing; G[k], k <= K2, is written
 // (column-major gk).  G[j1][0] is the row sum of g used for the FP64 mean mode.
-// E points per thread: 16 (runtime-length kernels, FP64) or 8 (compile-time
-// FP32 kernels: 512-thread CTAs at 64 registers, two CTAs per SM).
-template <int DIR, int LOG, int E, class V, class C>
-__device__ __forceinline__ void fft_line_e(CV<V> (&x)[E], int logn, int t, const Planes<V> &sm, const C *tw) {
-    if constexpr (E == 8) line_fft_ct<DIR, LOG, 8>(x, t, sm, tw + tw_table_len(LOG, 4), CtaBarrier{});
-    else fft_line<DIR, LOG>(x, logn, t, sm, tw);
-}
-
 template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
@@ -398,7 +435,7 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
     C *h_first = reinterpret_cast<C *>(base + 2 * plane_len_e<E>(M));
     auto row_ifft = [&](int q, CV<V>(&x)[E]) {
         const int row = 2 * pair + q;
-        const C *src = uv + 2 * (size_t)row * a.ldk;
+        const C *src = uv + uv_index(row, 0, a.ldk);  // element kk at src + 4 kk
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int n = t + r * T;
@@ -406,7 +443,7 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
             const int kk = (r < E / 2) ? n : M - n;
             C z{0, 0};
             if (valid && kk <= a.K2) {
-                UV<R> e = ld_uv<R>(src + 2 * kk);
+                UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
                 if (r < E / 2) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
                 else z = C{e.u.x + e.v.y, e.v.x - e.u.y};         // conj U + i conj V
             }
@@ -446,13 +483,9 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
             CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
             C w = __ldg(P + k);
             CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
-            C *dst = gk + (size_t)k * a.n1 + 2 * pair;  // rows 2p, 2p+1 adjacent
-            if constexpr (std::is_same<R, float>::value) {
-                *reinterpret_cast<float4 *>(dst) = make_float4(Y.re.x, Y.im.x, Y.re.y, Y.im.y);
-            } else {
-                dst[0] = lane0<R>(Y);
-                dst[1] = lane1<R>(Y);
-            }
+            C *dst = gk + gk_index(2 * pair, k, a.n1);  // row 2p+1 two slots further
+            dst[0] = lane0<R>(Y);
+            dst[2] = lane1<R>(Y);
         }
     }
 }
@@ -506,14 +539,21 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
     const bool va = c0 <= a.K2, vb = c0 + 1 <= a.K2;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
     auto sm = make_planes(base, N1);
-    const C *ga = gk + (size_t)c0 * N1, *gb = ga + N1;
+    const C *gp = gk + gk_index(0, c0, N1);  // row n: columns c0, c0+1 at gp[2n], gp[2n+1]
     CV<V> x[16];
     double colsum = 0.0;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int n = t + r * T;
-        C p = va ? __ldg(ga + n) : C{0, 0};
-        C q = vb ? __ldg(gb + n) : C{0, 0};
+        C p, q;
+        if constexpr (std::is_same<R, float>::value) {
+            const float4 pq = va ? __ldg(reinterpret_cast<const float4 *>(gp) + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+            p = C{pq.x, pq.y};
+            q = vb ? C{pq.z, pq.w} : C{0, 0};
+        } else {
+            p = va ? __ldg(gp + 2 * n) : C{0, 0};
+            q = vb ? __ldg(gp + 2 * n + 1) : C{0, 0};
+        }
         if (c0 == 0) colsum += (double)p.x;
         x[r] = pack2<R>(p, q);
     }
@@ -588,7 +628,15 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
 // equal-size flames (descriptor array, flame = blockIdx.y).  LOG > 0: line
 // length 2^LOG fixed at compile time; LOG = 0: any length.
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA(FlameDesc d, int pf) {
-    passA_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
+    passA_body<R, LOG, 16>(d, blockIdx.x, gridDim.x, pf);
+}
+// compile-time length, direct (scattered) stores instead of the cluster write-out
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAd(FlameDesc d, int pf) {
+    passA_body<R, LOG, 16, false>(d, blockIdx.x, gridDim.x, pf);
+}
+// 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
+template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(FlameDesc d, int pf) {
+    passA_body<R, LOG, 8>(d, blockIdx.x, gridDim.x, pf);
 }
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d, int pf) {
     passB_body<R, LOG, 16>(d, blockIdx.x, gridDim.x, pf);
@@ -602,7 +650,15 @@ template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds, int pf) {
-    passA_body<R, LOG>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+    passA_body<R, LOG, 16>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAd_n(const FlameDesc *__restrict__ ds, int pf) {
+    passA_body<R, LOG, 16, false>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG>
+__global__ void __launch_bounds__(512, 2) k_passA8_n(const FlameDesc *__restrict__ ds, int pf) {
+    passA_body<R, LOG, 8>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds, int pf) {

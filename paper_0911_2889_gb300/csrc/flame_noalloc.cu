@@ -156,7 +156,8 @@ flame_status flame_step_noalloc(const flame_params *params, void *state, double 
     const size_t off_twm = off_tw1 + align256(flame::tw_alloc_len(a.logn1) * csz);
     const size_t off_uv = off_twm + align256(flame::tw_alloc_len(a.logm) * csz);
     const size_t off_gk = off_uv + align256((size_t)a.n1 * a.ldk * 2 * csz);
-    const size_t off_sc = off_gk + align256((size_t)a.n1 * a.ldk * csz);
+    // gk holds column pairs: an even number of columns
+    const size_t off_sc = off_gk + align256((size_t)a.n1 * ((a.ldk + 1) & ~1) * csz);
     const size_t need = off_sc + 256;
     if (need > kNoAllocScratchBytes)
         return nfail(FLAME_EUNSUPPORTED,

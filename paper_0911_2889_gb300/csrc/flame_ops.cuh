@@ -137,6 +137,10 @@ template <class R> cudaError_t Ops<R>::prepare() {
         set((const void *)k_passB_n<R, L>);
         set((const void *)k_passB8<R, L>);
         set((const void *)k_passB8_n<R, L>);
+        set((const void *)k_passA8<R, L>);
+        set((const void *)k_passA8_n<R, L>);
+        set((const void *)k_passAd<R, L>);
+        set((const void *)k_passAd_n<R, L>);
         set((const void *)k_passC_n<R, L>);
     });
     set((const void *)k_areaA<R>);
@@ -179,15 +183,34 @@ cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int d
     return cudaGetLastError();
 }
 
+// pass A with 8 points per thread (compile-time length 2^L): fixed shape
+template <class R, int L> static Geom geom_passA8(int ncols) {
+    Geom g;
+    if constexpr (L > 0) {
+        g.threads = ShapeE<L, 8>::THREADS;
+        g.blocks = (ncols + ShapeE<L, 8>::G - 1) / ShapeE<L, 8>::G;
+        g.smem = (size_t)ShapeE<L, 8>::G * 2 * plane_len_e<8>(1 << L) * sizeof(typename VecOf<R>::type);
+    } else {
+        g.threads = g.blocks = 0;
+        g.smem = 0;
+    }
+    return g;
+}
+
 template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant) {
     Geom g = geom_cols(d.a.logn1, d.a.K2 + 1, 0);
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
-        if (cl > 1 && variant == kVariantDirect) {  // runtime-length kernel, direct stores
-            const int pf = resident_ctas((const void *)k_passA<R, 0>, g);
-            err = launch_cl(k_passA<R, 0>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+        if (cl > 1 && variant == kVariantDirect) {  // compile-time length, direct stores
+            const int pf = resident_ctas((const void *)k_passAd<R, L>, g);
+            err = launch_cl(k_passAd<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+        } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
+            const Geom g8 = geom_passA8<R, L>(d.a.K2 + 1);
+            constexpr int cl8 = ShapeE<L, 8>::CL;
+            const int pf = resident_ctas((const void *)k_passA8<R, L>, g8);
+            err = launch_cl(k_passA8<R, L>, dim3(round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
         } else {
             // the compile-time kernels assume Shape<L>::G groups per CTA
             const Geom gl = cl > 1 ? geom_cols(d.a.logn1, d.a.K2 + 1, Shape<L>::G) : g;
@@ -249,7 +272,11 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
         if (cl > 1 && variant == kVariantDirect) {
-            err = launch_cl(k_passA_n<R, 0>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+            err = launch_cl(k_passAd_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
+            const Geom g8 = geom_passA8<R, L>(a.K2 + 1);
+            constexpr int cl8 = ShapeE<L, 8>::CL;
+            err = launch_cl(k_passA8_n<R, L>, dim3(round_up(g8.blocks, cl8), n), g8.threads, g8.smem, s, cl8, ds, 0);
         } else {
             const Geom gl = cl > 1 ? geom_cols(a.logn1, a.K2 + 1, Shape<L>::G) : g;
             err = launch_cl(k_passA_n<R, L>, dim3(round_up(gl.blocks, cl), n), gl.threads, gl.smem, s, cl, ds, 0);
