@@ -332,6 +332,46 @@ __device__ __forceinline__ void line_fft(CV<V> (&x)[16], int logN, int t, const 
     }
 }
 
+// Twiddle sources of the compile-time transform.  TwGlobal reads the
+// per-length table; TwShared reads a factorised copy in shared memory: the
+// pass-1 section (w_256^(r m), 15 x 16 entries) and the first 16 entries of
+// each pass-2 row (w_4096^(r m), m < 16), so that for m = m_lo + 16 m_hi
+//   w_4096^(r m) = w_4096^(r m_lo) * w_256^(r m_hi),
+// 480 entries (3.75 KB in FP32) instead of 4080.
+template <class C> struct TwGlobal {
+    const C *tw;
+    template <int S, int LE>
+    __device__ __forceinline__ C get(int r, int m) const {
+        constexpr int Ns = 1 << (LE * S);
+        return __ldg(tw + tw_pass_offset(S, LE) + (r - 1) * Ns + m);
+    }
+};
+template <class C> struct TwShared {
+    const C *t1;   // [15][16]: w_256^(r m)
+    const C *t2;   // [15][16]: w_4096^(r m), m < 16
+    template <int S, int LE>
+    __device__ __forceinline__ C get(int r, int m) const {
+        static_assert(LE == 4 && S <= 2, "radix-16 passes 1 and 2 only");
+        if constexpr (S == 1) return t1[(r - 1) * 16 + m];
+        else {
+            const C a = t2[(r - 1) * 16 + (m & 15)], b = t1[(r - 1) * 16 + (m >> 4)];
+            return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+        }
+    }
+    // copies the factor tables of the radix-16 global table of a line of
+    // length 2^LOG into smem: pass 1 always (LOG >= 8), pass 2 when it
+    // exists (LOG >= 12); the caller synchronises before use
+    template <int LOG> __device__ __forceinline__ static void fill(C *dst, const C *tw) {
+        static_assert(LOG >= 8, "pass 1 needs N >= 256");
+        constexpr int n = LOG >= 12 ? 480 : 240;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int h = i / 240, j = i % 240, r = j / 16, m = j % 16;
+            dst[i] = h == 0 ? __ldg(tw + tw_pass_offset(1, 4) + r * 16 + m)
+                            : __ldg(tw + tw_pass_offset(2, 4) + r * 256 + m);
+        }
+    }
+};
+
 // Same transform with the length known at compile time (LOGN) and E points
 // per thread (radix-E passes, E = 16 or 8; T = N/E threads per line): pass
 // strides, twiddle-table offsets and padded exchange addresses fold into
@@ -340,9 +380,9 @@ __device__ __forceinline__ void line_fft(CV<V> (&x)[16], int logN, int t, const 
 //   store of pass s:  spad(idxD + r Ns) = spad(idxD) + r (Ns == 1 ? 1 : Ns + Ns/E)
 //   load:             spad(t + r T)     = spad(t) + r (T + T/E)      (T >= E)
 // `tw` is the radix-E table of this length.
-template <int DIR, int LOGN, int E, class V, class C, class Bar>
+template <int DIR, int LOGN, int E, class V, class C, class Bar, class TW = TwGlobal<C>>
 __device__ __forceinline__ void line_fft_ct(CV<V> (&x)[E], int t, const Planes<V> &sm,
-                                            const C *__restrict__ tw, Bar bar) {
+                                            const C *__restrict__ tw, Bar bar, TW twp = TW{nullptr}) {
     using Real = decltype(C::x);
     constexpr int LE = E == 16 ? 4 : 3;
     constexpr int N = 1 << LOGN, T = N / E, P = LOGN / LE, LR = LOGN % LE;
@@ -350,12 +390,13 @@ __device__ __forceinline__ void line_fft_ct(CV<V> (&x)[E], int t, const Planes<V
         constexpr int s = decltype(sc)::value;
         constexpr int Ns = 1 << (LE * s);
         if constexpr (s > 0) {
-            const C *tp = tw + tw_pass_offset(s, LE) + (t & (Ns - 1));
+            const int m = t & (Ns - 1);
+            TW src = twp;
+            if constexpr (std::is_same<TW, TwGlobal<C>>::value) src.tw = tw;
 #pragma unroll
             for (int r = 1; r < E; ++r) {
-                Real wr, wi;
-                load_tw<DIR>(tp, (r - 1) * Ns, wr, wi);
-                x[r] = cmul_s(x[r], wr, wi);
+                const C w = src.template get<s, LE>(r, m);
+                x[r] = cmul_s(x[r], w.x, DIR > 0 ? w.y : -w.y);
             }
         }
         dft<E, DIR>(x);
@@ -407,6 +448,15 @@ __device__ __forceinline__ void fft_line(CV<V> (&x)[16], int logn, int t, const 
                                          const C *__restrict__ tw) {
     if constexpr (LOG > 0) line_fft_ct<DIR, LOG, 16>(x, t, sm, tw, CtaBarrier{});
     else line_fft<DIR>(x, logn, t, sm, tw, CtaBarrier{});
+}
+// Compile-time length (8 <= LOG <= 12) with the radix-16 pass twiddles taken
+// from the shared-memory factors `stw` (see TwShared); the final-pass
+// twiddles still come from `tw`.
+template <int DIR, int LOG, class V, class C>
+__device__ __forceinline__ void fft_line_s(CV<V> (&x)[16], int t, const Planes<V> &sm, const C *__restrict__ tw,
+                                           const C *stw) {
+    static_assert(LOG >= 8 && LOG <= 12, "shared twiddles cover passes 1 and 2");
+    line_fft_ct<DIR, LOG, 16>(x, t, sm, tw, CtaBarrier{}, TwShared<C>{stw, stw + 240});
 }
 
 }  // namespace flame

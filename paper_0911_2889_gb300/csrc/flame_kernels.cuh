@@ -277,6 +277,29 @@ __device__ __forceinline__ void fft_line_e(CV<V> (&x)[E], int logn, int t, const
     else fft_line<DIR, LOG>(x, logn, t, sm, tw);
 }
 
+// Shared-memory twiddles of the compile-time FP32 pass-B kernels (E = 16,
+// 2^8..2^12; pass B's ~100 KB of shared memory per CTA leaves too little L1
+// for its 64 KB of global twiddle tables):
+// the 480 factor entries of TwShared, then (pass B) the factors of the real
+// post-processing table P[k] = exp(2 pi i k / 2M): Plo[k mod 64], Phi[k / 64].
+constexpr int kTwSmemBytes = 6144;  // >= (480 + 64 + 4096/64) * 8
+template <class R, int LOG, int E> constexpr bool kSharedTw = std::is_same<R, float>::value && LOG >= 8 && E == 16;
+
+template <class C> struct RealTw {
+    const C *lo, *hi;
+    __device__ __forceinline__ C operator()(int k) const {
+        const C a = lo[k & 63], b = hi[k >> 6];
+        return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+    }
+    // P = exp(2 pi i k / 2M), k < M = 2^LOGM
+    template <int LOGM> __device__ __forceinline__ static void fill(C *lo_dst, C *hi_dst, const C *P) {
+        for (int i = threadIdx.x; i < 64 + (1 << LOGM) / 64; i += blockDim.x) {
+            if (i < 64) lo_dst[i] = __ldg(P + i);
+            else hi_dst[i - 64] = __ldg(P + 64 * (i - 64));
+        }
+    }
+};
+
 // CTA shape of the compile-time kernels with E points per thread: G line
 // groups of T = 2^LOG / E threads (256 threads for E = 16, 512 for E = 8) and
 // clusters of CL CTAs holding 8 line groups (pass A's write-out).
@@ -327,6 +350,9 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
     const bool valid = k2 <= a.K2;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len_e<E>(N1);
     auto sm = make_planes(base, N1);
+    constexpr bool STW = false;  // pass A's twiddles stay in L1 (measured faster)
+    C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * 2 * plane_len_e<E>(N1));
+    if constexpr (STW) TwShared<C>::template fill<(STW ? LOG : 8)>(stw, tw1);  // synced by the transform
     const R s1 = (R)a.s1, s2k2 = (R)(a.s2 * k2);
     const C *col = state + (size_t)k2 * ld1 + a.K1;  // col[k1], k1 = -K1..K1
     // band rows: r < E/4 (k1 = n <= K1) and r >= 3E/4 (k1 = n - N1 >= -K1);
@@ -348,7 +374,12 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
             }
         }
     }
-    fft_line_e<1, LOG, E>(x, a.logn1, t, sm, tw1);
+    if constexpr (STW) {
+        __syncthreads();
+        fft_line_s<1, (STW ? LOG : 8)>(x, t, sm, tw1, stw);
+    } else {
+        fft_line_e<1, LOG, E>(x, a.logn1, t, sm, tw1);
+    }
     constexpr int CL = CLU ? ShapeE<LOG, E>::CL : 1;
     if constexpr (CL > 1 && std::is_same<R, float>::value) {
         // Park (U, V) of this column at its natural row index, then the CL
@@ -428,6 +459,24 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
     auto sm = make_planes(base, M);  // (E = 8 uses its own padding: st_raw/ld_raw)
     const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
     if (tile == 0 && threadIdx.x == 0) *d.t_copy = *d.t_in;
+    constexpr bool STW = kSharedTw<R, LOG, E>;
+    constexpr int LS = STW ? LOG : 8;
+    C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * (2 * plane_len_e<E>(M) + M));
+    RealTw<C> Pt{stw + 480, stw + 544};
+    if constexpr (STW) {
+        TwShared<C>::template fill<LS>(stw, twm);
+        RealTw<C>::template fill<LS>(stw + 480, stw + 544, P);
+        __syncthreads();
+    }
+    auto realtw = [&](int k) -> C {
+        if constexpr (STW) return Pt(k);
+        else return __ldg(P + k);
+    };
+    auto fft = [&](auto dirc, CV<V>(&x)[E]) {
+        constexpr int DIR = decltype(dirc)::value;
+        if constexpr (STW) fft_line_s<DIR, LS>(x, t, sm, twm, stw);
+        else fft_line_e<DIR, LOG, E>(x, a.logm, t, sm, twm);
+    };
 
     // |z|^2 of the first row is parked in shared memory (h_first, M entries
     // per group, after the exchange buffer) while the second row is
@@ -447,12 +496,12 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
                 if (r < E / 2) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
                 else z = C{e.u.x + e.v.y, e.v.x - e.u.y};         // conj U + i conj V
             }
-            C w = __ldg(P + kk);                                 // exp(2 pi i |k|/N2)
+            C w = realtw(kk);                                    // exp(2 pi i |k|/N2)
             C z1 = (r < E / 2) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
                            : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
             x[r] = pack2<R>(z, z1);
         }
-        fft_line_e<1, LOG, E>(x, a.logm, t, sm, twm);
+        fft(std::integral_constant<int, 1>{}, x);
     };
     CV<V> x[E];
     row_ifft(0, x);
@@ -468,7 +517,7 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
         V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
         x[r] = pack2<R>(h_first[t + r * T], C{sq.x, sq.y});
     }
-    fft_line_e<-1, LOG, E>(x, a.logm, t, sm, twm);
+    fft(std::integral_constant<int, -1>{}, x);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < E; ++r) sm.st_raw(spad_e<E>(t + r * T), x[r]);
@@ -481,7 +530,7 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
             const R hf = (R)0.5;
             CV<V> E{vmul(vadd(h.re, hc.re), vbc(hf)), vmul(vsub(h.im, hc.im), vbc(hf))};
             CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
-            C w = __ldg(P + k);
+            C w = realtw(k);
             CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
             C *dst = gk + gk_index(2 * pair, k, a.n1);  // row 2p+1 two slots further
             dst[0] = lane0<R>(Y);
@@ -539,6 +588,9 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
     const bool va = c0 <= a.K2, vb = c0 + 1 <= a.K2;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
     auto sm = make_planes(base, N1);
+    constexpr bool STW = false;  // pass C's twiddles stay in L1 (measured faster)
+    C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * 2 * plane_len(N1));
+    if constexpr (STW) TwShared<C>::template fill<(STW ? LOG : 8)>(stw, tw1);  // synced below
     const C *gp = gk + gk_index(0, c0, N1);  // row n: columns c0, c0+1 at gp[2n], gp[2n+1]
     CV<V> x[16];
     double colsum = 0.0;
@@ -580,7 +632,12 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
         }
         // red[0] is read by thread 0 after the transform's barriers
     }
-    fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
+    if constexpr (STW) {
+        __syncthreads();
+        fft_line_s<-1, (STW ? LOG : 8)>(x, t, sm, tw1, stw);
+    } else {
+        fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
+    }
 
     const Coef cf = step_coef(a, *d.t_copy);
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);

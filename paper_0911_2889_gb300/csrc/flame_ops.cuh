@@ -204,8 +204,9 @@ template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s,
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
         if (cl > 1 && variant == kVariantDirect) {  // compile-time length, direct stores
-            const int pf = resident_ctas((const void *)k_passAd<R, L>, g);
-            err = launch_cl(k_passAd<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+            Geom gd = g;
+            const int pf = resident_ctas((const void *)k_passAd<R, L>, gd);
+            err = launch_cl(k_passAd<R, L>, dim3(gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
             const Geom g8 = geom_passA8<R, L>(d.a.K2 + 1);
             constexpr int cl8 = ShapeE<L, 8>::CL;
@@ -213,7 +214,7 @@ template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s,
             err = launch_cl(k_passA8<R, L>, dim3(round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
         } else {
             // the compile-time kernels assume Shape<L>::G groups per CTA
-            const Geom gl = cl > 1 ? geom_cols(d.a.logn1, d.a.K2 + 1, Shape<L>::G) : g;
+            Geom gl = cl > 1 ? geom_cols(d.a.logn1, d.a.K2 + 1, Shape<L>::G) : g;
             const int pf = resident_ctas((const void *)k_passA<R, L>, gl);
             err = launch_cl(k_passA<R, L>, dim3(round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
         }
@@ -248,8 +249,10 @@ template <class R> cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s,
             const int pf = resident_ctas((const void *)k_passB8<R, L>, g8);
             err = launch_cl(k_passB8<R, L>, dim3(g8.blocks), g8.threads, g8.smem, s, 1, d, pf);
         } else {
-            const int pf = resident_ctas((const void *)k_passB<R, L>, g);
-            err = launch_cl(k_passB<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+            Geom gb = g;
+            if (kSharedTw<R, L, 16>) gb.smem += kTwSmemBytes;
+            const int pf = resident_ctas((const void *)k_passB<R, L>, gb);
+            err = launch_cl(k_passB<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf);
         }
     });
     if (err != cudaSuccess) return err;
@@ -278,7 +281,7 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
             constexpr int cl8 = ShapeE<L, 8>::CL;
             err = launch_cl(k_passA8_n<R, L>, dim3(round_up(g8.blocks, cl8), n), g8.threads, g8.smem, s, cl8, ds, 0);
         } else {
-            const Geom gl = cl > 1 ? geom_cols(a.logn1, a.K2 + 1, Shape<L>::G) : g;
+            Geom gl = cl > 1 ? geom_cols(a.logn1, a.K2 + 1, Shape<L>::G) : g;
             err = launch_cl(k_passA_n<R, L>, dim3(round_up(gl.blocks, cl), n), gl.threads, gl.smem, s, cl, ds, 0);
         }
     });
@@ -295,7 +298,8 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
             const Geom g8 = geom_passB8<R>(L, a.n1 / 2);
             err = launch_cl(k_passB8_n<R, L>, dim3(g8.blocks, n), g8.threads, g8.smem, s, 1, ds, 0);
         } else {
-            err = launch_cl(k_passB_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+            const size_t sm = g.smem + (kSharedTw<R, L, 16> ? kTwSmemBytes : 0);
+            err = launch_cl(k_passB_n<R, L>, dim3(g.blocks, n), g.threads, sm, s, 1, ds, 0);
         }
     });
     if (err != cudaSuccess) return err;
