@@ -12,7 +12,8 @@
  * Everything is double precision.  Complex numbers are C99 double _Complex,
  * which has the same memory layout as numpy complex128.
  *
- * Conventions (the readings are listed in the design doc of the repository):
+ * Conventions (where the paper is silent or its text garbled, these are the
+ * readings taken):
  *   grid         x_i = 2*pi*j_i/N_i, j_i = 0..N_i-1, i = 1 (theta), 2 (phi)
  *   coefficients Phi(x) = sum_k Phi_k exp(i (k1 x1 + k2 x2))
  *   wavenumbers  kappa = (s1 k1, s2 k2)      (s1 = s2 = theta_pi as printed)
@@ -418,8 +419,8 @@ double orc_area(const orc_params *p, const cplx *state, double mean, double t,
  *   lambda <- lambda + dt (omega_k lambda_k
  *             + c sum_i (-i kappa_i) ghat_i),  ghat_i = analysis of
  *             2 ell(x) d_i phi(x) / (n1 n2),  ell = synthesis of lambda.
- * The adjoint of the step under the full-spectrum inner product; derived in
- * the repository's design notes.  *dgamma accumulates
+ * The adjoint of the step under the full-spectrum inner product: the
+ * transpose of orc_step_jvp term by term.  *dgamma accumulates
  * <lambda_in, dt (|kappa|/(2 r0)) Phi> (the gamma-derivative of the step).
  * Pinned by the dot-product test against orc_step_jvp and by finite
  * differences. */

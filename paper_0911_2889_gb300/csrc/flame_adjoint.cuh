@@ -54,7 +54,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaA
             if (in_box) {
                 C phi = col[k1];
                 if (k1 == 0 && k2 == 0) phi = C{(R)mean0, 0};
-                const R f = (R)a.s1 * (R)k1;
+                const R f = scale1<R>(a) * (R)k1;
                 x[r] = pack2<R>(C{-f * phi.y, f * phi.x}, phi);
             }
         }
@@ -145,7 +145,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB
     C *park = reinterpret_cast<C *>(base + 2 * plane_len(M));  // M entries
     const C *P = twm + tw_real_offset(a.logm);
     const C *src = uv + uv_index(valid ? row : 0, 0, a.ldk);  // element kk at src + 4 kk
-    const R s2 = (R)a.s2;
+    const R s2 = scale2<R>(a);
     // phi at 2m, 2m+1 (real parts of the two lanes), parked
     CV<V> x[16];
     halfband_ifft<R>(x, a, t, P, twm,
@@ -254,7 +254,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaC
         const bool in_box = valid && ((r < 4) ? (n <= a.K1) : (k1 >= -a.K1));
         if (in_box) {
             C A = lane0<R>(x[r]), B1 = lane1<R>(x[r]);
-            const R f1 = (R)a.s1 * (R)k1, f2 = (R)a.s2 * (R)k2;
+            const R f1 = scale1<R>(a) * (R)k1, f2 = scale2<R>(a) * (R)k2;
             // A - i f1 B1 - i f2 B2
             C gr{A.x + f1 * B1.y + f2 * B2[i].y, A.y - f1 * B1.x - f2 * B2[i].x};
             if (k1 == 0 && k2 == 0) {
@@ -359,7 +359,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(
         x[r] = pack2<R>(h1, h2);
     }
     C *aw = static_cast<C *>(d.aw);
-    const R s2 = (R)a.s2;
+    const R s2 = scale2<R>(a);
     real_fwd<R>(x, a, t, P, twm, base, valid, [&](int k, CV<V> Y) {
         C q1 = lane0<R>(Y), q2 = lane1<R>(Y);
         const R f = s2 * (R)k;
@@ -392,16 +392,21 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(
         UV<R> e = valid ? ld_uv<R>(aw + 2 * n) : UV<R>{C{0, 0}, C{0, 0}};
         x[r] = pack2<R>(e.u, e.v);
     }
+    __shared__ CoefR<R> cfs;
+    Coef cf{};  // thread 0 only
+    if (threadIdx.x == 0) {
+        cf = step_coef(a, *d.t);
+        cfs = coef_r<R>(cf, a);
+    }
     line_fft<-1>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1), CtaBarrier{});
-    const Coef cf = step_coef(a, *d.t);
+    __syncthreads();  // cfs
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
-    const double inv = 1.0 / ((double)N1 * (double)a.n2);
-    const R ra = (R)cf.a, rb = (R)cf.b, rcs = (R)(cf.c * inv), rdt = (R)a.dt;
+    const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
+    const R s1 = scale1<R>(a), s2 = scale2<R>(a);
     const C *lam = static_cast<const C *>(d.lam) + (size_t)k2 * ld1 + a.K1;
     C *lout = static_cast<C *>(d.lam_out) + (size_t)k2 * ld1 + a.K1;
     const C *phi = static_cast<const C *>(d.state) + (size_t)k2 * ld1 + a.K1;
-    const double hdt = a.dt / (2.0 * cf.tn);
-    double dg = 0.0;
+    double dg = 0.0;  // sum of 2 kappa (lambda . Phi); times dt / (2 r0) at the end
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         if (r < 4 || r >= 12) {
@@ -411,15 +416,15 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(
             // k2 = 0, k1 < 0: conjugate mirror of +k1, written (and counted in
             // the gamma gradient, with the same value) by the owner of +k1
             if (!in_box || (k1 == 0 && k2 == 0) || (k2 == 0 && k1 < 0)) continue;
-            const R f1 = (R)a.s1 * (R)k1;
+            const R f1 = s1 * (R)k1;
             C Q1 = lane0<R>(x[r]), Q2 = lane1<R>(x[r]);
             C Pk{f1 * Q1.y + Q2.x, -f1 * Q1.x + Q2.y};  // -i f1 Q1 + Q2
             C l = lam[k1];
-            const R kap = kappa_norm<R>((R)a.s1 * (R)k1, (R)a.s2 * (R)k2);
+            const R kap = kappa_norm<R>(f1, s2 * (R)k2);
             if (lin) {
                 C ph = phi[k1];
                 // weight 2: k2 > 0 stands for +-k; k2 = 0 here counts +k1 and -k1
-                dg += 2.0 * hdt * (double)kap * ((double)l.x * ph.x + (double)l.y * ph.y);
+                dg += 2.0 * (double)kap * ((double)l.x * ph.x + (double)l.y * ph.y);
             }
             const R om = lin ? kap * (rb - kap * ra) : (R)0;
             const R cn = nl ? rcs : (R)0;
@@ -433,7 +438,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int i = 0; i < (int)blockDim.x; ++i) s += red[i];
-        if (s != 0.0) atomicAdd(d.dgamma, s);
+        if (s != 0.0) atomicAdd(d.dgamma, s * (a.dt / (2.0 * cf.tn)));
     }
 }
 

@@ -352,6 +352,8 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
     a.ldk = p.K2 + 1;
     a.s1 = p.s1;
     a.s2 = p.s2;
+    a.s1f = (float)p.s1;
+    a.s2f = (float)p.s2;
     a.gamma = p.gamma;
     a.t0 = p.t0;
     a.dt = p.dt;

@@ -25,6 +25,7 @@ struct StepArgs {
     int K1, K2;        // retained harmonics
     int ldk;           // row length of the compact box and workspaces (K2+1)
     double s1, s2;     // kappa = (s1 k1, s2 k2)
+    float s1f, s2f;    // s1, s2 rounded once on the host (FP32 kernels)
     double gamma, t0, dt;
     unsigned flags;
 };

@@ -27,6 +27,16 @@ namespace flame {
 template <class R> using CplxT = typename VecOf<R>::c;  // float2 / double2
 static_assert(sizeof(float2) == sizeof(VecOf<float>::type) && sizeof(double2) == sizeof(VecOf<double>::type), "C and V sizes");
 
+// s1, s2 in the kernel's precision (the FP32 copies are rounded on the host)
+template <class R> __device__ __forceinline__ R scale1(const StepArgs &s) {
+    if constexpr (std::is_same<R, float>::value) return s.s1f;
+    else return s.s1;
+}
+template <class R> __device__ __forceinline__ R scale2(const StepArgs &s) {
+    if constexpr (std::is_same<R, float>::value) return s.s2f;
+    else return s.s2;
+}
+
 // FP32 kernels fit 128 registers (two CTAs of 256 threads per SM); FP64
 // kernels need up to 255 (one CTA per SM).
 template <class R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
@@ -313,7 +323,7 @@ template <int E> struct ShapeE<0, E> {  // runtime-length kernels: no clusters
     static constexpr int T = 0, THREADS = 256, G = 0, CL = 1;
 };
 
-// Memory layouts (see include/flame.h and the design doc):
+// Memory layouts (the state's is also documented in include/flame.h):
 //   state  column-major compact box: element (k1, k2) at k2 * ld1 + (k1 + K1),
 //          ld1 = 2 K1 + 1
 //   uv     N1 x (K2+1) pairs (U, V), row pairs interleaved: element (j1, k2)
@@ -353,7 +363,7 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
     constexpr bool STW = false;  // pass A's twiddles stay in L1 (measured faster)
     C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * 2 * plane_len_e<E>(N1));
     if constexpr (STW) TwShared<C>::template fill<(STW ? LOG : 8)>(stw, tw1);  // synced by the transform
-    const R s1 = (R)a.s1, s2k2 = (R)(a.s2 * k2);
+    const R s1 = scale1<R>(a), s2k2 = scale2<R>(a) * (R)k2;
     const C *col = state + (size_t)k2 * ld1 + a.K1;  // col[k1], k1 = -K1..K1
     // band rows: r < E/4 (k1 = n <= K1) and r >= 3E/4 (k1 = n - N1 >= -K1);
     // the middle half of the registers is zero padding, dropped at compile time
@@ -554,9 +564,29 @@ __device__ __forceinline__ Coef step_coef(const StepArgs &s, double t) {
     return k;
 }
 
+// The step coefficients in the kernel's precision: 1/r0^2, gamma/(2 r0),
+// c/(N1 N2) (c = 1/(2 r0^2) with the inverse transform's scale folded in)
+// and dt.  Thread 0 of a CTA derives them once in FP64 and shares them:
+// GB300's FP64 pipe is narrow, and three divisions in every thread cost the
+// column pass more than its transform.
+template <class R> struct CoefR {
+    R a, b, cs, dt;
+};
+template <class R> __device__ __forceinline__ CoefR<R> coef_r(const Coef &cf, const StepArgs &s) {
+    const double inv = 1.0 / ((double)s.n1 * (double)s.n2);
+    return CoefR<R>{(R)cf.a, (R)cf.b, (R)(cf.c * inv), (R)s.dt};
+}
+
+// |kappa| = sqrt((s1 k1)^2 + (s2 k2)^2) for (k1, k2) != 0.  FP32: x times the
+// hardware reciprocal square root (within a few ulp, far inside the FP32
+// path's per-step tolerance); FP64: the correctly rounded square root.
 template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
-    if constexpr (std::is_same<R, float>::value) return __fsqrt_rn(fmaf(s1k1, s1k1, s2k2 * s2k2));
-    else return sqrt(fma(s1k1, s1k1, s2k2 * s2k2));
+    if constexpr (std::is_same<R, float>::value) {
+        const float x = fmaf(s1k1, s1k1, s2k2 * s2k2);
+        return x * rsqrtf(x);
+    } else {
+        return sqrt(fma(s1k1, s1k1, s2k2 * s2k2));
+    }
 }
 
 // Pass C (a7..a10): columns k2, k2+1 of gk -> forward FFT along j1 (outputs
@@ -583,6 +613,12 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
             l2_prefetch(gk + (size_t)c * N1, (size_t)nc * N1 * sizeof(C));
             l2_prefetch(state + (size_t)c * ld1, (size_t)nc * ld1 * sizeof(C));
         }
+    }
+    __shared__ CoefR<R> cfs;
+    Coef cf{};  // thread 0 only
+    if (threadIdx.x == 0) {
+        cf = step_coef(a, *d.t_copy);
+        cfs = coef_r<R>(cf, a);
     }
     const int c0 = 2 * (tile * G + g);
     const bool va = c0 <= a.K2, vb = c0 + 1 <= a.K2;
@@ -639,10 +675,10 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
         fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
     }
 
-    const Coef cf = step_coef(a, *d.t_copy);
+    __syncthreads();  // cfs (the transform may have no barrier for short lines)
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
-    const double inv = 1.0 / ((double)N1 * (double)a.n2);
-    const R ra = (R)cf.a, rb = (R)cf.b, rcs = (R)(cf.c * inv), rdt = (R)a.dt;
+    const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
+    const R s1 = scale1<R>(a), s2 = scale2<R>(a);
     int bad = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -663,7 +699,7 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
             }
             C gh = side == 0 ? lane0<R>(x[r]) : lane1<R>(x[r]);
             C ph = phi[i][side];
-            const R kap = kappa_norm<R>((R)a.s1 * (R)k1, (R)a.s2 * (R)k2);
+            const R kap = kappa_norm<R>(s1 * (R)k1, s2 * (R)k2);
             const R om = lin ? kap * (rb - kap * ra) : (R)0;
             const R cn = nl ? rcs : (R)0;
             C nw{ph.x + rdt * (om * ph.x + cn * gh.x), ph.y + rdt * (om * ph.y + cn * gh.y)};
@@ -674,7 +710,7 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
     }
     if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
     if (tile == 0 && threadIdx.x == 0) {
-        const double mg = red[0] * inv;  // mean of |grad Phi|^2
+        const double mg = red[0] / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
         if (nl) *d.mean += a.dt * cf.c * mg;
         long n = __double2ll_rn((cf.tn - a.t0) / a.dt);
         *d.t_out = a.t0 + (double)(n + 1) * a.dt;

@@ -84,7 +84,7 @@ def _dir_err(a, b):
 
 
 @pytest.mark.gpu
-def test_adjoint_config5_512x1024(fl, orc):
+def test_adjoint_512x1024_200_steps(fl, orc):
     # gradient of the final area over 200 FP32 steps on 512 x 1024 (|k| <= 64,
     # seed 7), checkpoints every 20 steps with recompute
     n1, n2, nsteps, ckpt = 512, 1024, 200, 20

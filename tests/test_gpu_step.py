@@ -48,7 +48,7 @@ def _box_err(a, b, K1):
 @pytest.mark.gpu
 @pytest.mark.parametrize("gamma", [0.8, 0.5])
 @pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
-def test_fp64_config1_trajectory(fl, orc, gamma, seed):
+def test_fp64_128x256_100_step_trajectory(fl, orc, gamma, seed):
     # 128 x 256, |k| <= 16, 100 explicit steps, dt = 1e-3, t0 = 200
     f, st0, state, mean, t = _setup(fl, 128, 256, "fp64", 16, seed, gamma=gamma)
     p = _oparams(orc, f)
@@ -118,7 +118,7 @@ def test_linear_and_nonlinear_only(fl, orc, flags, prec, tol):
 
 
 @pytest.mark.gpu
-def test_fp32_config2_one_step_and_drift(fl, orc):
+def test_fp32_1024x2048_one_step_and_drift(fl, orc):
     # 1024 x 2048, FP32 FFTs and pointwise work, FP64 mean mode and time,
     # |k| <= 256, compared with the FP64 oracle every 100 steps over 1000.
     f, st0, state, mean, t = _setup(fl, 1024, 2048, "fp32", 256, 0)

@@ -60,7 +60,7 @@ def _run_pair(fl, n1, n2, prec, seed, nsteps):
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_noalloc_matches_flame_step_on_two_calls(fl, prec):
-    # first call: 128 x 256 (the FP64 small configuration's grid) ...
+    # first call: 128 x 256 ...
     (a, ma, ta), (b, mb, tb) = _run_pair(fl, 128, 256, prec, seed=3, nsteps=4)
     assert rel_l2(b, a) < TOL[prec]
     assert tb == ta and abs(mb - ma) <= 1e-12 * abs(ma)
