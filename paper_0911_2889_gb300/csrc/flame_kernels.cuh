@@ -68,6 +68,25 @@ template <class R> __device__ __forceinline__ UV<R> ld_uv(const CplxT<R> *p) {
         return {__ldg(p), __ldg(p + 1)};
     }
 }
+// (U, V) in shared memory (16-byte aligned slots)
+template <class R> __device__ __forceinline__ UV<R> ld_uv_s(const UV<R> *p) {
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+    } else {
+        const double2 *d = reinterpret_cast<const double2 *>(p);
+        return {d[0], d[1]};
+    }
+}
+template <class R> __device__ __forceinline__ void st_uv_s(UV<R> *p, UV<R> e) {
+    if constexpr (std::is_same<R, float>::value) {
+        *reinterpret_cast<float4 *>(p) = make_float4(e.u.x, e.u.y, e.v.x, e.v.y);
+    } else {
+        double2 *d = reinterpret_cast<double2 *>(p);
+        d[0] = e.u;
+        d[1] = e.v;
+    }
+}
 template <class R> __device__ __forceinline__ void st_uv(CplxT<R> *p, CplxT<R> u, CplxT<R> v) {
     if constexpr (std::is_same<R, float>::value) {
         *reinterpret_cast<float4 *>(p) = make_float4(u.x, u.y, v.x, v.y);
@@ -488,40 +507,71 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
         else fft_line_e<DIR, LOG, E>(x, a.logm, t, sm, twm);
     };
 
-    // |z|^2 of the first row is parked in shared memory (h_first, M entries
-    // per group, after the exchange buffer) while the second row is
-    // transformed; the second row's stays in registers.
+    // Input staging.  Thread t loads, for k = t + r T (r < E/2: each k in
+    // [0, M/2) once; K2 < M/2), the (U, V) of both rows: one 32-byte sector
+    // of the row-pair interleave.  Row 2p's entries are staged in the
+    // exchange buffer (idle until the first transform's first exchange) and
+    // row 2p+1's in the h region (idle until the first row's |z|^2 is
+    // parked), so the negative frequencies -k, which other threads need,
+    // are read from shared memory instead of being loaded a second time.
+    // After row 2p's transform, |z|^2 of row 2p is parked in the h region
+    // (M entries per group) while row 2p+1 is transformed; row 2p+1's stays
+    // in registers.
     C *h_first = reinterpret_cast<C *>(base + 2 * plane_len_e<E>(M));
-    auto row_ifft = [&](int q, CV<V>(&x)[E]) {
-        const int row = 2 * pair + q;
-        const C *src = uv + uv_index(row, 0, a.ldk);  // element kk at src + 4 kk
+    UV<R> *stage0 = reinterpret_cast<UV<R> *>(base), *stage1 = reinterpret_cast<UV<R> *>(h_first);
+    const int half = M >> 1;
+    UV<R> e0[E / 2];
+    {
+        const C *src = uv + uv_index(2 * pair, 0, a.ldk);  // k: row 2p at src + 4k, row 2p+1 at src + 4k + 2
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) {
+            const int k = t + r * T;
+            UV<R> e1{C{0, 0}, C{0, 0}};
+            e0[r] = e1;
+            if (valid && k <= a.K2) {
+                e0[r] = ld_uv<R>(src + 4 * (size_t)k);
+                e1 = ld_uv<R>(src + 4 * (size_t)k + 2);
+            }
+            st_uv_s<R>(stage0 + k, e0[r]);
+            st_uv_s<R>(stage1 + k, e1);
+        }
+    }
+    __syncthreads();
+    // the full spectrum Z of one row (Z[k] = U[k] + i V[k], U[-k] = conj
+    // U[k]) split into the inputs of the two half-length inverse FFTs:
+    // lane 0 Z[k], lane 1 Z[k] exp(2 pi i k/N2)
+    auto build = [&](auto own, const UV<R> *stage, CV<V>(&x)[E]) {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int n = t + r * T;
             // r < E/2: k = n >= 0 (n < M/2); r >= E/2: k = n - M < 0
             const int kk = (r < E / 2) ? n : M - n;
-            C z{0, 0};
-            if (valid && kk <= a.K2) {
-                UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
-                if (r < E / 2) z = C{e.u.x - e.v.y, e.u.y + e.v.x};   // U + iV
-                else z = C{e.u.x + e.v.y, e.v.x - e.u.y};         // conj U + i conj V
+            UV<R> e{C{0, 0}, C{0, 0}};
+            if constexpr (decltype(own)::value) {
+                if (r < E / 2) e = e0[r];
+                else if (kk < half) e = ld_uv_s<R>(stage + kk);
+            } else {
+                if (kk < half) e = ld_uv_s<R>(stage + kk);
             }
-            C w = realtw(kk);                                    // exp(2 pi i |k|/N2)
+            C z = (r < E / 2) ? C{e.u.x - e.v.y, e.u.y + e.v.x}     // U + iV
+                              : C{e.u.x + e.v.y, e.v.x - e.u.y};    // conj U + i conj V
+            C w = realtw(kk);                                       // exp(2 pi i |k|/N2)
             C z1 = (r < E / 2) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
-                           : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
+                               : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
             x[r] = pack2<R>(z, z1);
         }
-        fft(std::integral_constant<int, 1>{}, x);
     };
     CV<V> x[E];
-    row_ifft(0, x);
+    build(std::true_type{}, stage0, x);
+    fft(std::integral_constant<int, 1>{}, x);
+    V sq0[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        // g at grid points 2m and 2m+1: |z_0|^2, |z_1|^2
-        V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
-        h_first[t + r * T] = C{sq.x, sq.y};
-    }
-    row_ifft(1, x);
+    for (int r = 0; r < E; ++r) sq0[r] = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));  // g at 2m, 2m+1
+    build(std::false_type{}, stage1, x);
+    __syncthreads();  // stage1 fully read: the h region takes row 2p's g
+#pragma unroll
+    for (int r = 0; r < E; ++r) h_first[t + r * T] = C{sq0[r].x, sq0[r].y};
+    fft(std::integral_constant<int, 1>{}, x);
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
