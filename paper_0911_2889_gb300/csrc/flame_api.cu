@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "flame.h"
 #include "flame_internal.h"
 #include "fft_engine.cuh"
@@ -63,6 +65,30 @@ constexpr int kGraphCache = 8;
 
 void flame::set_last_error(const char *msg) { g_err = msg; }
 
+bool flame::encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    if (!encode || !map || !uv || n1 < 2 || (n1 & 1) || ldk < 1) return false;
+    // uv as floats: (8 floats of a row pair) x k2 (32-byte stride) x row pair
+    const cuuint64_t dims[3] = {8, (cuuint64_t)ldk, (cuuint64_t)(n1 / 2)};
+    const cuuint64_t strides[2] = {32, (cuuint64_t)ldk * 32};
+    const cuuint32_t box[3] = {8, 1, (cuuint32_t)flame::uv_box_pairs(n1)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, uv, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct GraphEntry {
     const void *state;
     const double *mean, *t;
@@ -96,6 +122,10 @@ struct flame_ctx {
     size_t adj_cap = 0;
     // kernel variants picked by the autotuner for passes A and B
     int var_a = 0, var_b = 0;
+    // tensor map of uv for the tensor-store variant of pass A (FP32)
+    CUtensorMap uv_map;
+    bool has_uv_map = false;
+    const CUtensorMap *map() const { return has_uv_map ? &uv_map : nullptr; }
 };
 
 namespace {
@@ -151,7 +181,7 @@ cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
         if ((e = Ops<double>::passB(d, s, h->var_b)) != cudaSuccess) return e;
         return Ops<double>::passC(d, s);
     }
-    if ((e = Ops<float>::passA(d, s, h->var_a)) != cudaSuccess) return e;
+    if ((e = Ops<float>::passA(d, s, h->var_a, h->map())) != cudaSuccess) return e;
     if ((e = Ops<float>::passB(d, s, h->var_b)) != cudaSuccess) return e;
     return Ops<float>::passC(d, s);
 }
@@ -171,7 +201,9 @@ flame_status autotune(flame_ctx *h) {
     if (force) {
         int va = 0, vb = 0;
         if (sscanf(force, "%d,%d", &va, &vb) == 2) {
-            h->var_a = va == 2 ? flame::kVariantRadix8A : va ? flame::kVariantDirect : flame::kVariantDefault;
+            h->var_a = va == 3 ? flame::kVariantTma
+                       : va == 2 ? flame::kVariantRadix8A
+                       : va ? flame::kVariantDirect : flame::kVariantDefault;
             h->var_b = vb ? flame::kVariantRadix8 : flame::kVariantDefault;
             return FLAME_OK;
         }
@@ -217,7 +249,7 @@ flame_status autotune(flame_ctx *h) {
         for (int rep = 0; rep < 4 && r == cudaSuccess; ++rep) {
             r = cudaEventRecord(e0, h->cap);
             if (r == cudaSuccess)
-                r = pass == 0 ? Ops<float>::passA(d, h->cap, variant) : Ops<float>::passB(d, h->cap, variant);
+                r = pass == 0 ? Ops<float>::passA(d, h->cap, variant, h->map()) : Ops<float>::passB(d, h->cap, variant);
             if (r == cudaSuccess) r = cudaEventRecord(e1, h->cap);
             if (r == cudaSuccess) r = cudaEventSynchronize(e1);
             float t = 0.f;
@@ -227,10 +259,11 @@ flame_status autotune(flame_ctx *h) {
         *ms = total / 3.f;
         return r;
     };
-    const int avars[3] = {flame::kVariantDefault, flame::kVariantDirect, flame::kVariantRadix8A};
+    const int avars[4] = {flame::kVariantDefault, flame::kVariantDirect, flame::kVariantRadix8A, flame::kVariantTma};
     const int bvars[2] = {flame::kVariantDefault, flame::kVariantRadix8};
     float best_a = 1e30f, best_b = 1e30f;
     for (int v : avars) {
+        if (v == flame::kVariantTma && !h->has_uv_map) continue;
         float ms = 0;
         if (e == cudaSuccess) e = time_it(0, v, &ms);
         if (e == cudaSuccess && ms < best_a) {
@@ -392,6 +425,8 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap);
         if (e != cudaSuccess) st = fail(FLAME_ECUDA, "flame_create: %s", cudaGetErrorString(e));
     }
+    if (st == FLAME_OK && p.prec == FLAME_FP32_MIXED && h->logn1 >= 8 && h->logn1 <= 12)
+        h->has_uv_map = flame::encode_uv_map(&h->uv_map, h->uv, (int)n1, (int)ldk);
     if (st == FLAME_OK) st = autotune(h);
     if (st != FLAME_OK) {
         free_ctx(h);
@@ -502,7 +537,7 @@ flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode
         CUDA_TRY(pass == 0 ? Ops<double>::passA(d, s, h->var_a)
                  : pass == 1 ? Ops<double>::passB(d, s, h->var_b) : Ops<double>::passC(d, s));
     else
-        CUDA_TRY(pass == 0 ? Ops<float>::passA(d, s, h->var_a)
+        CUDA_TRY(pass == 0 ? Ops<float>::passA(d, s, h->var_a, h->map())
                  : pass == 1 ? Ops<float>::passB(d, s, h->var_b) : Ops<float>::passC(d, s));
     return FLAME_OK;
 }

@@ -2,6 +2,7 @@
 // per-precision kernel translation units.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <type_traits>
 
@@ -17,6 +18,7 @@ constexpr int kVariantDefault = 0;
 constexpr int kVariantDirect = 1;   // pass A: direct stores (no cluster write-out)
 constexpr int kVariantRadix8 = 1;   // pass B: 8 points per thread, 512-thread CTAs
 constexpr int kVariantRadix8A = 2;  // pass A: 8 points per thread, cluster write-out
+constexpr int kVariantTma = 3;      // pass A: column written by tensor stores (FP32)
 
 // Plain-old-data arguments of the step kernels.
 struct StepArgs {
@@ -88,8 +90,11 @@ template <class R> struct Ops {
     // One step pass for one flame (desc by value) or for nflames flames of
     // the same grid (descs: device array of nflames entries, shape from a).
     // variant: kVariantDefault, or a tuned alternative (pass A: kVariantDirect
-    // = no cluster write-out; pass B: kVariantRadix8 = 8 points per thread)
-    static cudaError_t passA(const FlameDesc &d, cudaStream_t s, int variant = 0);
+    // = no cluster write-out, kVariantTma = tensor-store write-out through
+    // uv_map, a map of d.uv made by encode_uv_map; pass B: kVariantRadix8 = 8
+    // points per thread)
+    static cudaError_t passA(const FlameDesc &d, cudaStream_t s, int variant = 0,
+                             const CUtensorMap *uv_map = nullptr);
     static cudaError_t passB(const FlameDesc &d, cudaStream_t s, int variant = 0);
     static cudaError_t passC(const FlameDesc &d, cudaStream_t s);
     static cudaError_t passA_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
@@ -107,5 +112,14 @@ template <class R> struct Ops {
     static cudaError_t adj_step(const AdjDesc &d, cudaStream_t s);
     static cudaError_t prepare();  // opt-in shared memory sizes (idempotent)
 };
+
+// Row pairs per tensor store of the uv write-out of pass A (<= 256).
+__host__ __device__ constexpr int uv_box_pairs(int n1) { return n1 / 2 < 256 ? n1 / 2 : 256; }
+
+// Tensor map of an FP32 uv workspace (n1 rows, ldk columns) for the
+// tensor-store write-out of pass A: dimensions (8 floats of a row pair, k2,
+// row pair), box (8, 1, uv_box_pairs(n1)).  False when the driver has no
+// tensor-map encoder or rejects the map (the variant is then not offered).
+bool encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk);
 
 }  // namespace flame

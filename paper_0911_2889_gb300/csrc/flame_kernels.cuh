@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda.h>  // CUtensorMap
 
 #include "fft_engine.cuh"
 #include "flame_internal.h"
@@ -285,6 +286,23 @@ __device__ __forceinline__ void l2_prefetch(const void *begin, size_t bytes) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((unsigned)(e - b)) : "memory");
 }
 
+// Tensor stores (TMA) from shared memory.  The writing threads fence their
+// shared-memory stores towards the async proxy, the CTA synchronises, then one
+// thread issues the copies, commits them as a bulk group and waits until they
+// have read shared memory (a hardware wait on the copy engine, no spinning).
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, const void *smem, int x, int y, int z) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<unsigned long long>(tm)),
+                 "r"(sa), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_wait_read() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 // Compile-time CTA shape of the FP32 step kernels (LOG > 0): G line groups of
 // T = 2^LOG / 16 threads, and, for pass A, clusters of CL CTAs (CL G = 8
 // columns) that write their transposed output cooperatively through
@@ -359,8 +377,9 @@ template <int E> struct ShapeE<0, E> {  // runtime-length kernels: no clusters
 // r = 4..11 of the first pass are always zero and are dropped at compile
 // time).  Writes uv[j1][k2] = (U, V) with U = synthesis of a, V = i s2 k2 x
 // synthesis of b.
-template <class R, int LOG, int E, bool CLU = true>
-__device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+template <class R, int LOG, int E, bool CLU = true, bool TMA = false>
+__device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf,
+                                           const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -447,6 +466,40 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
             if (kc <= a.K2) *reinterpret_cast<float4 *>(uv + uv_index(n, kc, a.ldk)) = v;
         }
         cluster.sync();
+    } else if constexpr (TMA && std::is_same<R, float>::value && LOG > 0) {
+        // Park (U, V) of this column at row n (16 bytes per row: the order of
+        // a column of the interleaved uv, row pair by row pair), then the
+        // first thread of the group writes the column with tensor stores of
+        // uv_box_pairs(N1) row pairs (32 bytes each, one uv sector per row
+        // pair).  The copy engine, not the load/store unit, then issues the
+        // scattered sector writes of a column.
+        __syncthreads();  // the transform's last exchange has been read
+        float4 *park = reinterpret_cast<float4 *>(base);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int n = t + r * T;
+            C U = lane0<R>(x[r]);
+            C Vb = lane1<R>(x[r]);
+            park[n] = make_float4(U.x, U.y, -s2k2 * Vb.y, s2k2 * Vb.x);
+        }
+        fence_async_smem();
+        __syncthreads();
+        // a tensor copy needs a 128-byte aligned shared address: any other
+        // placement of the dynamic shared memory takes the direct stores
+        const bool aligned = (__cvta_generic_to_shared(smraw) & 127) == 0;
+        if (!aligned && valid) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int n = t + r * T;
+                *reinterpret_cast<float4 *>(uv + uv_index(n, k2, a.ldk)) = park[n];
+            }
+        }
+        if (aligned && t == 0 && valid) {
+            constexpr int BP = uv_box_pairs(1 << LOG);
+#pragma unroll 1
+            for (int p0 = 0; p0 < (N1 >> 1); p0 += BP) tma_store_3d(tm, park + 2 * p0, 0, k2, p0);
+            bulk_commit_and_wait_read();
+        }
     } else if (valid) {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
@@ -776,6 +829,12 @@ template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>
 // compile-time length, direct (scattered) stores instead of the cluster write-out
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAd(FlameDesc d, int pf) {
     passA_body<R, LOG, 16, false>(d, blockIdx.x, gridDim.x, pf);
+}
+// compile-time length, column written out by tensor stores (FP32); the
+// tensor map describes uv as (8 floats of a row pair) x k2 x row pair
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAt(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
+    passA_body<R, LOG, 16, false, true>(d, blockIdx.x, gridDim.x, pf, &tm);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(FlameDesc d, int pf) {

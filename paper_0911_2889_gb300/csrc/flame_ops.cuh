@@ -141,6 +141,7 @@ template <class R> cudaError_t Ops<R>::prepare() {
         set((const void *)k_passA8_n<R, L>);
         set((const void *)k_passAd<R, L>);
         set((const void *)k_passAd_n<R, L>);
+        set((const void *)k_passAt<R, L>);
         set((const void *)k_passC_n<R, L>);
     });
     set((const void *)k_areaA<R>);
@@ -197,13 +198,17 @@ template <class R, int L> static Geom geom_passA8(int ncols) {
     return g;
 }
 
-template <class R> cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant) {
+template <class R>
+cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *uv_map) {
     Geom g = geom_cols(d.a.logn1, d.a.K2 + 1, 0);
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
-        if (cl > 1 && variant == kVariantDirect) {  // compile-time length, direct stores
+        if (sizeof(R) == 4 && L > 0 && variant == kVariantTma && uv_map) {  // tensor-store write-out
+            const int pf = resident_ctas((const void *)k_passAt<R, L>, g);
+            err = launch_cl(k_passAt<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
+        } else if (cl > 1 && (variant == kVariantDirect || variant == kVariantTma)) {  // direct stores
             Geom gd = g;
             const int pf = resident_ctas((const void *)k_passAd<R, L>, gd);
             err = launch_cl(k_passAd<R, L>, dim3(gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
@@ -274,7 +279,7 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
     with_log<R>(a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
-        if (cl > 1 && variant == kVariantDirect) {
+        if (cl > 1 && (variant == kVariantDirect || variant == kVariantTma)) {  // (no tensor maps per flame)
             err = launch_cl(k_passAd_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
             const Geom g8 = geom_passA8<R, L>(a.K2 + 1);
