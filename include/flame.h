@@ -104,8 +104,8 @@ flame_status flame_get_params(flame_t h, flame_params *out);
  * creation, FLAME_AUTOTUNE=0 disables it): pass A 0 = cluster write-out
  * through distributed shared memory, 1 = direct stores, 2 = 8 points per
  * thread with the cluster write-out, 3 = write-out by tensor (TMA) stores;
- * pass B 0 = 16 points per thread, 1 = 8 points per thread.  EINVAL on null
- * pointers. */
+ * pass B 0 = 16 points per thread, 1 = 8 points per thread, 2 = 16 points
+ * per thread with the write-out by tensor stores.  EINVAL on null pointers. */
 flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant);
 
 /* Number of complex entries of the compact box, (2 K1 + 1) * (K2 + 1). */

@@ -65,7 +65,9 @@ constexpr int kGraphCache = 8;
 
 void flame::set_last_error(const char *msg) { g_err = msg; }
 
-bool flame::encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk) {
+namespace {
+// the driver's tensor-map encoder, looked up once (null when unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -78,6 +80,26 @@ bool flame::encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk) {
         else
             cudaGetLastError();
     });
+    return encode;
+}
+}  // namespace
+
+bool flame::encode_gk_map(CUtensorMap *map, void *gk, int n1, int ldk) {
+    const auto encode = tensor_map_encoder();
+    if (!encode || !map || !gk || n1 < 2 || (n1 & 1) || ldk < 1) return false;
+    // gk as floats: (8 floats: rows 2p, 2p+1 x columns 2q, 2q+1) x row pair
+    // (32-byte stride) x column pair (n1 x 16-byte stride)
+    const cuuint64_t dims[3] = {8, (cuuint64_t)(n1 / 2), (cuuint64_t)((ldk + 1) / 2)};
+    const cuuint64_t strides[2] = {32, (cuuint64_t)n1 * 16};
+    const cuuint32_t box[3] = {8, 1, (cuuint32_t)flame::gk_box_pairs(ldk)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, gk, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool flame::encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk) {
+    const auto encode = tensor_map_encoder();
     if (!encode || !map || !uv || n1 < 2 || (n1 & 1) || ldk < 1) return false;
     // uv as floats: (8 floats of a row pair) x k2 (32-byte stride) x row pair
     const cuuint64_t dims[3] = {8, (cuuint64_t)ldk, (cuuint64_t)(n1 / 2)};
@@ -123,9 +145,10 @@ struct flame_ctx {
     // kernel variants picked by the autotuner for passes A and B
     int var_a = 0, var_b = 0;
     // tensor map of uv for the tensor-store variant of pass A (FP32)
-    CUtensorMap uv_map;
-    bool has_uv_map = false;
+    CUtensorMap uv_map, gk_map;  // tensor maps of uv and gk for the tensor-store variants (FP32)
+    bool has_uv_map = false, has_gk_map = false;
     const CUtensorMap *map() const { return has_uv_map ? &uv_map : nullptr; }
+    const CUtensorMap *gmap() const { return has_gk_map ? &gk_map : nullptr; }
 };
 
 namespace {
@@ -182,7 +205,7 @@ cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
         return Ops<double>::passC(d, s);
     }
     if ((e = Ops<float>::passA(d, s, h->var_a, h->map())) != cudaSuccess) return e;
-    if ((e = Ops<float>::passB(d, s, h->var_b)) != cudaSuccess) return e;
+    if ((e = Ops<float>::passB(d, s, h->var_b, h->gmap())) != cudaSuccess) return e;
     return Ops<float>::passC(d, s);
 }
 
@@ -204,7 +227,7 @@ flame_status autotune(flame_ctx *h) {
             h->var_a = va == 3 ? flame::kVariantTma
                        : va == 2 ? flame::kVariantRadix8A
                        : va ? flame::kVariantDirect : flame::kVariantDefault;
-            h->var_b = vb ? flame::kVariantRadix8 : flame::kVariantDefault;
+            h->var_b = vb == 2 ? flame::kVariantTmaB : vb ? flame::kVariantRadix8 : flame::kVariantDefault;
             return FLAME_OK;
         }
     }
@@ -249,7 +272,8 @@ flame_status autotune(flame_ctx *h) {
         for (int rep = 0; rep < 4 && r == cudaSuccess; ++rep) {
             r = cudaEventRecord(e0, h->cap);
             if (r == cudaSuccess)
-                r = pass == 0 ? Ops<float>::passA(d, h->cap, variant, h->map()) : Ops<float>::passB(d, h->cap, variant);
+                r = pass == 0 ? Ops<float>::passA(d, h->cap, variant, h->map())
+                              : Ops<float>::passB(d, h->cap, variant, h->gmap());
             if (r == cudaSuccess) r = cudaEventRecord(e1, h->cap);
             if (r == cudaSuccess) r = cudaEventSynchronize(e1);
             float t = 0.f;
@@ -260,7 +284,7 @@ flame_status autotune(flame_ctx *h) {
         return r;
     };
     const int avars[4] = {flame::kVariantDefault, flame::kVariantDirect, flame::kVariantRadix8A, flame::kVariantTma};
-    const int bvars[2] = {flame::kVariantDefault, flame::kVariantRadix8};
+    const int bvars[3] = {flame::kVariantDefault, flame::kVariantRadix8, flame::kVariantTmaB};
     float best_a = 1e30f, best_b = 1e30f;
     for (int v : avars) {
         if (v == flame::kVariantTma && !h->has_uv_map) continue;
@@ -272,6 +296,7 @@ flame_status autotune(flame_ctx *h) {
         }
     }
     for (int v : bvars) {
+        if (v == flame::kVariantTmaB && !h->has_gk_map) continue;
         float ms = 0;
         if (e == cudaSuccess) e = time_it(1, v, &ms);
         if (e == cudaSuccess && ms < best_b) {
@@ -427,6 +452,8 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
     }
     if (st == FLAME_OK && p.prec == FLAME_FP32_MIXED && h->logn1 >= 8 && h->logn1 <= 12)
         h->has_uv_map = flame::encode_uv_map(&h->uv_map, h->uv, (int)n1, (int)ldk);
+    if (st == FLAME_OK && p.prec == FLAME_FP32_MIXED && h->logm >= 8 && h->logm <= 12)
+        h->has_gk_map = flame::encode_gk_map(&h->gk_map, h->gk, (int)n1, (int)ldk);
     if (st == FLAME_OK) st = autotune(h);
     if (st != FLAME_OK) {
         free_ctx(h);
@@ -538,7 +565,7 @@ flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode
                  : pass == 1 ? Ops<double>::passB(d, s, h->var_b) : Ops<double>::passC(d, s));
     else
         CUDA_TRY(pass == 0 ? Ops<float>::passA(d, s, h->var_a, h->map())
-                 : pass == 1 ? Ops<float>::passB(d, s, h->var_b) : Ops<float>::passC(d, s));
+                 : pass == 1 ? Ops<float>::passB(d, s, h->var_b, h->gmap()) : Ops<float>::passC(d, s));
     return FLAME_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr int kVariantDirect = 1;   // pass A: direct stores (no cluster write-o
 constexpr int kVariantRadix8 = 1;   // pass B: 8 points per thread, 512-thread CTAs
 constexpr int kVariantRadix8A = 2;  // pass A: 8 points per thread, cluster write-out
 constexpr int kVariantTma = 3;      // pass A: column written by tensor stores (FP32)
+constexpr int kVariantTmaB = 2;     // pass B: row pair written by tensor stores (FP32)
 
 // Plain-old-data arguments of the step kernels.
 struct StepArgs {
@@ -95,7 +96,8 @@ template <class R> struct Ops {
     // points per thread)
     static cudaError_t passA(const FlameDesc &d, cudaStream_t s, int variant = 0,
                              const CUtensorMap *uv_map = nullptr);
-    static cudaError_t passB(const FlameDesc &d, cudaStream_t s, int variant = 0);
+    static cudaError_t passB(const FlameDesc &d, cudaStream_t s, int variant = 0,
+                             const CUtensorMap *gk_map = nullptr);
     static cudaError_t passC(const FlameDesc &d, cudaStream_t s);
     static cudaError_t passA_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
                                    int variant = 0);
@@ -116,10 +118,18 @@ template <class R> struct Ops {
 // Row pairs per tensor store of the uv write-out of pass A (<= 256).
 __host__ __device__ constexpr int uv_box_pairs(int n1) { return n1 / 2 < 256 ? n1 / 2 : 256; }
 
+// Column pairs per tensor store of the gk write-out of pass B (<= 256).
+__host__ __device__ constexpr int gk_box_pairs(int ldk) { return (ldk + 1) / 2 < 256 ? (ldk + 1) / 2 : 256; }
+
 // Tensor map of an FP32 uv workspace (n1 rows, ldk columns) for the
 // tensor-store write-out of pass A: dimensions (8 floats of a row pair, k2,
 // row pair), box (8, 1, uv_box_pairs(n1)).  False when the driver has no
 // tensor-map encoder or rejects the map (the variant is then not offered).
 bool encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk);
+// Tensor map of an FP32 gk workspace (n1 rows, ldk columns, the column count
+// rounded up to even) for the tensor-store write-out of pass B: dimensions
+// (8 floats of a row pair and column pair, row pair, column pair), box
+// (8, 1, gk_box_pairs(ldk)).
+bool encode_gk_map(CUtensorMap *map, void *gk, int n1, int ldk);
 
 }  // namespace flame

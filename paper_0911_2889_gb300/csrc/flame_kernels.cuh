@@ -519,7 +519,9 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
 // u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
 // forward with the real-input post-processing; G[k], k <= K2, is written
 // (column-major gk).  G[j1][0] is the row sum of g used for the FP64 mean mode.
-template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+template <class R, int LOG, int E, bool TMA = false>
+__device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf,
+                                           const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -635,6 +637,14 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
 #pragma unroll
     for (int r = 0; r < E; ++r) sm.st_raw(spad_e<E>(t + r * T), x[r]);
     __syncthreads();
+    // Tensor-store write-out (FP32, compile-time lengths): G of the row pair
+    // is staged in the h region (free again: the forward transform has read
+    // it) in the order of the column-pair interleaved gk, complex index
+    // 4 (k/2) + k%2 for row 2p and + 2 for row 2p+1, and the first thread of
+    // the group writes it with tensor stores of gk_box_pairs(ldk) column
+    // pairs.  Other cases store directly.
+    constexpr bool kTma = TMA && std::is_same<R, float>::value && LOG > 0;
+    const bool staged = kTma && (__cvta_generic_to_shared(smraw) & 127) == 0;
 #pragma unroll
     for (int r = 0; r < E / 2; ++r) {
         const int k = t + r * T;
@@ -645,9 +655,22 @@ template <class R, int LOG, int E> __device__ __forceinline__ void passB_body(co
             CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
             C w = realtw(k);
             CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
-            C *dst = gk + gk_index(2 * pair, k, a.n1);  // row 2p+1 two slots further
+            C *dst = staged ? h_first + 4 * (k >> 1) + (k & 1)
+                            : gk + gk_index(2 * pair, k, a.n1);  // row 2p+1 two slots further
             dst[0] = lane0<R>(Y);
             dst[2] = lane1<R>(Y);
+        }
+    }
+    if constexpr (kTma) {
+        if (staged) {
+            fence_async_smem();
+            __syncthreads();
+            if (t == 0 && valid) {
+                const int nq = (a.ldk + 1) >> 1, BQ = gk_box_pairs(a.ldk);
+#pragma unroll 1
+                for (int q0 = 0; q0 < nq; q0 += BQ) tma_store_3d(tm, h_first + 4 * q0, 0, pair, q0);
+                bulk_commit_and_wait_read();
+            }
         }
     }
 }
@@ -842,6 +865,13 @@ template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(F
 }
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d, int pf) {
     passB_body<R, LOG, 16>(d, blockIdx.x, gridDim.x, pf);
+}
+// compile-time length, G written out by tensor stores (FP32); the tensor map
+// describes gk as (8 floats of a row pair and column pair) x row pair x
+// column pair
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBt(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
+    passB_body<R, LOG, 16, true>(d, blockIdx.x, gridDim.x, pf, &tm);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passB8(FlameDesc d, int pf) {

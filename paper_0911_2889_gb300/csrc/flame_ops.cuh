@@ -142,6 +142,7 @@ template <class R> cudaError_t Ops<R>::prepare() {
         set((const void *)k_passAd<R, L>);
         set((const void *)k_passAd_n<R, L>);
         set((const void *)k_passAt<R, L>);
+        set((const void *)k_passBt<R, L>);
         set((const void *)k_passC_n<R, L>);
     });
     set((const void *)k_areaA<R>);
@@ -244,12 +245,18 @@ template <class R> static Geom geom_passB8(int logm, int nlines) {
     return g;
 }
 
-template <class R> cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant) {
+template <class R>
+cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *gk_map) {
     Geom g = geom_passB<R>(d.a.logm, d.a.n1 / 2);
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {
+        if (sizeof(R) == 4 && L > 0 && variant == kVariantTmaB && gk_map) {  // tensor-store write-out
+            Geom gb = g;
+            if (kSharedTw<R, L, 16>) gb.smem += kTwSmemBytes;
+            const int pf = resident_ctas((const void *)k_passBt<R, L>, gb);
+            err = launch_cl(k_passBt<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf, *gk_map);
+        } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {
             const Geom g8 = geom_passB8<R>(L, d.a.n1 / 2);
             const int pf = resident_ctas((const void *)k_passB8<R, L>, g8);
             err = launch_cl(k_passB8<R, L>, dim3(g8.blocks), g8.threads, g8.smem, s, 1, d, pf);
