@@ -332,14 +332,16 @@ def run_ours(args):
     e2e_value = pts * nk / (e2e_ms * 1e-3) * world
     io_bytes = state.numel() * state.element_size() + 16
 
+    # DRAM bytes per launch of the dominant kernel from an ncu capture,
+    # valid only for the kernel sources it was taken on
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
-            tr = json.load(open(prof))
-            key = f"{w['workload']}:pass{'ABC'[dom]}"
-            traffic = tr.get(key)
-        except Exception:
+            entry = json.load(open(prof)).get(f"{w['workload']}:pass{'ABC'[dom]}")
+            if entry and entry.get("csrc_sha256") == kernel_sources_sha256():
+                traffic = entry["dram_bytes_per_launch"]
+        except (OSError, ValueError, KeyError):
             traffic = None
 
     batched = adjoint = None
@@ -426,6 +428,20 @@ def run_suite(args):
             print(json.dumps({"suite": f"fft-pair-{n1}x{n2}-{prec}", "ms": ms, "alg_bytes": alg,
                               "effective_gbs": gbs, "frac_of_hbm": gbs / peak, "peak_kind": kind}), flush=True)
             f.close()
+
+
+def kernel_sources_sha256():
+    """Hash of the CUDA sources (csrc/*.cu, *.cuh, *.h), to tell whether an
+    ncu traffic figure was taken on the kernels that run now."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_0911_2889_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
 
 
 def run_profile(args):
