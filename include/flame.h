@@ -108,6 +108,13 @@ flame_status flame_get_params(flame_t h, flame_params *out);
  * per thread with the write-out by tensor stores.  EINVAL on null pointers. */
 flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant);
 
+/* *enabled = 1 when flame_step with nsteps > 1 runs the column pass of each
+ * step fused with the first column pass of the next (the same arithmetic as
+ * separate steps, one HBM read of the state fewer per step).  Decided by the
+ * autotuner at creation for FP32 grids with 256 <= N1 <= 4096;
+ * FLAME_FUSE=0 disables it.  EINVAL on null pointers. */
+flame_status flame_fused_steps(flame_t h, int *enabled);
+
 /* Number of complex entries of the compact box, (2 K1 + 1) * (K2 + 1). */
 size_t flame_state_len(flame_t h);
 
@@ -144,10 +151,12 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
 /* Enqueues one pass of one step: pass 0 = A (derivatives and column
  * inverse FFT), 1 = B (row inverse FFT, |grad Phi|^2, row forward FFT),
  * 2 = C (column forward FFT, linear operator, Euler update, symmetrization,
- * mean mode, time).  Calling passes 0, 1, 2 in order on one stream is
- * exactly flame_step(h, state, mean_mode, t, 1, stream); the split exists so
- * that each kernel can be timed with events on the launching stream.
- * EINVAL for pass outside 0..2 or null pointers. */
+ * mean mode, time), 3 = C fused with pass A of the next step (only when
+ * flame_fused_steps reports 1, else EUNSUPPORTED).  Calling passes 0, 1, 2
+ * in order on one stream is exactly flame_step(h, state, mean_mode, t, 1,
+ * stream); 0, then (1, 3) n - 1 times, then 1, 2 is exactly flame_step(...,
+ * n, ...).  The split exists so that each kernel can be timed with events on
+ * the launching stream.  EINVAL for pass outside 0..3 or null pointers. */
 flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode, double *t,
                              void *stream);
 

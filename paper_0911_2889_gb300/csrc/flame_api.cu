@@ -2,6 +2,7 @@
 // parameter validation, handle and workspace ownership, twiddle tables,
 // launch sequencing, CUDA-graph capture of multi-step calls, ensembles,
 // error reporting.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -149,6 +150,11 @@ struct flame_ctx {
     bool has_uv_map = false, has_gk_map = false;
     const CUtensorMap *map() const { return has_uv_map ? &uv_map : nullptr; }
     const CUtensorMap *gmap() const { return has_gk_map ? &gk_map : nullptr; }
+    // multi-step runs fuse pass C of each step with pass A of the next
+    bool fuse = false;
+    // L2 persisting window over the caller's state (passes A and C)
+    size_t l2_state_bytes = 0;
+    float l2_state_hit = 0.f;
 };
 
 namespace {
@@ -194,6 +200,7 @@ FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
     d.mean = mean;
     d.t_out = t;
     d.status = h->status;
+    if (h->l2_state_bytes) d.l2_state = flame::L2Window{state, h->l2_state_bytes, h->l2_state_hit};
     return d;
 }
 
@@ -209,14 +216,65 @@ cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
     return Ops<float>::passC(d, s);
 }
 
+// n steps with pass C of each step fused with pass A of the next:
+// A, (B, CA) x (n - 1), B, C.  Same arithmetic as n separate steps.
+cudaError_t enqueue_steps_fused(flame_ctx *h, const FlameDesc &d, int n, cudaStream_t s) {
+    cudaError_t e = Ops<float>::passA(d, s, h->var_a, h->map());
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = Ops<float>::passB(d, s, h->var_b, h->gmap());
+        if (e == cudaSuccess) e = i + 1 < n ? Ops<float>::passCA(d, s, h->map()) : Ops<float>::passC(d, s);
+    }
+    return e;
+}
+
+// The state is written by pass C and read by the next step's pass A (and by
+// the following pass C).  A persisting L2 window over it (a per-launch
+// attribute of passes A and C) keeps it resident while uv and gk stream
+// through the rest of the L2; as it is rewritten in place every step, its
+// lines need not go back to HBM in between.  (A second window over gk, for
+// pass B's writes, measured slower: it leaves too little L2 to pass A's uv
+// stores.)  The set-aside is a limit of this process's context, raised to
+// the state's size when the device allows it and never lowered.
+// FLAME_L2_PERSIST=0 turns the window off.
+void setup_l2_window(flame_ctx *h, size_t state_bytes) {
+    const char *env = getenv("FLAME_L2_PERSIST");
+    if (env && strcmp(env, "0") == 0) return;
+    int max_persist = 0, max_window = 0;
+    if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (max_persist <= 0 || max_window <= 0) return;
+    size_t cur = 0;
+    const size_t want = std::min((size_t)max_persist, state_bytes);
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess ||
+        (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) ||
+        cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cur == 0) return;
+    h->l2_state_bytes = std::min(state_bytes, (size_t)max_window);
+    h->l2_state_hit = (float)std::min(1.0, (double)cur / (double)h->l2_state_bytes);
+}
+
 // ---------------------------------------------------------------- autotuner
 // For FP32 grids with compile-time kernels (N1, N2/2 in 256..4096) the
 // alternative shapes of passes A and B are timed once per (grid, K,
 // precision, device) on scratch buffers, and the fastest is kept for the
 // process.  FLAME_AUTOTUNE=0 keeps the default shapes.
 using TuneKey = std::tuple<int, int, int, int, int, int>;
-std::map<TuneKey, std::pair<int, int>> g_tune;
+std::map<TuneKey, std::tuple<int, int, bool>> g_tune;
 std::mutex g_tune_mu;
+
+// Fusion of pass C with the next pass A needs the FP32 compile-time column
+// kernels and the uv tensor map; FLAME_FUSE=0 disables it.
+bool fuse_allowed(const flame_ctx *h) {
+    const char *env = getenv("FLAME_FUSE");
+    if (env && strcmp(env, "0") == 0) return false;
+    return h->p.prec == FLAME_FP32_MIXED && h->has_uv_map && h->logn1 >= 8 && h->logn1 <= 12;
+}
 
 flame_status autotune(flame_ctx *h) {
     // FLAME_FORCE_VARIANTS=a,b fixes the variants (tests exercise each one)
@@ -228,11 +286,15 @@ flame_status autotune(flame_ctx *h) {
                        : va == 2 ? flame::kVariantRadix8A
                        : va ? flame::kVariantDirect : flame::kVariantDefault;
             h->var_b = vb == 2 ? flame::kVariantTmaB : vb ? flame::kVariantRadix8 : flame::kVariantDefault;
+            h->fuse = fuse_allowed(h);
             return FLAME_OK;
         }
     }
     const char *env = getenv("FLAME_AUTOTUNE");
-    if (env && strcmp(env, "0") == 0) return FLAME_OK;
+    if (env && strcmp(env, "0") == 0) {
+        h->fuse = fuse_allowed(h);
+        return FLAME_OK;
+    }
     if (h->p.prec != FLAME_FP32_MIXED || h->logn1 < 8 || h->logn1 > 12 || h->logm < 8 || h->logm > 12)
         return FLAME_OK;
     const TuneKey key{h->p.n_theta, h->p.n_phi, h->p.K1, h->p.K2, (int)h->p.prec, h->device};
@@ -240,8 +302,9 @@ flame_status autotune(flame_ctx *h) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            h->var_a = it->second.first;
-            h->var_b = it->second.second;
+            h->var_a = std::get<0>(it->second);
+            h->var_b = std::get<1>(it->second);
+            h->fuse = std::get<2>(it->second) && fuse_allowed(h);
             return FLAME_OK;
         }
     }
@@ -266,14 +329,22 @@ flame_status autotune(flame_ctx *h) {
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const FlameDesc d = make_desc(h, st, sc, sc + 1);
+    // pass 0: A, 1: B, 2: C then A (variant), 3: C fused with A
     auto time_it = [&](int pass, int variant, float *ms) -> cudaError_t {
         cudaError_t r = cudaSuccess;
         float total = 0.f;
         for (int rep = 0; rep < 4 && r == cudaSuccess; ++rep) {
             r = cudaEventRecord(e0, h->cap);
-            if (r == cudaSuccess)
-                r = pass == 0 ? Ops<float>::passA(d, h->cap, variant, h->map())
-                              : Ops<float>::passB(d, h->cap, variant, h->gmap());
+            if (r == cudaSuccess) {
+                if (pass == 0) r = Ops<float>::passA(d, h->cap, variant, h->map());
+                else if (pass == 1) r = Ops<float>::passB(d, h->cap, variant, h->gmap());
+                else if (pass == 2) {
+                    r = Ops<float>::passC(d, h->cap);
+                    if (r == cudaSuccess) r = Ops<float>::passA(d, h->cap, variant, h->map());
+                } else {
+                    r = Ops<float>::passCA(d, h->cap, h->map());
+                }
+            }
             if (r == cudaSuccess) r = cudaEventRecord(e1, h->cap);
             if (r == cudaSuccess) r = cudaEventSynchronize(e1);
             float t = 0.f;
@@ -304,10 +375,16 @@ flame_status autotune(flame_ctx *h) {
             h->var_b = v;
         }
     }
+    if (fuse_allowed(h) && e == cudaSuccess) {
+        float sep = 0, fused = 0;
+        e = time_it(2, h->var_a, &sep);
+        if (e == cudaSuccess) e = time_it(3, 0, &fused);
+        if (e == cudaSuccess) h->fuse = fused < sep;
+    }
     cleanup();
     if (e != cudaSuccess) return fail(FLAME_ECUDA, "autotune: %s", cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = {h->var_a, h->var_b};
+    g_tune[key] = std::make_tuple(h->var_a, h->var_b, h->fuse);
     return FLAME_OK;
 }
 
@@ -316,7 +393,10 @@ flame_status capture_steps(flame_ctx *h, const FlameDesc &d, int n, cudaGraphExe
     cudaGraph_t graph = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
-    for (int i = 0; i < n && le == cudaSuccess; ++i) le = enqueue_step(h, d, h->cap);
+    if (h->fuse && n > 1)
+        le = enqueue_steps_fused(h, d, n, h->cap);
+    else
+        for (int i = 0; i < n && le == cudaSuccess; ++i) le = enqueue_step(h, d, h->cap);
     cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
     if (le != cudaSuccess || ee != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -450,6 +530,8 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap);
         if (e != cudaSuccess) st = fail(FLAME_ECUDA, "flame_create: %s", cudaGetErrorString(e));
     }
+    if (st == FLAME_OK)
+        setup_l2_window(h, (2 * (size_t)p.K1 + 1) * ldk * h->csz);
     if (st == FLAME_OK && p.prec == FLAME_FP32_MIXED && h->logn1 >= 8 && h->logn1 <= 12)
         h->has_uv_map = flame::encode_uv_map(&h->uv_map, h->uv, (int)n1, (int)ldk);
     if (st == FLAME_OK && p.prec == FLAME_FP32_MIXED && h->logm >= 8 && h->logm <= 12)
@@ -463,6 +545,12 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
     return FLAME_OK;
 }
 
+flame_status flame_fused_steps(flame_t h, int *enabled) {
+    if (!h || !enabled) return fail(FLAME_EINVAL, "flame_fused_steps: null pointer");
+    *enabled = h->fuse ? 1 : 0;
+    return FLAME_OK;
+}
+
 flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant) {
     if (!h || !pass_a_variant || !pass_b_variant) return fail(FLAME_EINVAL, "flame_tuning: null pointer");
     *pass_a_variant = h->var_a;
@@ -473,6 +561,8 @@ flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant) {
 flame_status flame_destroy(flame_t h) {
     if (!h) return FLAME_OK;
     cudaError_t e = cudaDeviceSynchronize();
+    // persisting lines of this handle's windows go back to normal lines
+    if (h->l2_state_bytes && e == cudaSuccess) e = cudaCtxResetPersistingL2Cache();
     free_ctx(h);
     if (e != cudaSuccess) return fail(FLAME_ECUDA, "flame_destroy: %s", cudaGetErrorString(e));
     return FLAME_OK;
@@ -557,9 +647,14 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, in
 
 flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode, double *t, void *stream) {
     if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step_pass: null pointer");
-    if (pass < 0 || pass > 2) return fail(FLAME_EINVAL, "flame_step_pass: pass=%d not in 0..2", pass);
+    if (pass < 0 || pass > 3) return fail(FLAME_EINVAL, "flame_step_pass: pass=%d not in 0..3", pass);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const FlameDesc d = make_desc(h, state, mean_mode, t);
+    if (pass == 3) {
+        if (!h->fuse) return fail(FLAME_EUNSUPPORTED, "flame_step_pass: no fused column pass for this handle");
+        CUDA_TRY(Ops<float>::passCA(d, s, h->map()));
+        return FLAME_OK;
+    }
     if (h->p.prec == FLAME_FP64)
         CUDA_TRY(pass == 0 ? Ops<double>::passA(d, s, h->var_a)
                  : pass == 1 ? Ops<double>::passB(d, s, h->var_b) : Ops<double>::passC(d, s));

@@ -36,6 +36,12 @@ struct StepArgs {
 // Everything one flame's step passes need: parameters, the caller's state
 // buffers and the handle's tables and workspace.  Passed by value for a
 // single flame, or as a device array indexed by blockIdx.y for an ensemble.
+struct L2Window {
+    const void *base;
+    size_t bytes;
+    float hit;  // fraction of the window's accesses that persist
+};
+
 struct FlameDesc {
     StepArgs a;
     void *state;            // compact box (in place)
@@ -48,6 +54,9 @@ struct FlameDesc {
     double *mean;           // caller's mean mode
     double *t_out;          // caller's t (written by pass C)
     int *status;            // handle's device status word
+    // L2 persisting window over the state for the launches of passes A and
+    // C (a launch attribute, not read by the kernels); bytes = 0: none
+    L2Window l2_state;
 };
 
 // Workspace pointers of the area / adjoint kernels.
@@ -99,6 +108,9 @@ template <class R> struct Ops {
     static cudaError_t passB(const FlameDesc &d, cudaStream_t s, int variant = 0,
                              const CUtensorMap *gk_map = nullptr);
     static cudaError_t passC(const FlameDesc &d, cudaStream_t s);
+    // Pass C of one step fused with pass A of the next (FP32, 256 <= N1 <=
+    // 4096, uv written through uv_map); cudaErrorNotSupported otherwise.
+    static cudaError_t passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap *uv_map);
     static cudaError_t passA_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
                                    int variant = 0);
     static cudaError_t passB_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,

@@ -721,7 +721,9 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
 // is written from its k1 > 0 half and its conjugate mirror; the block owning
 // column 0 sums G[j1][0] in FP64 for the mean mode and advances t.  The state
 // entries of the epilogue are loaded before the transform.
-template <class R, int LOG> __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf) {
+template <class R, int LOG, bool FUSE_A = false>
+__device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf,
+                                           const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -806,6 +808,7 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
     const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
     const R s1 = scale1<R>(a), s2 = scale2<R>(a);
     int bad = 0;
+    C nphi[8][2];  // the updated entries (kept for the fused pass A of the next step)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int r = i < 4 ? i : i + 8;
@@ -815,6 +818,7 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int k2 = c0 + side;
+            nphi[i][side] = C{0, 0};
             const bool ok = in_box && (side == 0 ? va : vb);
             if (!ok) continue;
             if (k2 == 0 && k1 < 0) continue;  // written as the mirror of +k1
@@ -831,6 +835,7 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
             C nw{ph.x + rdt * (om * ph.x + cn * gh.x), ph.y + rdt * (om * ph.y + cn * gh.y)};
             bad |= !(isfinite(nw.x) && isfinite(nw.y));
             col[k1] = nw;
+            nphi[i][side] = nw;
             if (k2 == 0) col[-k1] = C{nw.x, -nw.y};
         }
     }
@@ -840,6 +845,69 @@ template <class R, int LOG> __device__ __forceinline__ void passC_body(const Fla
         if (nl) *d.mean += a.dt * cf.c * mg;
         long n = __double2ll_rn((cf.tn - a.t0) / a.dt);
         *d.t_out = a.t0 + (double)(n + 1) * a.dt;
+    }
+    if constexpr (FUSE_A && std::is_same<R, float>::value && LOG > 0) {
+        // Pass A of the next step (a1, a2) on the two updated columns, from
+        // registers: the same prologue, transform and tensor-store write-out
+        // as k_passAt.  The k2 = 0 column's k1 < 0 half was written by other
+        // threads (the conjugate mirror) and is read back after the barrier,
+        // which also frees the exchange buffer.
+        __syncthreads();
+        if (c0 == 0) {
+#pragma unroll
+            for (int i = 4; i < 8; ++i) {
+                const int k1 = t + (i + 8) * T - N1;
+                if (k1 >= -a.K1) nphi[i][0] = sa[k1];
+            }
+        }
+        const C *__restrict__ tw1a = static_cast<const C *>(d.tw1);
+        float4 *park = reinterpret_cast<float4 *>(base);
+        const bool aligned = (__cvta_generic_to_shared(smraw) & 127) == 0;
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+            const int k2 = c0 + side;
+            const bool valid = side == 0 ? va : vb;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                x[r] = CV<V>{vzero(V{}), vzero(V{})};
+                if (r < 4 || r >= 12) {
+                    const int i = r < 4 ? r : r - 8;
+                    const int n = t + r * T;
+                    const int k1 = (r < 4) ? n : n - N1;
+                    if (!(valid && ((r < 4) ? (n <= a.K1) : (k1 >= -a.K1)))) continue;
+                    C phi = side == 0 ? nphi[i][0] : nphi[i][1];
+                    if (k1 == 0 && k2 == 0) phi = C{0, 0};
+                    const R f = s1 * (R)k1;
+                    x[r] = pack2<R>(C{-f * phi.y, f * phi.x}, phi);  // (i s1 k1 Phi, Phi)
+                }
+            }
+            fft_line<1, LOG>(x, a.logn1, t, sm, tw1a);
+            const R s2k2 = s2 * (R)k2;
+            __syncthreads();  // the transform's last exchange has been read
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int n = t + r * T;
+                C U = lane0<R>(x[r]);
+                C Vb = lane1<R>(x[r]);
+                park[n] = make_float4(U.x, U.y, -s2k2 * Vb.y, s2k2 * Vb.x);
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (!aligned && valid) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int n = t + r * T;
+                    *reinterpret_cast<float4 *>(static_cast<C *>(d.uv) + uv_index(n, k2, a.ldk)) = park[n];
+                }
+            }
+            if (aligned && t == 0 && valid) {
+                constexpr int BP = uv_box_pairs(1 << LOG);
+#pragma unroll 1
+                for (int p0 = 0; p0 < (N1 >> 1); p0 += BP) tma_store_3d(tm, park + 2 * p0, 0, k2, p0);
+                bulk_commit_and_wait_read();
+            }
+            __syncthreads();  // the park may be overwritten by the next transform
+        }
     }
 }
 
@@ -879,6 +947,13 @@ template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passB8(F
 }
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
     passC_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
+}
+// pass C of one step fused with pass A of the next (FP32, compile-time
+// lengths): the updated column pair is transformed back and written to uv
+// by tensor stores (the uv map of k_passAt)
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passCA(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
+    passC_body<R, LOG, true>(d, blockIdx.x, gridDim.x, pf, &tm);
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds, int pf) {

@@ -77,11 +77,13 @@ template <class R, class F> static void with_log(int logn, F &&f) {
 }
 
 // Launch with a thread-block cluster of `cl` CTAs along x (grid.x must be a
-// multiple of cl); cl <= 1 is a plain launch.
+// multiple of cl; cl <= 1: none) and, when w.bytes > 0, an L2 persisting
+// access window over [w.base, w.base + w.bytes) (a fraction w.hit of its
+// accesses persisting, the rest streaming).
 template <class... KArgs, class... Args>
-static cudaError_t launch_cl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t s, int cl,
-                             Args... args) {
-    if (cl <= 1) {
+static cudaError_t launch_w(const L2Window &w, void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
+                            cudaStream_t s, int cl, Args... args) {
+    if (cl <= 1 && w.bytes == 0) {
         kernel<<<grid, threads, smem, s>>>(args...);
         return cudaGetLastError();
     }
@@ -90,14 +92,32 @@ static cudaError_t launch_cl(void (*kernel)(KArgs...), dim3 grid, int threads, s
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    unsigned n = 0;
+    if (cl > 1) {
+        attr[n].id = cudaLaunchAttributeClusterDimension;
+        attr[n].val.clusterDim.x = cl;
+        attr[n].val.clusterDim.y = 1;
+        attr[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    if (w.bytes > 0) {
+        attr[n].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[n].val.accessPolicyWindow.base_ptr = const_cast<void *>(w.base);
+        attr[n].val.accessPolicyWindow.num_bytes = w.bytes;
+        attr[n].val.accessPolicyWindow.hitRatio = w.hit;
+        attr[n].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[n].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        ++n;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = n;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <class... KArgs, class... Args>
+static cudaError_t launch_cl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t s, int cl,
+                             Args... args) {
+    return launch_w(L2Window{nullptr, 0, 0.f}, kernel, grid, threads, smem, s, cl, args...);
 }
 template <class R, int L> static constexpr int cluster_of() {
     return (sizeof(R) == 4 && L > 0) ? Shape<L>::CL : 1;
@@ -143,6 +163,7 @@ template <class R> cudaError_t Ops<R>::prepare() {
         set((const void *)k_passAd_n<R, L>);
         set((const void *)k_passAt<R, L>);
         set((const void *)k_passBt<R, L>);
+        if constexpr (sizeof(R) == 4 && L > 0) set((const void *)k_passCA<R, L>);
         set((const void *)k_passC_n<R, L>);
     });
     set((const void *)k_areaA<R>);
@@ -208,21 +229,21 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
         constexpr int cl = cluster_of<R, L>();
         if (sizeof(R) == 4 && L > 0 && variant == kVariantTma && uv_map) {  // tensor-store write-out
             const int pf = resident_ctas((const void *)k_passAt<R, L>, g);
-            err = launch_cl(k_passAt<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
+            err = launch_w(d.l2_state, k_passAt<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
         } else if (cl > 1 && (variant == kVariantDirect || variant == kVariantTma)) {  // direct stores
             Geom gd = g;
             const int pf = resident_ctas((const void *)k_passAd<R, L>, gd);
-            err = launch_cl(k_passAd<R, L>, dim3(gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
+            err = launch_w(d.l2_state, k_passAd<R, L>, dim3(gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
             const Geom g8 = geom_passA8<R, L>(d.a.K2 + 1);
             constexpr int cl8 = ShapeE<L, 8>::CL;
             const int pf = resident_ctas((const void *)k_passA8<R, L>, g8);
-            err = launch_cl(k_passA8<R, L>, dim3(round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
+            err = launch_w(d.l2_state, k_passA8<R, L>, dim3(round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
         } else {
             // the compile-time kernels assume Shape<L>::G groups per CTA
             Geom gl = cl > 1 ? geom_cols(d.a.logn1, d.a.K2 + 1, Shape<L>::G) : g;
             const int pf = resident_ctas((const void *)k_passA<R, L>, gl);
-            err = launch_cl(k_passA<R, L>, dim3(round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
+            err = launch_w(d.l2_state, k_passA<R, L>, dim3(round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
         }
     });
     if (err != cudaSuccess) return err;
@@ -272,11 +293,28 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
 }
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
     Geom g = geom_cols(d.a.logn1, (d.a.K2 + 2) / 2, 0);
+    cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         const int pf = resident_ctas((const void *)k_passC<R, L>, g);
-        k_passC<R, L><<<g.blocks, g.threads, g.smem, s>>>(d, pf);
+        err = launch_w(d.l2_state, k_passC<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
     });
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+template <class R>
+cudaError_t Ops<R>::passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap *uv_map) {
+    if (sizeof(R) != 4 || !uv_map || d.a.logn1 < 8 || d.a.logn1 > 12) return cudaErrorNotSupported;
+    Geom g = geom_cols(d.a.logn1, (d.a.K2 + 2) / 2, 0);
+    cudaError_t err = cudaErrorNotSupported;
+    with_log<R>(d.a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if constexpr (sizeof(R) == 4 && L > 0) {
+            const int pf = resident_ctas((const void *)k_passCA<R, L>, g);
+            err = launch_w(d.l2_state, k_passCA<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
+        }
+    });
+    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 template <class R>

@@ -54,6 +54,7 @@ SIGNATURES = {
     "flame_get_params": (_i, [_vp, ctypes.POINTER(flame_params)]),
     "flame_state_len": (_sz, [_vp]),
     "flame_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "flame_fused_steps": (_i, [_vp, ctypes.POINTER(_i)]),
     "flame_fft_r2c": (_i, [_vp, _vp, _vp, _vp]),
     "flame_fft_c2r": (_i, [_vp, _vp, _vp, _vp]),
     "flame_step": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
@@ -139,6 +140,14 @@ def flame_tuning(h):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(load().flame_tuning(ctypes.c_void_p(h), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def flame_fused_steps(h):
+    """True when multi-step runs fuse each column pass with the next step's
+    first column pass."""
+    e = ctypes.c_int()
+    _check(load().flame_fused_steps(ctypes.c_void_p(h), ctypes.byref(e)))
+    return bool(e.value)
 
 
 def flame_fft_r2c(h, real_in, spec_out, stream=None):

@@ -243,3 +243,52 @@ def test_autotuner_choice_is_valid_and_cached(fl, monkeypatch):
     assert v1 == v2 and v1[0] in (0, 1, 2, 3) and v1[1] in (0, 1, 2)
     f1.close()
     f2.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [(256, 512), (1024, 2048), (4096, 8192)])
+def test_fused_multi_step_is_bitwise_equal_to_single_steps(fl, monkeypatch, shape):
+    # flame_step(n > 1) runs pass C of each step fused with pass A of the
+    # next; it must give exactly what n separate steps give (state, mean, t)
+    monkeypatch.setenv("FLAME_FORCE_VARIANTS", "3,2")
+    monkeypatch.delenv("FLAME_FUSE", raising=False)
+    n1, n2 = shape
+    f, st0, state, mean, t = _setup(fl, n1, n2, "fp32", 64, 21, amp=1e-2)
+    assert fl.flame_fused_steps(f.h)
+    s2, m2, t2 = state.clone(), mean.clone(), t.clone()
+    f.step(state, mean, t, 6)
+    for _ in range(6):
+        f.step(s2, m2, t2, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(state, s2)
+    assert mean.item() == m2.item() and t.item() == t2.item()
+    f.close()
+
+
+@pytest.mark.gpu
+def test_fusion_can_be_disabled(fl, monkeypatch):
+    monkeypatch.setenv("FLAME_FUSE", "0")
+    f = fl.Flame(512, 1024, prec="fp32")
+    assert not fl.flame_fused_steps(f.h)
+    f.close()
+    g = fl.Flame(128, 256, prec="fp64")
+    assert not fl.flame_fused_steps(g.h)
+    g.close()
+
+
+@pytest.mark.gpu
+def test_l2_persisting_window_changes_no_result(fl, monkeypatch):
+    # the state's L2 window is a cache hint of the pass A / C launches
+    outs = []
+    for mode in ("0", None):
+        if mode is None:
+            monkeypatch.delenv("FLAME_L2_PERSIST", raising=False)
+        else:
+            monkeypatch.setenv("FLAME_L2_PERSIST", mode)
+        f, st0, state, mean, t = _setup(fl, 1024, 2048, "fp32", 64, 17, amp=1e-2)
+        f.step(state, mean, t, 3)
+        torch.cuda.synchronize()
+        outs.append((state.clone(), mean.item(), t.item()))
+        f.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:]
