@@ -27,7 +27,7 @@ template <class R> __device__ __forceinline__ CplxT<R> cmulc(CplxT<R> a, CplxT<R
 // --- area, pass A: columns of (i s1 k1 Phi, Phi with the mean mode) ---------
 // writes uv[j1][k2] = (U, P) with U = synthesis of i s1 k1 Phi and P the
 // column synthesis of Phi (the mean mode at k = 0).
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaA(AdjDesc d) {
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaA(AdjDesc d) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -59,7 +59,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaA
             }
         }
     }
-    line_fft<1>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1), CtaBarrier{});
+    fft_line<1, LOG>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1));
     if (valid) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -73,7 +73,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaA
 // S[-k] = conj S[k] unless `full`) builds the lanes Y_q[k mod M] =
 // S[k] e^{2 pi i k q / N2} (q = 0, 1) and transforms them; lane q of x[r]
 // is then the synthesis at grid point 2m + q, m = t + r T.
-template <class R, class Get>
+template <class R, int LOG, class Get>
 __device__ __forceinline__ void halfband_ifft(CV<typename VecOf<R>::type> (&x)[16], const StepArgs &a, int t,
                                               const CplxT<R> *P, const CplxT<R> *twm, Get get, bool valid,
                                               void *smbase) {
@@ -92,20 +92,20 @@ __device__ __forceinline__ void halfband_ifft(CV<typename VecOf<R>::type> (&x)[1
                        : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
         x[r] = pack2<R>(z, z1);
     }
-    line_fft<1>(x, a.logm, t, sm, twm, CtaBarrier{});
+    fft_line<1, LOG>(x, a.logm, t, sm, twm);
 }
 
 // Forward real transform of two real rows given as h_q[m] = f_q[2m] + i
 // f_q[2m+1] in the lanes of x (q = 0, 1); on return out(k, Y) is called for
 // k = 0..K2 (r < 8) with Y the pair of analyses (lane 0: f_0, lane 1: f_1).
-template <class R, class Out>
+template <class R, int LOG, class Out>
 __device__ __forceinline__ void real_fwd(CV<typename VecOf<R>::type> (&x)[16], const StepArgs &a, int t,
                                          const CplxT<R> *P, const CplxT<R> *twm, void *smbase, bool valid,
                                          Out out) {
     using V = typename VecOf<R>::type;
     const int M = 1 << a.logm, T = M >> 4;
     auto sm = make_planes(static_cast<V *>(smbase), M);
-    line_fft<-1>(x, a.logm, t, sm, twm, CtaBarrier{});
+    fft_line<-1, LOG>(x, a.logm, t, sm, twm);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 16; ++r) sm.st(t + r * T, x[r]);
@@ -129,7 +129,7 @@ __device__ __forceinline__ void real_fwd(CV<typename VecOf<R>::type> (&x)[16], c
 // u + iv from U, V = i s2 k2 P; phi from P; pointwise area terms; forward
 // real transforms of a, b1, b2.  Writes aw[k2][j1] = (hat a, hat b1) and
 // gk[k2][j1] = hat b2 (column-major), rowsum[j1] = sum_x of w R S over the row.
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB(AdjDesc d) {
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB(AdjDesc d) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -148,7 +148,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB
     const R s2 = scale2<R>(a);
     // phi at 2m, 2m+1 (real parts of the two lanes), parked
     CV<V> x[16];
-    halfband_ifft<R>(x, a, t, P, twm,
+    halfband_ifft<R, LOG>(x, a, t, P, twm,
                      [&](int kk, bool pos) {
                          UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
                          return pos ? e.v : C{e.v.x, -e.v.y};
@@ -157,7 +157,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB
 #pragma unroll
     for (int r = 0; r < 16; ++r) park[t + r * T] = C{x[r].re.x, x[r].re.y};
     // u + iv at 2m, 2m+1
-    halfband_ifft<R>(x, a, t, P, twm,
+    halfband_ifft<R, LOG>(x, a, t, P, twm,
                      [&](int kk, bool pos) {
                          UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
                          const R f = s2 * (R)kk;
@@ -194,13 +194,13 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB
     red[t] = part;  // summed by thread 0 after the barriers of real_fwd
     C *aw = static_cast<C *>(d.aw);
     C *gk = static_cast<C *>(d.gk);
-    real_fwd<R>(y, a, t, P, twm, base, valid, [&](int k, CV<V> Y) {
+    real_fwd<R, LOG>(y, a, t, P, twm, base, valid, [&](int k, CV<V> Y) {
         C *dst = aw + 2 * ((size_t)k * a.n1 + row);
         st_uv<R>(dst, lane0<R>(Y), lane1<R>(Y));
     });
 #pragma unroll
     for (int r = 0; r < 16; ++r) y[r] = pack2<R>(hb2[r], C{0, 0});
-    real_fwd<R>(y, a, t, P, twm, base, valid, [&](int k, CV<V> Y) { gk[(size_t)k * a.n1 + row] = lane0<R>(Y); });
+    real_fwd<R, LOG>(y, a, t, P, twm, base, valid, [&](int k, CV<V> Y) { gk[(size_t)k * a.n1 + row] = lane0<R>(Y); });
     if (t == 0 && valid) {
         double s = 0.0;
         for (int i = 0; i < (int)blockDim.x; ++i) s += red[i];
@@ -212,7 +212,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaB
 // forward column transforms of (hat a, hat b1) and hat b2, combination
 // grad = A - i s1 k1 B1 - i s2 k2 B2 on the box; block 0 also reduces the
 // row sums into the area and writes dA/dPhi_0.
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaC(AdjDesc d) {
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaC(AdjDesc d) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -234,7 +234,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaC
         const int n = t + r * T;
         x[r] = pack2<R>(valid ? gk[n] : C{0, 0}, C{0, 0});
     }
-    line_fft<-1>(x, a.logn1, t, sm, tw1, CtaBarrier{});
+    fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
     C B2[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) B2[i] = lane0<R>(x[i < 4 ? i : i + 8]);
@@ -244,7 +244,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaC
         UV<R> e = valid ? ld_uv<R>(aw + 2 * n) : UV<R>{C{0, 0}, C{0, 0}};
         x[r] = pack2<R>(e.u, e.v);
     }
-    line_fft<-1>(x, a.logn1, t, sm, tw1, CtaBarrier{});
+    fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
     C *grad = static_cast<C *>(d.grad);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -273,7 +273,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_areaC
 
 // --- adjoint: column synthesis of lambda (two columns per group) -------------
 // gk[j1][k2] (row-major) = column synthesis of lambda, lambda_0 at k = 0.
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjL(AdjDesc d) {
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjL(AdjDesc d) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -302,7 +302,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjL(
             x[r] = pack2<R>(p, q);
         }
     }
-    line_fft<1>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1), CtaBarrier{});
+    fft_line<1, LOG>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1));
     C *gk = static_cast<C *>(d.gk);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -316,7 +316,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjL(
 // ell from the lambda row (gk), u + iv from uv; q_i = 2 ell d_i phi;
 // forward real transforms of q1 and q2 (paired); writes
 // aw[k2][j1] = (hat q1, -i s2 k2 hat q2) column-major.
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(AdjDesc d) {
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(AdjDesc d) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -334,7 +334,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(
     const C *src = uv + uv_index(valid ? row : 0, 0, a.ldk);  // element kk at src + 4 kk
     const C *lsrc = lrow + (size_t)(valid ? row : 0) * a.ldk;
     CV<V> x[16];
-    halfband_ifft<R>(x, a, t, P, twm,
+    halfband_ifft<R, LOG>(x, a, t, P, twm,
                      [&](int kk, bool pos) {
                          C e = lsrc[kk];
                          return pos ? e : C{e.x, -e.y};
@@ -342,7 +342,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(
                      valid, base);
 #pragma unroll
     for (int r = 0; r < 16; ++r) park[t + r * T] = C{x[r].re.x, x[r].re.y};  // ell(2m), ell(2m+1)
-    halfband_ifft<R>(x, a, t, P, twm,
+    halfband_ifft<R, LOG>(x, a, t, P, twm,
                      [&](int kk, bool pos) {
                          UV<R> e = ld_uv<R>(src + 4 * (size_t)kk);
                          if (pos) return C{e.u.x - e.v.y, e.u.y + e.v.x};
@@ -360,7 +360,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(
     }
     C *aw = static_cast<C *>(d.aw);
     const R s2 = scale2<R>(a);
-    real_fwd<R>(x, a, t, P, twm, base, valid, [&](int k, CV<V> Y) {
+    real_fwd<R, LOG>(x, a, t, P, twm, base, valid, [&](int k, CV<V> Y) {
         C q1 = lane0<R>(Y), q2 = lane1<R>(Y);
         const R f = s2 * (R)k;
         st_uv<R>(aw + 2 * ((size_t)k * a.n1 + row), q1, C{f * q2.y, -f * q2.x});  // -i f q2
@@ -371,7 +371,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjB(
 // forward column transforms of (hat q1, -i k2 hat q2), P = (-i s1 k1 Q1 + Q2)
 // / (N1 N2), lambda update on the box, k2 = 0 column from its k1 > 0 half,
 // dL/dgamma contribution (FP64, one atomic per block).
-template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(AdjDesc d) {
+template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(AdjDesc d) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -398,7 +398,7 @@ template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_adjC(
         cf = step_coef(a, *d.t);
         cfs = coef_r<R>(cf, a);
     }
-    line_fft<-1>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1), CtaBarrier{});
+    fft_line<-1, LOG>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1));
     __syncthreads();  // cfs
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
     const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;

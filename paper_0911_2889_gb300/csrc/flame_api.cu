@@ -140,9 +140,15 @@ struct flame_ctx {
     std::vector<FlameDesc> batch_key;
     int batch_n = 0;
     cudaGraphExec_t batch_exec = nullptr;
-    // adjoint arena (grown on demand by flame_adjoint)
+    // adjoint arena (grown on demand by flame_adjoint) and the graphs of its
+    // calls, keyed by every pointer and size of the call
     void *adj = nullptr;
     size_t adj_cap = 0;
+    struct AdjGraph {
+        std::vector<const void *> key;
+        cudaGraphExec_t exec;
+    };
+    std::vector<AdjGraph> adj_graphs;
     // kernel variants picked by the autotuner for passes A and B
     int var_a = 0, var_b = 0;
     // tensor map of uv for the tensor-store variant of pass A (FP32)
@@ -170,6 +176,7 @@ template <class R> flame_status alloc_tables(flame_ctx *h) {
 void free_ctx(flame_ctx *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto &g : h->adj_graphs) cudaGraphExecDestroy(g.exec);
     if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
     cudaFree(h->batch_desc);
     cudaFree(h->tw1);
@@ -806,6 +813,8 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, c
     const size_t need = nbox * box + 2 * ((size_t)nseg + K) * sizeof(double) + 256;
     if (h->adj_cap < need) {
         CUDA_TRY(cudaDeviceSynchronize());
+        for (auto &g : h->adj_graphs) cudaGraphExecDestroy(g.exec);  // they point into the old arena
+        h->adj_graphs.clear();
         cudaFree(h->adj);
         h->adj = nullptr;
         h->adj_cap = 0;
@@ -825,58 +834,102 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, c
     double *trt = trm + K;
     double *lam0 = h->dscal + 1, *dgam = h->dscal + 2;
     const bool f64 = h->p.prec == FLAME_FP64;
-    auto step1 = [&](void *st, double *m, double *t) -> cudaError_t {
-        return enqueue_step(h, make_desc(h, st, m, t), s);
+    auto step1 = [&](void *st, double *m, double *t, cudaStream_t q) -> cudaError_t {
+        return enqueue_step(h, make_desc(h, st, m, t), q);
     };
-    // forward sweep: checkpoints every K steps
-    if (nseg > 0) {
-        CUDA_TRY(cudaMemcpyAsync(ckpt(0), state0, box, cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(ckm, mean0, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(ckt, t_start, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // The forward sweep, the recomputations and the adjoint steps run on the
+    // handle's arena only (the caller's inputs are copied in before, the
+    // results out after), captured once per (arena, nsteps, ckpt_every) and
+    // replayed as a graph: at small grids the ~10 operations per step would
+    // otherwise be bound by the host's launch rate.
+#define ADJ_TRY(x)                          \
+    do {                                    \
+        const cudaError_t e_ = (x);         \
+        if (e_ != cudaSuccess) return e_;   \
+    } while (0)
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        // forward sweep from ckpt(0): checkpoints every K steps
+        for (int g = 1; g < nseg; ++g) {
+            ADJ_TRY(cudaMemcpyAsync(ckpt(g), ckpt(g - 1), box, cudaMemcpyDeviceToDevice, q));
+            ADJ_TRY(cudaMemcpyAsync(ckm + g, ckm + g - 1, sizeof(double), cudaMemcpyDeviceToDevice, q));
+            ADJ_TRY(cudaMemcpyAsync(ckt + g, ckt + g - 1, sizeof(double), cudaMemcpyDeviceToDevice, q));
+            for (int i = 0; i < K; ++i) ADJ_TRY(step1(ckpt(g), ckm + g, ckt + g, q));
+        }
+        // reverse sweep from lam, lam0 (the final adjoint)
+        ADJ_TRY(cudaMemsetAsync(lam + k0, 0, h->csz, q));
+        ADJ_TRY(cudaMemsetAsync(dgam, 0, sizeof(double), q));
+        flame::AdjDesc d;
+        memset(&d, 0, sizeof d);
+        d.a = h->sa;
+        d.lam = lam;
+        d.lam_out = lam;
+        d.lam0 = lam0;
+        d.uv = h->uv;
+        d.gk = h->gk;
+        d.aw = h->aw;
+        d.dgamma = dgam;
+        d.tw1 = h->tw1;
+        d.twm = h->twm;
+        for (int g = nseg - 1; g >= 0; --g) {
+            const int len = (g == nseg - 1) ? nsteps - g * K : K;
+            ADJ_TRY(cudaMemcpyAsync(traj(0), ckpt(g), box, cudaMemcpyDeviceToDevice, q));
+            ADJ_TRY(cudaMemcpyAsync(trm, ckm + g, sizeof(double), cudaMemcpyDeviceToDevice, q));
+            ADJ_TRY(cudaMemcpyAsync(trt, ckt + g, sizeof(double), cudaMemcpyDeviceToDevice, q));
+            for (int i = 1; i < len; ++i) {
+                ADJ_TRY(cudaMemcpyAsync(traj(i), traj(i - 1), box, cudaMemcpyDeviceToDevice, q));
+                ADJ_TRY(cudaMemcpyAsync(trm + i, trm + i - 1, sizeof(double), cudaMemcpyDeviceToDevice, q));
+                ADJ_TRY(cudaMemcpyAsync(trt + i, trt + i - 1, sizeof(double), cudaMemcpyDeviceToDevice, q));
+                ADJ_TRY(step1(traj(i), trm + i, trt + i, q));
+            }
+            for (int i = len - 1; i >= 0; --i) {
+                d.state = traj(i);
+                d.t = trt + i;
+                if (f64) ADJ_TRY(Ops<double>::adj_step(d, q));
+                else ADJ_TRY(Ops<float>::adj_step(d, q));
+            }
+        }
+        return cudaSuccess;
+    };
+#undef ADJ_TRY
+    if (nseg == 0) {  // no step: the gradient is the final adjoint
+        CUDA_TRY(cudaMemcpyAsync(grad_state0, lambda_T, box, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(grad_mean0, lambda0_T, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemsetAsync(grad_gamma, 0, sizeof(double), s));
+        return FLAME_OK;
     }
-    for (int g = 1; g < nseg; ++g) {
-        CUDA_TRY(cudaMemcpyAsync(ckpt(g), ckpt(g - 1), box, cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(ckm + g, ckm + g - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(ckt + g, ckt + g - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        for (int i = 0; i < K; ++i) CUDA_TRY(step1(ckpt(g), ckm + g, ckt + g));
+    const std::vector<const void *> key{h->adj, reinterpret_cast<const void *>((size_t)nsteps),
+                                        reinterpret_cast<const void *>((size_t)ckpt_every)};
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : h->adj_graphs)
+        if (g.key == key) exec = g.exec;
+    if (!exec) {
+        if (h->adj_graphs.size() >= 4) {  // an evicted graph may still be pending on some stream
+            CUDA_TRY(cudaDeviceSynchronize());
+            cudaGraphExecDestroy(h->adj_graphs.front().exec);
+            h->adj_graphs.erase(h->adj_graphs.begin());
+        }
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = enqueue(h->cap);
+        const cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(FLAME_ECUDA, "flame_adjoint: graph capture failed: %s",
+                        cudaGetErrorString(le != cudaSuccess ? le : ee));
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(FLAME_ECUDA, "flame_adjoint: graph instantiate: %s", cudaGetErrorString(ie));
+        h->adj_graphs.push_back(flame_ctx::AdjGraph{key, exec});
     }
-    // reverse sweep
+    CUDA_TRY(cudaMemcpyAsync(ckpt(0), state0, box, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ckm, mean0, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ckt, t_start, sizeof(double), cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(lam, lambda_T, box, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(lam + k0, 0, h->csz, s));
     CUDA_TRY(cudaMemcpyAsync(lam0, lambda0_T, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(dgam, 0, sizeof(double), s));
-    flame::AdjDesc d;
-    memset(&d, 0, sizeof d);
-    d.a = h->sa;
-    d.lam = lam;
-    d.lam_out = lam;
-    d.lam0 = lam0;
-    d.uv = h->uv;
-    d.gk = h->gk;
-    d.aw = h->aw;
-    d.dgamma = dgam;
-    d.tw1 = h->tw1;
-    d.twm = h->twm;
-    for (int g = nseg - 1; g >= 0; --g) {
-        const int len = (g == nseg - 1) ? nsteps - g * K : K;
-        CUDA_TRY(cudaMemcpyAsync(traj(0), ckpt(g), box, cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(trm, ckm + g, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(trt, ckt + g, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        for (int i = 1; i < len; ++i) {
-            CUDA_TRY(cudaMemcpyAsync(traj(i), traj(i - 1), box, cudaMemcpyDeviceToDevice, s));
-            CUDA_TRY(cudaMemcpyAsync(trm + i, trm + i - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
-            CUDA_TRY(cudaMemcpyAsync(trt + i, trt + i - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
-            CUDA_TRY(step1(traj(i), trm + i, trt + i));
-        }
-        for (int i = len - 1; i >= 0; --i) {
-            d.state = traj(i);
-            d.t = trt + i;
-            if (f64) CUDA_TRY(Ops<double>::adj_step(d, s));
-            else CUDA_TRY(Ops<float>::adj_step(d, s));
-        }
-    }
-    CUDA_TRY(cudaMemcpyAsync(grad_state0, nseg > 0 ? lam : lambda_T, box, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(grad_mean0, nseg > 0 ? lam0 : lambda0_T, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(exec, s));
+    CUDA_TRY(cudaMemcpyAsync(grad_state0, lam, box, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(grad_mean0, lam0, sizeof(double), cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(grad_gamma, dgam, sizeof(double), cudaMemcpyDeviceToDevice, s));
     return FLAME_OK;
 }

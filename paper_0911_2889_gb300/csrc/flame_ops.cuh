@@ -1,8 +1,12 @@
-// flame_ops.cuh -- launch geometry and launchers of the kernels, instantiated
-// once per precision by flame_f32.cu and flame_f64.cu.
+// flame_ops.cuh -- launch geometry and launchers of the kernels.  FP64 is
+// instantiated whole by flame_f64.cu; the FP32 launchers are split over
+// flame_f32_*.cu so that their kernels compile in parallel.
 #pragma once
 
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "flame_adjoint.cuh"
 
@@ -44,9 +48,34 @@ template <class R> static Geom make_geom(int logn, int nlines, int hint, size_t 
     return g;
 }
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum (less its static shared memory), once per kernel and device,
+// before its first launch.
+static cudaError_t opt_in(const void *kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({kernel, dev})) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert({kernel, dev});
+    return e;
+}
+
 // CTAs of one kernel resident at once on the current device: a tile that
 // starts now is followed, one wave later, by tile + resident_ctas.
 static int resident_ctas(const void *kernel, const Geom &g) {
+    if (opt_in(kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     const int nsm = sm_count();
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, g.threads, g.smem) != cudaSuccess) {
@@ -83,6 +112,8 @@ template <class R, class F> static void with_log(int logn, F &&f) {
 template <class... KArgs, class... Args>
 static cudaError_t launch_w(const L2Window &w, void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
                             cudaStream_t s, int cl, Args... args) {
+    const cudaError_t oe = opt_in((const void *)kernel);
+    if (oe != cudaSuccess) return oe;
     if (cl <= 1 && w.bytes == 0) {
         kernel<<<grid, threads, smem, s>>>(args...);
         return cudaGetLastError();
@@ -127,83 +158,35 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { return make_geom<R>(logn, nlines, hint); }
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
-template <class R> cudaError_t Ops<R>::prepare() {
-    static int done_dev = -1;  // the attribute is per function; set once per process
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (done_dev >= 0) return cudaSuccess;
-    int optin = 0;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    auto set = [&](const void *f) {
-        cudaFuncAttributes fa;
-        cudaError_t r = cudaFuncGetAttributes(&fa, f);
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     optin - (int)fa.sharedSizeBytes);
-        if (r != cudaSuccess) e = r;
-    };
-    set((const void *)k_rows_r2c<R>);
-    set((const void *)k_rows_c2r<R>);
-    set((const void *)k_cols<R, -1>);
-    set((const void *)k_cols<R, 1>);
-    for_each_log<R>([&](auto lc) {
-        constexpr int L = decltype(lc)::value;
-        set((const void *)k_passA<R, L>);
-        set((const void *)k_passB<R, L>);
-        set((const void *)k_passC<R, L>);
-        set((const void *)k_passA_n<R, L>);
-        set((const void *)k_passB_n<R, L>);
-        set((const void *)k_passB8<R, L>);
-        set((const void *)k_passB8_n<R, L>);
-        set((const void *)k_passA8<R, L>);
-        set((const void *)k_passA8_n<R, L>);
-        set((const void *)k_passAd<R, L>);
-        set((const void *)k_passAd_n<R, L>);
-        set((const void *)k_passAt<R, L>);
-        set((const void *)k_passBt<R, L>);
-        if constexpr (sizeof(R) == 4 && L > 0) set((const void *)k_passCA<R, L>);
-        set((const void *)k_passC_n<R, L>);
-    });
-    set((const void *)k_areaA<R>);
-    set((const void *)k_areaB<R>);
-    set((const void *)k_areaC<R>);
-    set((const void *)k_adjL<R>);
-    set((const void *)k_adjB<R>);
-    set((const void *)k_adjC<R>);
-    if (e == cudaSuccess) done_dev = dev;
-    return e;
-}
+// Kernels opt in to large dynamic shared memory at their first launch
+// (opt_in); nothing to do ahead of time.
+template <class R> cudaError_t Ops<R>::prepare() { return cudaSuccess; }
 
 template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStream_t s) {
     // radix-16 table, then the radix-8 table (tw_alloc_len entries in all)
     const int len16 = tw_table_len(logN, 4), len8 = tw_table_len(logN, 3);
-    k_twiddles<R><<<(len16 + 255) / 256, 256, 0, s>>>(tab, logN, 4);
-    k_twiddles<R><<<(len8 + 255) / 256, 256, 0, s>>>(tab + len16, logN, 3);
-    return cudaGetLastError();
+    cudaError_t e = launch_cl(k_twiddles<R>, dim3((len16 + 255) / 256), 256, 0, s, 1, tab, logN, 4);
+    if (e == cudaSuccess) e = launch_cl(k_twiddles<R>, dim3((len8 + 255) / 256), 256, 0, s, 1, tab + len16, logN, 3);
+    return e;
 }
 
 template <class R>
 cudaError_t Ops<R>::rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s) {
     Geom g = geom_rows(logm, n1 / 2, 0);
-    k_rows_r2c<R><<<g.blocks, g.threads, g.smem, s>>>(in, out, n1, logm, tw);
-    return cudaGetLastError();
+    return launch_cl(k_rows_r2c<R>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, n1, logm, tw);
 }
 
 template <class R>
 cudaError_t Ops<R>::rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s) {
     Geom g = geom_rows(logm, n1 / 2, 0);
-    k_rows_c2r<R><<<g.blocks, g.threads, g.smem, s>>>(in, out, n1, logm, tw);
-    return cudaGetLastError();
+    return launch_cl(k_rows_c2r<R>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, n1, logm, tw);
 }
 
 template <class R>
 cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw, cudaStream_t s) {
     Geom g = geom_cols(logn, (ncols + 1) / 2, 0);
-    if (dir < 0) k_cols<R, -1><<<g.blocks, g.threads, g.smem, s>>>(in, out, logn, ncols, ld, tw);
-    else k_cols<R, 1><<<g.blocks, g.threads, g.smem, s>>>(in, out, logn, ncols, ld, tw);
-    return cudaGetLastError();
+    if (dir < 0) return launch_cl(k_cols<R, -1>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, logn, ncols, ld, tw);
+    return launch_cl(k_cols<R, 1>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, logn, ncols, ld, tw);
 }
 
 // pass A with 8 points per thread (compile-time length 2^L): fixed shape
@@ -358,11 +341,12 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
 template <class R>
 cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
+    cudaError_t e = cudaSuccess;
     with_log<R>(a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        k_passC_n<R, L><<<dim3(g.blocks, n), g.threads, g.smem, s>>>(ds, 0);
+        e = launch_cl(k_passC_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
     });
-    return cudaGetLastError();
+    return e;
 }
 
 // one row per CTA (N2/32 threads): exchange buffer + one parked row
@@ -374,14 +358,26 @@ template <class R> static Geom geom_row1(int logm, int nrows) {
     return g;
 }
 
+// The area and adjoint kernels take the column length (log2 N1) or the
+// half row length (log2 N2/2) as their compile-time LOG (0: any length).
 template <class R> cudaError_t Ops<R>::area(const AdjDesc &d, cudaStream_t s) {
     const StepArgs &a = d.a;
     Geom ga = geom_cols(a.logn1, a.K2 + 1, 0);
-    k_areaA<R><<<ga.blocks, ga.threads, ga.smem, s>>>(d);
     Geom gb = geom_row1<R>(a.logm, a.n1);
-    k_areaB<R><<<gb.blocks, gb.threads, gb.smem, s>>>(d);
-    k_areaC<R><<<ga.blocks, ga.threads, ga.smem, s>>>(d);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    with_log<R>(a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        e = launch_cl(k_areaA<R, L>, dim3(ga.blocks), ga.threads, ga.smem, s, 1, d);
+    });
+    with_log<R>(a.logm, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (e == cudaSuccess) e = launch_cl(k_areaB<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d);
+    });
+    with_log<R>(a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (e == cudaSuccess) e = launch_cl(k_areaC<R, L>, dim3(ga.blocks), ga.threads, ga.smem, s, 1, d);
+    });
+    return e;
 }
 
 template <class R> cudaError_t Ops<R>::adj_step(const AdjDesc &d, cudaStream_t s) {
@@ -392,14 +388,24 @@ template <class R> cudaError_t Ops<R>::adj_step(const AdjDesc &d, cudaStream_t s
     f.state = const_cast<void *>(d.state);
     f.uv = d.uv;
     f.tw1 = d.tw1;
-    Geom ga = geom_cols(a.logn1, a.K2 + 1, 0);
-    k_passA<R, 0><<<ga.blocks, ga.threads, ga.smem, s>>>(f, 0);
+    cudaError_t e = passA(f, s, kVariantDirect);  // compile-time kernel with direct stores where there is one
+    if (e != cudaSuccess) return e;
     Geom gl = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
-    k_adjL<R><<<gl.blocks, gl.threads, gl.smem, s>>>(d);
     Geom gb = geom_row1<R>(a.logm, a.n1);
-    k_adjB<R><<<gb.blocks, gb.threads, gb.smem, s>>>(d);
-    k_adjC<R><<<ga.blocks, ga.threads, ga.smem, s>>>(d);
-    return cudaGetLastError();
+    Geom ga = geom_cols(a.logn1, a.K2 + 1, 0);
+    with_log<R>(a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        e = launch_cl(k_adjL<R, L>, dim3(gl.blocks), gl.threads, gl.smem, s, 1, d);
+    });
+    with_log<R>(a.logm, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (e == cudaSuccess) e = launch_cl(k_adjB<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d);
+    });
+    with_log<R>(a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (e == cudaSuccess) e = launch_cl(k_adjC<R, L>, dim3(ga.blocks), ga.threads, ga.smem, s, 1, d);
+    });
+    return e;
 }
 
 }  // namespace flame
