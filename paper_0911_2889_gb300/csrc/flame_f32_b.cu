@@ -3,5 +3,6 @@
 
 namespace flame {
 template cudaError_t Ops<float>::passB(const FlameDesc &, cudaStream_t, int, const CUtensorMap *);
-template cudaError_t Ops<float>::passB_batch(const FlameDesc *, int, const StepArgs &, cudaStream_t, int);
+template cudaError_t Ops<float>::passB_batch(const FlameDesc *, int, const StepArgs &, cudaStream_t, int,
+                                             const CUtensorMap *);
 }  // namespace flame

@@ -111,10 +111,12 @@ template <class R> struct Ops {
     // Pass C of one step fused with pass A of the next (FP32, 256 <= N1 <=
     // 4096, uv written through uv_map); cudaErrorNotSupported otherwise.
     static cudaError_t passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap *uv_map);
+    // maps (nullable): per-flame tensor maps in device memory (uv maps for
+    // pass A, gk maps for pass B) for the tensor-store variants
     static cudaError_t passA_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
-                                   int variant = 0);
+                                   int variant = 0, const CUtensorMap *maps = nullptr);
     static cudaError_t passB_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
-                                   int variant = 0);
+                                   int variant = 0, const CUtensorMap *maps = nullptr);
     static cudaError_t passC_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
     // geometry used by the step passes (for the autotuner and the tests)
     static Geom geom_cols(int logn, int nlines, int groups_hint);

@@ -298,6 +298,12 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, const void *
                  "r"(sa), "r"(x), "r"(y), "r"(z)
                  : "memory");
 }
+// A tensor map read from global memory (one per flame of an ensemble) is
+// made visible to the tensor-map proxy before its first use.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<unsigned long long>(tm))
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit_and_wait_read() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -377,7 +383,7 @@ template <int E> struct ShapeE<0, E> {  // runtime-length kernels: no clusters
 // r = 4..11 of the first pass are always zero and are dropped at compile
 // time).  Writes uv[j1][k2] = (U, V) with U = synthesis of a, V = i s2 k2 x
 // synthesis of b.
-template <class R, int LOG, int E, bool CLU = true, bool TMA = false>
+template <class R, int LOG, int E, bool CLU = true, bool TMA = false, bool GMAP = false>
 __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
@@ -496,6 +502,7 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
         }
         if (aligned && t == 0 && valid) {
             constexpr int BP = uv_box_pairs(1 << LOG);
+            if constexpr (GMAP) tensormap_acquire(tm);
 #pragma unroll 1
             for (int p0 = 0; p0 < (N1 >> 1); p0 += BP) tma_store_3d(tm, park + 2 * p0, 0, k2, p0);
             bulk_commit_and_wait_read();
@@ -519,7 +526,7 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
 // u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
 // forward with the real-input post-processing; G[k], k <= K2, is written
 // (column-major gk).  G[j1][0] is the row sum of g used for the FP64 mean mode.
-template <class R, int LOG, int E, bool TMA = false>
+template <class R, int LOG, int E, bool TMA = false, bool GMAP = false>
 __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
@@ -667,6 +674,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
             __syncthreads();
             if (t == 0 && valid) {
                 const int nq = (a.ldk + 1) >> 1, BQ = gk_box_pairs(a.ldk);
+                if constexpr (GMAP) tensormap_acquire(tm);
 #pragma unroll 1
                 for (int q0 = 0; q0 < nq; q0 += BQ) tma_store_3d(tm, h_first + 4 * q0, 0, pair, q0);
                 bulk_commit_and_wait_read();
@@ -970,6 +978,18 @@ __global__ void __launch_bounds__(512, 2) k_passA8_n(const FlameDesc *__restrict
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB_n(const FlameDesc *__restrict__ ds, int pf) {
     passB_body<R, LOG, 16>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+// ensembles with the tensor-store write-outs: maps[flame] is the flame's
+// uv map (pass A) or gk map (pass B), in global memory
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAt_n(const FlameDesc *__restrict__ ds, int pf,
+                                                               const CUtensorMap *maps) {
+    passA_body<R, LOG, 16, false, true, true>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf, maps + blockIdx.y);
+}
+template <class R, int LOG>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBt_n(const FlameDesc *__restrict__ ds, int pf,
+                                                               const CUtensorMap *maps) {
+    passB_body<R, LOG, 16, true, true>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf, maps + blockIdx.y);
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(512, 2) k_passB8_n(const FlameDesc *__restrict__ ds, int pf) {

@@ -301,13 +301,16 @@ cudaError_t Ops<R>::passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap
     return cudaGetLastError();
 }
 template <class R>
-cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant) {
+cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
+                                const CUtensorMap *maps) {
     Geom g = geom_cols(a.logn1, a.K2 + 1, 0);
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         constexpr int cl = cluster_of<R, L>();
-        if (cl > 1 && (variant == kVariantDirect || variant == kVariantTma)) {  // (no tensor maps per flame)
+        if (sizeof(R) == 4 && L > 0 && variant == kVariantTma && maps) {
+            err = launch_cl(k_passAt_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0, maps);
+        } else if (cl > 1 && (variant == kVariantDirect || variant == kVariantTma)) {
             err = launch_cl(k_passAd_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
             const Geom g8 = geom_passA8<R, L>(a.K2 + 1);
@@ -322,12 +325,16 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
     return cudaGetLastError();
 }
 template <class R>
-cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant) {
+cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
+                                const CUtensorMap *maps) {
     Geom g = geom_passB<R>(a.logm, a.n1 / 2);
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {
+        if (sizeof(R) == 4 && L > 0 && variant == kVariantTmaB && maps) {
+            const size_t sm = g.smem + (kSharedTw<R, L, 16> ? kTwSmemBytes : 0);
+            err = launch_cl(k_passBt_n<R, L>, dim3(g.blocks, n), g.threads, sm, s, 1, ds, 0, maps);
+        } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {
             const Geom g8 = geom_passB8<R>(L, a.n1 / 2);
             err = launch_cl(k_passB8_n<R, L>, dim3(g8.blocks, n), g8.threads, g8.smem, s, 1, ds, 0);
         } else {

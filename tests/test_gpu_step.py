@@ -219,6 +219,36 @@ def test_batch_equals_individual(fl, prec):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("variants", ["3,2", "1,0", None])
+def test_batch_of_compile_time_grids_equals_individual(fl, monkeypatch, variants):
+    # grids with compile-time kernels: the ensemble runs the grouped kernels
+    # (with per-flame tensor maps for the tensor-store variants 3 and 2)
+    if variants is None:
+        monkeypatch.delenv("FLAME_FORCE_VARIANTS", raising=False)
+    else:
+        monkeypatch.setenv("FLAME_FORCE_VARIANTS", variants)
+    monkeypatch.setenv("FLAME_BATCH_TMA", "1" if variants == "3,2" else "0")
+    shapes = [(256, 512), (512, 1024), (256, 512), (1024, 2048)]
+    fs, ss, ms, ts, ref = [], [], [], [], []
+    for i, (n1, n2) in enumerate(shapes):
+        f, st0, state, mean, t = _setup(fl, n1, n2, "fp32", 32, 200 + i, amp=1e-2, gamma=0.7 + 0.05 * i)
+        fs.append(f)
+        ss.append(state)
+        ms.append(mean)
+        ts.append(t)
+        ref.append((state.clone(), mean.clone(), t.clone()))
+    fl.flame_step_batch([f.h for f in fs], ss, ms, ts, nsteps=3)
+    for f, (s, m, t) in zip(fs, ref):
+        f.step(s, m, t, 3)
+    torch.cuda.synchronize()
+    for i in range(len(fs)):
+        assert torch.equal(ss[i], ref[i][0]), i
+        assert torch.equal(ms[i], ref[i][1]) and torch.equal(ts[i], ref[i][2])
+    for f in fs:
+        f.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("variants", ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2"])
 @pytest.mark.parametrize("shape", [(256, 512), (1024, 2048), (4096, 8192)])
 def test_every_tuned_variant_matches_oracle(fl, orc, monkeypatch, variants, shape):
