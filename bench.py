@@ -423,7 +423,7 @@ def run_suite(args):
         ms = _ev_time(lambda: f.step(st, m, t, nsteps), s)
         f.sync_status()
         esz = 16 if prec == "fp64" else 8
-        gbs = sum(pass_bytes(n1, n2, f.K1, f.K2, esz)) / (ms * 1e-3 / nsteps) / 1e9
+        gbs = sum(pass_bytes(n1, n2, f.K1, f.K2, esz)[:3]) / (ms * 1e-3 / nsteps) / 1e9  # passes A, B, C
         print(json.dumps({"suite": f"trajectory-{n1}x{n2}-{prec}", "steps": nsteps, "ms_per_step": ms / nsteps,
                           "points_per_s": n1 * n2 * nsteps / (ms * 1e-3), "effective_gbs": gbs,
                           "note": "graph-captured; L2-resident" if n1 * n2 <= 2 ** 21 else "graph-captured"}),

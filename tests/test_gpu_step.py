@@ -322,3 +322,29 @@ def test_l2_persisting_window_changes_no_result(fl, monkeypatch):
         f.close()
     assert torch.equal(outs[0][0], outs[1][0])
     assert outs[0][1:] == outs[1][1:]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+@pytest.mark.parametrize("shape", [(128, 256), (1024, 2048)])
+def test_linear_only_matches_discrete_product(fl, prec, tol, shape):
+    # the GPU path against the closed form of the linear Euler step (no
+    # oracle involved): Phi_k(t_n) = Phi_k(t0) prod_m (1 + dt omega_k(t_m)),
+    # omega = -|kappa|^2 / t_m^2 + gamma |kappa| / (2 t_m)
+    n1, n2 = shape
+    gamma, t0, dt, n = 0.8, 200.0, 1e-3, 25
+    f, st0, state, mean, t = _setup(fl, n1, n2, prec, 32, 5, amp=1e-2, gamma=gamma, flags=fl.FLAME_LINEAR_ONLY)
+    f.step(state, mean, t, n)
+    torch.cuda.synchronize()
+    K1, K2 = f.K1, f.K2
+    k1 = np.arange(-K1, K1 + 1)[:, None].astype(float)
+    k2 = np.arange(K2 + 1)[None, :].astype(float)
+    kap = np.hypot(k1, k2)
+    fac = np.ones((2 * K1 + 1, K2 + 1))
+    for m in range(n):
+        r0 = t0 + m * dt
+        fac *= 1.0 + dt * (-kap * kap / (r0 * r0) + gamma * kap / (2.0 * r0))
+    want = st0 * fac
+    assert _box_err(_host(fl, state), want, K1) < tol
+    assert t.item() == t0 + n * dt
+    f.close()

@@ -217,3 +217,27 @@ def test_area_gradient_fd(orc):
         assert abs(fd - an) <= 1e-5 * max(abs(an), 1.0)
     fdm = (orc.area(p, st, 0.3 + h, 10.0) - orc.area(p, st, 0.3 - h, 10.0)) / (2 * h)
     assert abs(fdm - gm) < 1e-6 * abs(gm)
+
+
+@pytest.mark.parametrize("gamma,t0,dt", [(0.8, 200.0, 1e-3), (0.5, 3.0, 0.01)])
+def test_linear_only_matches_discrete_product(orc, gamma, t0, dt):
+    # FLAME_LINEAR_ONLY with explicit Euler: every mode is multiplied by
+    # (1 + dt omega_k(t_m)) at t_m = t0 + m dt, r0 = t_m, with
+    # omega = -|kappa|^2 / r0^2 + gamma |kappa| / (2 r0) (the linear part of
+    # eq. (SivCurv1c)), so after n steps Phi_k(t_n) = Phi_k(t0) prod_m (...)
+    p = orc.Params(32, 64, t0=t0, dt=dt, gamma=gamma, s1=1.0, s2=0.5, flags=orc.LINEAR_ONLY)
+    st = _rand_state(p, 9, amp=0.1)
+    n = 37
+    out, mean, t = orc.step(p, st, 0.5, t0, n)
+    k1 = np.arange(-p.K1, p.K1 + 1)[:, None].astype(float)
+    k2 = np.arange(p.K2 + 1)[None, :].astype(float)
+    kap = np.sqrt((1.0 * k1) ** 2 + (0.5 * k2) ** 2)
+    fac = np.ones(p.box_shape)
+    for m in range(n):
+        r0 = t0 + m * dt
+        fac *= 1.0 + dt * (-kap * kap / (r0 * r0) + gamma * kap / (2.0 * r0))
+    want = st * fac
+    want[p.K1, 0] = 0
+    assert _rel(out, want) < 1e-13
+    assert mean == 0.5              # no nonlinear term: the mean mode stays
+    assert t == t0 + n * dt
