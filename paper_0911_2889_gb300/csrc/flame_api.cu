@@ -67,7 +67,7 @@ constexpr int kGraphCache = 8;
 void flame::set_last_error(const char *msg) { g_err = msg; }
 
 namespace {
-// the driver's tensor-map encoder, looked up once (null when unavailable)
+// the CUDA driver's tensor-map encoder, looked up once (null when unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;

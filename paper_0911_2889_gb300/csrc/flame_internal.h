@@ -137,7 +137,7 @@ __host__ __device__ constexpr int gk_box_pairs(int ldk) { return (ldk + 1) / 2 <
 
 // Tensor map of an FP32 uv workspace (n1 rows, ldk columns) for the
 // tensor-store write-out of pass A: dimensions (8 floats of a row pair, k2,
-// row pair), box (8, 1, uv_box_pairs(n1)).  False when the driver has no
+// row pair), box (8, 1, uv_box_pairs(n1)).  False when the CUDA driver has no
 // tensor-map encoder or rejects the map (the variant is then not offered).
 bool encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk);
 // Tensor map of an FP32 gk workspace (n1 rows, ldk columns, the column count
