@@ -154,7 +154,9 @@ def test_adjoint_graph_replay_is_exact_and_independent_of_buffers(fl, prec):
     # flame_adjoint captures its work once per (arena, nsteps, ckpt_every) and
     # replays it; the caller's buffers are copied in and out around the graph,
     # so a second call with other input and output tensors must reproduce the
-    # first bit for bit, and a call with another input must follow that input
+    # first bit for bit, and a call with another input must follow that input.
+    # dL/dgamma is summed over CTAs with FP64 atomics, whose order varies from
+    # run to run: it is held to rounding (1e-14 relative), the rest exactly.
     n1, n2, nsteps, ckpt = 64, 128, 9, 4
     f = fl.Flame(n1, n2, prec=prec, t0=5.0, dt=0.05, gamma=0.8)
     st0 = _dev(fl, inputs.spectrum_ic(n1, n2, 8, seed=6, amp=0.2, K1=f.K1, K2=f.K2), f)
@@ -165,14 +167,16 @@ def test_adjoint_graph_replay_is_exact_and_independent_of_buffers(fl, prec):
     g1, gm1, gg1 = g1.clone(), gm1.item(), gg1.item()
     g2, gm2, gg2 = f.adjoint(st0.clone(), _d(0.1), _d(5.0), nsteps, ckpt, lam.clone(), lam0.clone())
     torch.cuda.synchronize()
-    assert torch.equal(g1, g2) and gm1 == gm2.item() and gg1 == gg2.item()
+    assert torch.equal(g1, g2) and gm1 == gm2.item()
+    assert abs(gg1 - gg2.item()) <= 1e-14 * abs(gg1)
     # another starting state through the same cached graph
     st1 = _dev(fl, inputs.spectrum_ic(n1, n2, 8, seed=7, amp=0.2, K1=f.K1, K2=f.K2), f)
     g3, _, gg3 = f.adjoint(st1, _d(0.1), _d(5.0), nsteps, ckpt, lam, lam0)
     fresh = fl.Flame(n1, n2, prec=prec, t0=5.0, dt=0.05, gamma=0.8)
     g4, _, gg4 = fresh.adjoint(st1, _d(0.1), _d(5.0), nsteps, ckpt, lam, lam0)
     torch.cuda.synchronize()
-    assert torch.equal(g3, g4) and gg3.item() == gg4.item()
+    assert torch.equal(g3, g4)
+    assert abs(gg3.item() - gg4.item()) <= 1e-14 * abs(gg4.item())
     assert not torch.equal(g3, g1)
     f.close()
     fresh.close()
