@@ -728,7 +728,7 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
 // 1/(N1 N2) -> ghat; Phi <- Phi + dt (omega Phi + c ghat); the k2 = 0 column
 // is written from its k1 > 0 half and its conjugate mirror; the block owning
 // column 0 sums G[j1][0] in FP64 for the mean mode and advances t.  The state
-// entries of the epilogue are loaded before the transform.
+// entries of the epilogue are loaded after the transform.
 template <class R, int LOG, bool FUSE_A = false>
 __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
@@ -784,16 +784,6 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     // state entries this thread updates: rows r < 4 (k1 = n) and r >= 12
     // (k1 = n - N1) of columns c0 and c0 + 1
     C *sa = state + (size_t)c0 * ld1 + a.K1, *sb = sa + ld1;
-    C phi[8][2];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int r = i < 4 ? i : i + 8;
-        const int n = t + r * T;
-        const int k1 = (r < 4) ? n : n - N1;
-        const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
-        phi[i][0] = (in_box && va) ? sa[k1] : C{0, 0};
-        phi[i][1] = (in_box && vb) ? sb[k1] : C{0, 0};
-    }
     if (tile == 0) {  // block-uniform: FP64 row-sum reduction of column 0 (any block size)
         red[threadIdx.x] = colsum;
         __syncthreads();
@@ -812,6 +802,18 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     }
 
     __syncthreads();  // cfs (the transform may have no barrier for short lines)
+    // the state entries, read after the transform (they are L2-resident in
+    // the persisting window; holding them across the transform cost more)
+    C phi[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = i < 4 ? i : i + 8;
+        const int n = t + r * T;
+        const int k1 = (r < 4) ? n : n - N1;
+        const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
+        phi[i][0] = (in_box && va) ? sa[k1] : C{0, 0};
+        phi[i][1] = (in_box && vb) ? sb[k1] : C{0, 0};
+    }
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
     const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
     const R s1 = scale1<R>(a), s2 = scale2<R>(a);
