@@ -79,6 +79,8 @@ def test_fp64_128x256_100_step_trajectory(fl, orc, gamma, seed):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 @pytest.mark.parametrize("shape,K,s", [
     ((16, 32), (0, 0), (1.0, 1.0)),      # smallest grid
+    ((16, 32), (1, 1), (1.0, 1.0)),      # smallest retained box (3 x 2 entries)
+    ((1024, 64), (1, 15), (1.0, 1.0)),   # one k1 harmonic on a tall grid
     ((32, 64), (5, 3), (1.0, 1.0)),      # truncation below the padding limit
     ((64, 32), (0, 0), (2.0, 0.5)),      # anisotropic kappa, N1 > N2
     ((256, 512), (0, 0), (1.0, 1.0)),
