@@ -90,7 +90,17 @@ typedef struct flame_ctx *flame_t;
 /* Creates a handle: validates params (EINVAL / EUNSUPPORTED), resolves K and
  * s, builds the FP64-generated twiddle tables and allocates the workspace on
  * the current CUDA device (ENOMEM, ECUDA).  *out is set only on success.
- * Synchronises the device. */
+ * Synchronises the device.
+ *
+ * It also tunes the handle (see flame_tuning, flame_fused_steps) and, unless
+ * FLAME_L2_PERSIST=0, raises this process's persisting-L2 set-aside
+ * (cudaLimitPersistingL2CacheSize, a limit of the CUDA context) to the
+ * state's size where the device allows it: the column passes then launch
+ * with a persisting access window over the caller's state, which is a cache
+ * hint only (results are identical either way).  Environment: FLAME_AUTOTUNE=0
+ * keeps the default kernel variants, FLAME_FORCE_VARIANTS=a,b fixes them,
+ * FLAME_FUSE=0 keeps the column passes of consecutive steps separate,
+ * FLAME_BATCH_TMA=1 lets flame_step_batch use the tensor-store variants. */
 flame_status flame_create(const flame_params *params, flame_t *out);
 
 /* Destroys a handle (NULL is accepted).  Synchronises the device. */
