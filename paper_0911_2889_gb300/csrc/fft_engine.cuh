@@ -247,6 +247,8 @@ template <> struct Planes<double2> {
     double2 *re, *im;
     int len;
     __device__ __forceinline__ Planes(double2 *base, int n) : re(base), im(base + plane_len(n)) {}
+    // planes of `plane` slots each (the radix-8 padding needs plane_len_e<8>)
+    __device__ __forceinline__ Planes(double2 *base, int n, int plane) : re(base), im(base + plane) {}
     __device__ __forceinline__ void st(int i, CV<double2> v) const { re[spad(i)] = v.re; im[spad(i)] = v.im; }
     __device__ __forceinline__ CV<double2> ld(int i) const { return {re[spad(i)], im[spad(i)]}; }
     __device__ __forceinline__ void st_raw(int j, CV<double2> v) const { re[j] = v.re; im[j] = v.im; }
@@ -255,6 +257,13 @@ template <> struct Planes<double2> {
 // Exchange buffer of a group: `base` points at 2 * plane_len(n) V slots.
 __device__ __forceinline__ Planes<float2> make_planes(float2 *base, int n) { return Planes<float2>(base); }
 __device__ __forceinline__ Planes<double2> make_planes(double2 *base, int n) { return Planes<double2>(base, n); }
+// exchange buffer of a radix-E transform (E = 8 pads one slot every 8)
+template <int E> __device__ __forceinline__ Planes<float2> make_planes_e(float2 *base, int n) {
+    return Planes<float2>(base);
+}
+template <int E> __device__ __forceinline__ Planes<double2> make_planes_e(double2 *base, int n) {
+    return Planes<double2>(base, n, plane_len_e<E>(n));
+}
 
 // Loads the twiddle of a table entry (stored with + sign) for direction DIR.
 template <int DIR, class C> __device__ __forceinline__ void load_tw(const C *tab, int i, decltype(C::x) &wr,

@@ -403,7 +403,7 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
     const int k2 = tile * G + g;
     const bool valid = k2 <= a.K2;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len_e<E>(N1);
-    auto sm = make_planes(base, N1);
+    auto sm = make_planes_e<E>(base, N1);
     constexpr bool STW = false;  // pass A's twiddles stay in L1 (measured faster)
     C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * 2 * plane_len_e<E>(N1));
     if constexpr (STW) TwShared<C>::template fill<(STW ? LOG : 8)>(stw, tw1);  // synced by the transform
@@ -547,7 +547,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     // per group: the exchange buffer, then M entries of C (sizeof(C) ==
     // sizeof(V) in both precisions)
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len_e<E>(M) + M);
-    auto sm = make_planes(base, M);  // (E = 8 uses its own padding: st_raw/ld_raw)
+    auto sm = make_planes_e<E>(base, M);  // (E = 8 pads one slot every 8: st_raw/ld_raw)
     const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
     if (tile == 0 && threadIdx.x == 0) *d.t_copy = *d.t_in;
     constexpr bool STW = kSharedTw<R, LOG, E>;
@@ -729,18 +729,20 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
 // is written from its k1 > 0 half and its conjugate mirror; the block owning
 // column 0 sums G[j1][0] in FP64 for the mean mode and advances t.  The state
 // entries of the epilogue are loaded after the transform.
-template <class R, int LOG, bool FUSE_A = false>
+template <class R, int LOG, bool FUSE_A = false, int E = 16>
 __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
+    static_assert(E == 16 || (E == 8 && !FUSE_A), "E points per thread: 16, or 8 without the fused pass A");
+    constexpr int QE = E / 4;  // band registers: r < QE (k1 >= 0) and r >= E - QE (k1 < 0)
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[256];  // one per thread (blockDim <= 256)
     const StepArgs &a = d.a;
     const C *__restrict__ gk = static_cast<const C *>(d.gk);
     C *__restrict__ state = static_cast<C *>(d.state);
     const C *__restrict__ tw1 = static_cast<const C *>(d.tw1);
-    const int N1 = LOG > 0 ? (1 << LOG) : (1 << a.logn1), T = N1 >> 4;
+    const int N1 = LOG > 0 ? (1 << LOG) : (1 << a.logn1), T = N1 / E;
     const int G = blockDim.x / T, g = threadIdx.x / T, t = threadIdx.x % T;
     const int ld1 = 2 * a.K1 + 1;
     if (threadIdx.x == 0 && pf > 0 && tile + pf < ntiles) {
@@ -758,16 +760,16 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     }
     const int c0 = 2 * (tile * G + g);
     const bool va = c0 <= a.K2, vb = c0 + 1 <= a.K2;
-    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(N1);
-    auto sm = make_planes(base, N1);
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len_e<E>(N1);
+    auto sm = make_planes_e<E>(base, N1);
     constexpr bool STW = false;  // pass C's twiddles stay in L1 (measured faster)
-    C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * 2 * plane_len(N1));
+    C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * 2 * plane_len_e<E>(N1));
     if constexpr (STW) TwShared<C>::template fill<(STW ? LOG : 8)>(stw, tw1);  // synced below
     const C *gp = gk + gk_index(0, c0, N1);  // row n: columns c0, c0+1 at gp[2n], gp[2n+1]
-    CV<V> x[16];
+    CV<V> x[E];
     double colsum = 0.0;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < E; ++r) {
         const int n = t + r * T;
         C p, q;
         if constexpr (std::is_same<R, float>::value) {
@@ -781,7 +783,7 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         if (c0 == 0) colsum += (double)p.x;
         x[r] = pack2<R>(p, q);
     }
-    // state entries this thread updates: rows r < 4 (k1 = n) and r >= 12
+    // state entries this thread updates: rows r < QE (k1 = n) and r >= E - QE
     // (k1 = n - N1) of columns c0 and c0 + 1
     C *sa = state + (size_t)c0 * ld1 + a.K1, *sb = sa + ld1;
     if (tile == 0) {  // block-uniform: FP64 row-sum reduction of column 0 (any block size)
@@ -798,19 +800,19 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         __syncthreads();
         fft_line_s<-1, (STW ? LOG : 8)>(x, t, sm, tw1, stw);
     } else {
-        fft_line<-1, LOG>(x, a.logn1, t, sm, tw1);
+        fft_line_e<-1, LOG, E>(x, a.logn1, t, sm, tw1);
     }
 
     __syncthreads();  // cfs (the transform may have no barrier for short lines)
     // the state entries, read after the transform (they are L2-resident in
     // the persisting window; holding them across the transform cost more)
-    C phi[8][2];
+    C phi[E / 2][2];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int r = i < 4 ? i : i + 8;
+    for (int i = 0; i < E / 2; ++i) {
+        const int r = i < QE ? i : i + E / 2;
         const int n = t + r * T;
-        const int k1 = (r < 4) ? n : n - N1;
-        const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
+        const int k1 = (r < QE) ? n : n - N1;
+        const bool in_box = (r < QE) ? (n <= a.K1) : (k1 >= -a.K1);
         phi[i][0] = (in_box && va) ? sa[k1] : C{0, 0};
         phi[i][1] = (in_box && vb) ? sb[k1] : C{0, 0};
     }
@@ -818,13 +820,13 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
     const R s1 = scale1<R>(a), s2 = scale2<R>(a);
     int bad = 0;
-    C nphi[8][2];  // the updated entries (kept for the fused pass A of the next step)
+    C nphi[E / 2][2];  // the updated entries (kept for the fused pass A of the next step)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int r = i < 4 ? i : i + 8;
+    for (int i = 0; i < E / 2; ++i) {
+        const int r = i < QE ? i : i + E / 2;
         const int n = t + r * T;
-        const int k1 = (r < 4) ? n : n - N1;
-        const bool in_box = (r < 4) ? (n <= a.K1) : (k1 >= -a.K1);
+        const int k1 = (r < QE) ? n : n - N1;
+        const bool in_box = (r < QE) ? (n <= a.K1) : (k1 >= -a.K1);
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int k2 = c0 + side;
@@ -936,6 +938,30 @@ template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAt(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
     passA_body<R, LOG, 16, false, true>(d, blockIdx.x, gridDim.x, pf, &tm);
+}
+// FP64, 8 points per thread at short compile-time lengths (2^4 .. 2^7): one
+// line pair per CTA of 2^LOG / 8 threads, twice the threads of the runtime
+// kernels for the latency-bound small FP64 grids
+template <class R, int LOG> __global__ void __launch_bounds__(128, 1) k_passA8d(FlameDesc d, int pf) {
+    passA_body<R, LOG, 8, false>(d, blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG> __global__ void __launch_bounds__(128, 1) k_passB8d(FlameDesc d, int pf) {
+    passB_body<R, LOG, 8>(d, blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG> __global__ void __launch_bounds__(128, 1) k_passC8d(FlameDesc d, int pf) {
+    passC_body<R, LOG, false, 8>(d, blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG>
+__global__ void __launch_bounds__(128, 1) k_passC8d_n(const FlameDesc *__restrict__ ds, int pf) {
+    passC_body<R, LOG, false, 8>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG>
+__global__ void __launch_bounds__(128, 1) k_passA8d_n(const FlameDesc *__restrict__ ds, int pf) {
+    passA_body<R, LOG, 8, false>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
+template <class R, int LOG>
+__global__ void __launch_bounds__(128, 1) k_passB8d_n(const FlameDesc *__restrict__ ds, int pf) {
+    passB_body<R, LOG, 8>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(FlameDesc d, int pf) {

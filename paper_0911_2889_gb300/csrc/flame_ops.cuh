@@ -203,8 +203,29 @@ template <class R, int L> static Geom geom_passA8(int ncols) {
     return g;
 }
 
+// FP64 lines of 2^4 .. 2^7 points: 8 points per thread, one line pair per
+// CTA (the runtime kernels give such lines 2^LOG/16 threads, a quarter warp
+// at 128 points, and are bound by the latency of their FP64 chains)
+template <class R> static bool small_fp64(int logn) { return sizeof(R) == 8 && logn >= 4 && logn <= 7; }
+template <class R> static Geom geom_small_fp64(int logn, int nlines, size_t extra) {
+    Geom g;
+    g.threads = (1 << logn) / 8;
+    g.blocks = nlines;
+    g.smem = 2 * (size_t)plane_len_e<8>(1 << logn) * sizeof(typename VecOf<R>::type) + extra;
+    return g;
+}
+
 template <class R>
 cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *uv_map) {
+    if (small_fp64<R>(d.a.logn1)) {
+        const Geom g = geom_small_fp64<R>(d.a.logn1, d.a.K2 + 1, 0);
+        cudaError_t err = cudaErrorInvalidValue;
+        static_for<4, 8>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (d.a.logn1 == L) err = launch_w(d.l2_state, k_passA8d<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+        });
+        return err;
+    }
     Geom g = geom_cols(d.a.logn1, d.a.K2 + 1, 0);
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logn1, [&](auto lc) {
@@ -251,6 +272,15 @@ template <class R> static Geom geom_passB8(int logm, int nlines) {
 
 template <class R>
 cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *gk_map) {
+    if (small_fp64<R>(d.a.logm)) {  // + M entries of the parked |z|^2 per row pair
+        const Geom g = geom_small_fp64<R>(d.a.logm, d.a.n1 / 2, (size_t)(1 << d.a.logm) * sizeof(typename VecOf<R>::c));
+        cudaError_t err = cudaErrorInvalidValue;
+        static_for<4, 8>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (d.a.logm == L) err = launch_cl(k_passB8d<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+        });
+        return err;
+    }
     Geom g = geom_passB<R>(d.a.logm, d.a.n1 / 2);
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logm, [&](auto lc) {
@@ -275,6 +305,15 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
     return cudaGetLastError();
 }
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
+    if (small_fp64<R>(d.a.logn1)) {
+        const Geom g = geom_small_fp64<R>(d.a.logn1, (d.a.K2 + 2) / 2, 0);
+        cudaError_t err = cudaErrorInvalidValue;
+        static_for<4, 8>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (d.a.logn1 == L) err = launch_w(d.l2_state, k_passC8d<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+        });
+        return err;
+    }
     Geom g = geom_cols(d.a.logn1, (d.a.K2 + 2) / 2, 0);
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logn1, [&](auto lc) {
@@ -303,6 +342,15 @@ cudaError_t Ops<R>::passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap
 template <class R>
 cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
                                 const CUtensorMap *maps) {
+    if (small_fp64<R>(a.logn1)) {  // the kernels of passA, so that a flame's ensemble step equals its own
+        const Geom g = geom_small_fp64<R>(a.logn1, a.K2 + 1, 0);
+        cudaError_t err = cudaErrorInvalidValue;
+        static_for<4, 8>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (a.logn1 == L) err = launch_cl(k_passA8d_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        });
+        return err;
+    }
     Geom g = geom_cols(a.logn1, a.K2 + 1, 0);
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logn1, [&](auto lc) {
@@ -327,6 +375,15 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
 template <class R>
 cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
                                 const CUtensorMap *maps) {
+    if (small_fp64<R>(a.logm)) {
+        const Geom g = geom_small_fp64<R>(a.logm, a.n1 / 2, (size_t)(1 << a.logm) * sizeof(typename VecOf<R>::c));
+        cudaError_t err = cudaErrorInvalidValue;
+        static_for<4, 8>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (a.logm == L) err = launch_cl(k_passB8d_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        });
+        return err;
+    }
     Geom g = geom_passB<R>(a.logm, a.n1 / 2);
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logm, [&](auto lc) {
@@ -347,6 +404,15 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
 }
 template <class R>
 cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
+    if (small_fp64<R>(a.logn1)) {
+        const Geom g = geom_small_fp64<R>(a.logn1, (a.K2 + 2) / 2, 0);
+        cudaError_t err = cudaErrorInvalidValue;
+        static_for<4, 8>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (a.logn1 == L) err = launch_cl(k_passC8d_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        });
+        return err;
+    }
     Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
     cudaError_t e = cudaSuccess;
     with_log<R>(a.logn1, [&](auto lc) {
