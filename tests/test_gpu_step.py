@@ -350,3 +350,28 @@ def test_linear_only_matches_discrete_product(fl, prec, tol, shape):
     assert _box_err(_host(fl, state), want, K1) < tol
     assert t.item() == t0 + n * dt
     f.close()
+
+
+@pytest.mark.gpu
+def test_ensemble_members_match_oracle(fl, orc):
+    # 8 members of the bench's uneven ensemble (grids drawn with size seed
+    # 1234, spectrum seed 1000 + i, |k| <= batch_kmax), stepped together as
+    # one ensemble and each compared with the FP64 oracle after 3 steps
+    grids = inputs.batch_grids(8)
+    fs, ss, ms, ts, st0s = [], [], [], [], []
+    for i, (n1, n2) in enumerate(grids):
+        f, st0, state, mean, t = _setup(fl, n1, n2, "fp32", inputs.batch_kmax(n1), 1000 + i,
+                                        amp=1e-2, gamma=0.8, t0=200.0, dt=1e-3)
+        fs.append(f)
+        ss.append(state)
+        ms.append(mean)
+        ts.append(t)
+        st0s.append(st0)
+    fl.flame_step_batch([f.h for f in fs], ss, ms, ts, nsteps=3)
+    torch.cuda.synchronize()
+    for f, s, m, t, st0 in zip(fs, ss, ms, ts, st0s):
+        ref, mref, tref = orc.step(_oparams(orc, f), st0, 0.0, 200.0, 3)
+        assert _box_err(_host(fl, s), ref, f.K1) < 2e-5
+        assert t.item() == tref
+        assert abs(m.item() - mref) <= 1e-6 * abs(mref)
+        f.close()
