@@ -786,15 +786,18 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     // state entries this thread updates: rows r < QE (k1 = n) and r >= E - QE
     // (k1 = n - N1) of columns c0 and c0 + 1
     C *sa = state + (size_t)c0 * ld1 + a.K1, *sb = sa + ld1;
-    if (tile == 0) {  // block-uniform: FP64 row-sum reduction of column 0 (any block size)
+    // block-uniform: FP64 row sum of column 0, in spans of up to 32 threads
+    // (power-of-two blocks) summed by each span's first thread in parallel
+    const int span = min((int)blockDim.x, 32);
+    if (tile == 0) {
         red[threadIdx.x] = colsum;
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x % span == 0) {
             double s = 0.0;
-            for (int w = 0; w < (int)blockDim.x; ++w) s += red[w];
-            red[0] = s;
+            for (int w = 0; w < span; ++w) s += red[threadIdx.x + w];
+            red[threadIdx.x] = s;  // the span's own slots: no other thread touches them
         }
-        // red[0] is read by thread 0 after the transform's barriers
+        // the span sums are read by thread 0 after the transform's barriers
     }
     if constexpr (STW) {
         __syncthreads();
@@ -853,7 +856,9 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     }
     if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
     if (tile == 0 && threadIdx.x == 0) {
-        const double mg = red[0] / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
+        double rs = 0.0;
+        for (int w = 0; w < (int)blockDim.x; w += span) rs += red[w];
+        const double mg = rs / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
         if (nl) *d.mean += a.dt * cf.c * mg;
         long n = __double2ll_rn((cf.tn - a.t0) / a.dt);
         *d.t_out = a.t0 + (double)(n + 1) * a.dt;

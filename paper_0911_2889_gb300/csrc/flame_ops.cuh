@@ -217,7 +217,7 @@ template <class R> static Geom geom_small_fp64(int logn, int nlines, size_t extr
 
 template <class R>
 cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *uv_map) {
-    if (small_fp64<R>(d.a.logn1)) {
+    if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logn1)) {
         const Geom g = geom_small_fp64<R>(d.a.logn1, d.a.K2 + 1, 0);
         cudaError_t err = cudaErrorInvalidValue;
         static_for<4, 8>([&](auto lc) {
@@ -272,7 +272,7 @@ template <class R> static Geom geom_passB8(int logm, int nlines) {
 
 template <class R>
 cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *gk_map) {
-    if (small_fp64<R>(d.a.logm)) {  // + M entries of the parked |z|^2 per row pair
+    if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logm)) {  // + M entries of the parked |z|^2 per row pair
         const Geom g = geom_small_fp64<R>(d.a.logm, d.a.n1 / 2, (size_t)(1 << d.a.logm) * sizeof(typename VecOf<R>::c));
         cudaError_t err = cudaErrorInvalidValue;
         static_for<4, 8>([&](auto lc) {
@@ -305,7 +305,7 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
     return cudaGetLastError();
 }
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
-    if (small_fp64<R>(d.a.logn1)) {
+    if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logn1)) {
         const Geom g = geom_small_fp64<R>(d.a.logn1, (d.a.K2 + 2) / 2, 0);
         cudaError_t err = cudaErrorInvalidValue;
         static_for<4, 8>([&](auto lc) {
@@ -342,7 +342,7 @@ cudaError_t Ops<R>::passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap
 template <class R>
 cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
                                 const CUtensorMap *maps) {
-    if (small_fp64<R>(a.logn1)) {  // the kernels of passA, so that a flame's ensemble step equals its own
+    if constexpr (sizeof(R) == 8) if (small_fp64<R>(a.logn1)) {  // the kernels of passA, so that a flame's ensemble step equals its own
         const Geom g = geom_small_fp64<R>(a.logn1, a.K2 + 1, 0);
         cudaError_t err = cudaErrorInvalidValue;
         static_for<4, 8>([&](auto lc) {
@@ -375,7 +375,7 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
 template <class R>
 cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
                                 const CUtensorMap *maps) {
-    if (small_fp64<R>(a.logm)) {
+    if constexpr (sizeof(R) == 8) if (small_fp64<R>(a.logm)) {
         const Geom g = geom_small_fp64<R>(a.logm, a.n1 / 2, (size_t)(1 << a.logm) * sizeof(typename VecOf<R>::c));
         cudaError_t err = cudaErrorInvalidValue;
         static_for<4, 8>([&](auto lc) {
@@ -404,7 +404,7 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
 }
 template <class R>
 cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
-    if (small_fp64<R>(a.logn1)) {
+    if constexpr (sizeof(R) == 8) if (small_fp64<R>(a.logn1)) {
         const Geom g = geom_small_fp64<R>(a.logn1, (a.K2 + 2) / 2, 0);
         cudaError_t err = cudaErrorInvalidValue;
         static_for<4, 8>([&](auto lc) {
