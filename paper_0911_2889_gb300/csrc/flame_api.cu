@@ -130,7 +130,7 @@ struct flame_ctx {
     void *spec;       // c2r workspace, N1 x (N2/2 + 1)
     void *aw;         // area / adjoint workspace, N1 x ldk pairs
     double *rowsum;   // N1 per-row area sums
-    double *dscal;    // [0]: t_n copy, [1]: lambda_0, [2]: dgamma, [3]: dA/dPhi_0 scratch
+    double *dscal;    // [1]: lambda_0, [2]: dgamma, [3]: dA/dPhi_0 scratch, [8..13]: step coefficients
     int *status;
     cudaStream_t cap;  // capture stream
     std::vector<GraphEntry> graphs;
@@ -204,7 +204,7 @@ FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
     d.tw1 = h->tw1;
     d.twm = h->twm;
     d.t_in = t;
-    d.t_copy = h->dscal;
+    d.coef = h->dscal + 8;
     d.mean = mean;
     d.t_out = t;
     d.status = h->status;
@@ -518,7 +518,7 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
               dev_alloc(&h->twm, flame::tw_alloc_len(h->logm) * h->csz) &&
               dev_alloc(&h->uv, n1 * ldk * 2 * h->csz) && dev_alloc(&h->gk, n1 * ((ldk + 1) & ~(size_t)1) * h->csz) &&
               dev_alloc(&h->spec, n1 * m1 * h->csz) && dev_alloc(&h->aw, n1 * ldk * 2 * h->csz) &&
-              dev_alloc((void **)&h->rowsum, n1 * sizeof(double)) && dev_alloc((void **)&h->dscal, 4 * sizeof(double)) &&
+              dev_alloc((void **)&h->rowsum, n1 * sizeof(double)) && dev_alloc((void **)&h->dscal, 16 * sizeof(double)) &&
               dev_alloc((void **)&h->status, sizeof(int));
     if (!ok) {
         cudaGetLastError();
@@ -534,7 +534,7 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
     flame_status st = p.prec == FLAME_FP64 ? alloc_tables<double>(h) : alloc_tables<float>(h);
     if (st == FLAME_OK) {
         e = cudaMemsetAsync(h->status, 0, sizeof(int), h->cap);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->dscal, 0, 4 * sizeof(double), h->cap);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->dscal, 0, 16 * sizeof(double), h->cap);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap);
         if (e != cudaSuccess) st = fail(FLAME_ECUDA, "flame_create: %s", cudaGetErrorString(e));
     }

@@ -50,7 +50,11 @@ struct FlameDesc {
     const void *tw1;        // twiddles of length N1
     const void *twm;        // twiddles of length N2/2 (+ real table)
     const double *t_in;     // caller's t (read by pass B)
-    double *t_copy;         // t_n for pass C (handle scalar)
+    // the step's coefficients, derived from t once by pass B (block 0) and
+    // read by pass C: [0] t_n, [1] c = 1/(2 r0^2), then from byte 16 the
+    // kernel-precision CoefR (1/r0^2, gamma/(2 r0), c/(N1 N2), dt); 48 bytes,
+    // 16-byte aligned (handle scratch)
+    double *coef;
     double *mean;           // caller's mean mode
     double *t_out;          // caller's t (written by pass C)
     int *status;            // handle's device status word

@@ -519,6 +519,44 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
     }
 }
 
+// Step coefficients at t_n, evaluated in FP64 (then rounded for FP32).
+struct Coef {
+    double tn, a, b, c;  // a = 1/r0^2, b = gamma/(2 r0), c = 1/(2 r0^2)
+};
+__device__ __forceinline__ Coef step_coef(const StepArgs &s, double t) {
+    long n = __double2ll_rn((t - s.t0) / s.dt);
+    double tn = s.t0 + (double)n * s.dt;
+    Coef k;
+    k.tn = tn;
+    k.a = 1.0 / (tn * tn);
+    k.b = s.gamma / (2.0 * tn);
+    k.c = 0.5 * k.a;
+    return k;
+}
+
+// The step coefficients in the kernel's precision: 1/r0^2, gamma/(2 r0),
+// c/(N1 N2) (c = 1/(2 r0^2) with the inverse transform's scale folded in)
+// and dt.  One thread of pass B derives them in FP64 for the whole step and
+// pass C loads them: GB300's FP64 pipe is narrow, and the divisions cost a
+// column-pass CTA more than its loads when every CTA derives them.
+template <class R> struct CoefR {
+    R a, b, cs, dt;
+};
+template <class R> __device__ __forceinline__ CoefR<R> coef_r(const Coef &cf, const StepArgs &s) {
+    const double inv = 1.0 / ((double)s.n1 * (double)s.n2);
+    return CoefR<R>{(R)cf.a, (R)cf.b, (R)(cf.c * inv), (R)s.dt};
+}
+// Layout of FlameDesc::coef: t_n, c, then CoefR<R> from byte 16.
+template <class R> __device__ __forceinline__ void store_coef(double *coef, const StepArgs &s, double t) {
+    const Coef cf = step_coef(s, t);
+    coef[0] = cf.tn;
+    coef[1] = cf.c;
+    *reinterpret_cast<CoefR<R> *>(coef + 2) = coef_r<R>(cf, s);
+}
+template <class R> __device__ __forceinline__ CoefR<R> load_coef(const double *coef) {
+    return *reinterpret_cast<const CoefR<R> *>(coef + 2);
+}
+
 // Pass B (a3..a6): rows 2p and 2p+1 of uv.  For each row the full spectrum
 // Z[k] = U[k] + i V[k] (k = -K2..K2, U[-k] = conj U[k]) is transformed by
 // two half-length inverse FFTs (even and odd grid points:
@@ -549,7 +587,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len_e<E>(M) + M);
     auto sm = make_planes_e<E>(base, M);  // (E = 8 pads one slot every 8: st_raw/ld_raw)
     const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
-    if (tile == 0 && threadIdx.x == 0) *d.t_copy = *d.t_in;
+    if (tile == 0 && threadIdx.x == 0) store_coef<R>(d.coef, a, *d.t_in);
     constexpr bool STW = kSharedTw<R, LOG, E>;
     constexpr int LS = STW ? LOG : 8;
     C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * (2 * plane_len_e<E>(M) + M));
@@ -683,34 +721,6 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     }
 }
 
-// Step coefficients at t_n, evaluated in FP64 (then rounded for FP32).
-struct Coef {
-    double tn, a, b, c;  // a = 1/r0^2, b = gamma/(2 r0), c = 1/(2 r0^2)
-};
-__device__ __forceinline__ Coef step_coef(const StepArgs &s, double t) {
-    long n = __double2ll_rn((t - s.t0) / s.dt);
-    double tn = s.t0 + (double)n * s.dt;
-    Coef k;
-    k.tn = tn;
-    k.a = 1.0 / (tn * tn);
-    k.b = s.gamma / (2.0 * tn);
-    k.c = 0.5 * k.a;
-    return k;
-}
-
-// The step coefficients in the kernel's precision: 1/r0^2, gamma/(2 r0),
-// c/(N1 N2) (c = 1/(2 r0^2) with the inverse transform's scale folded in)
-// and dt.  Thread 0 of a CTA derives them once in FP64 and shares them:
-// GB300's FP64 pipe is narrow, and three divisions in every thread cost the
-// column pass more than its transform.
-template <class R> struct CoefR {
-    R a, b, cs, dt;
-};
-template <class R> __device__ __forceinline__ CoefR<R> coef_r(const Coef &cf, const StepArgs &s) {
-    const double inv = 1.0 / ((double)s.n1 * (double)s.n2);
-    return CoefR<R>{(R)cf.a, (R)cf.b, (R)(cf.c * inv), (R)s.dt};
-}
-
 // |kappa| = sqrt((s1 k1)^2 + (s2 k2)^2) for (k1, k2) != 0.  FP32: x times the
 // hardware reciprocal square root (within a few ulp, far inside the FP32
 // path's per-step tolerance); FP64: the correctly rounded square root.
@@ -752,12 +762,7 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             l2_prefetch(state + (size_t)c * ld1, (size_t)nc * ld1 * sizeof(C));
         }
     }
-    __shared__ CoefR<R> cfs;
-    Coef cf{};  // thread 0 only
-    if (threadIdx.x == 0) {
-        cf = step_coef(a, *d.t_copy);
-        cfs = coef_r<R>(cf, a);
-    }
+    const CoefR<R> cfs = load_coef<R>(d.coef);  // derived by pass B
     const int c0 = 2 * (tile * G + g);
     const bool va = c0 <= a.K2, vb = c0 + 1 <= a.K2;
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len_e<E>(N1);
@@ -806,7 +811,7 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         fft_line_e<-1, LOG, E>(x, a.logn1, t, sm, tw1);
     }
 
-    __syncthreads();  // cfs (the transform may have no barrier for short lines)
+    __syncthreads();  // block 0's span sums (the transform may have no CTA barrier)
     // the state entries, read after the transform (they are L2-resident in
     // the persisting window; holding them across the transform cost more)
     C phi[E / 2][2];
@@ -859,8 +864,8 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         double rs = 0.0;
         for (int w = 0; w < (int)blockDim.x; w += span) rs += red[w];
         const double mg = rs / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
-        if (nl) *d.mean += a.dt * cf.c * mg;
-        long n = __double2ll_rn((cf.tn - a.t0) / a.dt);
+        if (nl) *d.mean += a.dt * d.coef[1] * mg;
+        long n = __double2ll_rn((d.coef[0] - a.t0) / a.dt);
         *d.t_out = a.t0 + (double)(n + 1) * a.dt;
     }
     if constexpr (FUSE_A && std::is_same<R, float>::value && LOG > 0) {

@@ -96,7 +96,7 @@ flame_status run_steps(const flame::StepArgs &a, unsigned char *base, size_t off
     d.tw1 = base + off_tw1;
     d.twm = base + off_twm;
     d.t_in = t;
-    d.t_copy = dscal;
+    d.coef = dscal + 8;  // 48 bytes at off_sc + 64 (the arena keeps 256 bytes there)
     d.mean = mean;
     d.t_out = t;
     d.status = status;
