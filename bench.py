@@ -406,7 +406,8 @@ def run_ours(args):
 
 def run_suite(args):
     """Secondary configurations (one JSON line each): the FP64 128x256 and
-    FP32 1024x2048 trajectories' step rates and the 2-D real FFT pair sweep."""
+    FP32 1024x2048 trajectories' step rates, the initial state from the
+    paper's physical-space perturbation, and the 2-D real FFT pair sweep."""
     import torch
 
     from paper_0911_2889_gb300 import flame, inputs
@@ -428,6 +429,27 @@ def run_suite(args):
                           "points_per_s": n1 * n2 * nsteps / (ms * 1e-3), "effective_gbs": gbs,
                           "note": "graph-captured; L2-resident" if n1 * n2 <= 2 ** 21 else "graph-captured"}),
               flush=True)
+        f.close()
+    for (n1, n2, prec) in ((128, 256, "fp64"), (4096, 8192, "fp32")):
+        # flame_state_from_field: r2c (rows, columns) into the workspace, then
+        # the retained modes.  Bytes: the field read; the N1 x (N2/2+1)
+        # spectrum written by the row pass, read and written by the column
+        # pass and read by the box extraction (4 x its size, an upper bound);
+        # the box written
+        f = flame.Flame(n1, n2, prec=prec)
+        x = torch.from_numpy(inputs.physical_ic(n1, n2, 0)).cuda().to(f.rdtype)
+        st, m = f.state_from_field(x)
+        reps, tot = 5, 0.0
+        for _ in range(reps):
+            flush.zero_()
+            tot += _ev_time(lambda: f.state_from_field(x), s)
+        ms = tot / reps
+        rsz = 4 if prec == "fp32" else 8
+        spec = n1 * (n2 // 2 + 1) * 2 * rsz
+        alg = n1 * n2 * rsz + 4 * spec + (2 * f.K1 + 1) * (f.K2 + 1) * 2 * rsz
+        print(json.dumps({"suite": f"initial-state-from-field-{n1}x{n2}-{prec}", "ms": ms, "alg_bytes": alg,
+                          "effective_gbs": alg / (ms * 1e-3) / 1e9,
+                          "frac_of_hbm": alg / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind}), flush=True)
         f.close()
     sizes = [(256, 256), (256, 512), (512, 512), (512, 1024), (1024, 1024), (1024, 2048), (2048, 2048),
              (2048, 4096), (4096, 4096), (4096, 8192)]

@@ -144,6 +144,26 @@ flame_status flame_fft_r2c(flame_t h, const void *real_in, void *spec_out,
 flame_status flame_fft_c2r(flame_t h, const void *spec_in, void *real_out,
                            void *stream);
 
+/* Initial state from a physical-space perturbation.  Sec. 2 starts its runs
+ * from Phi(theta, phi, t0) = eps eta(theta, phi), with |eta| <= 1 drawn for
+ * every grid point; this call projects such a field on the retained modes:
+ *   field     N1 x N2 real, row-major (j1 slowest), device memory, in the
+ *             handle's real type (double for FLAME_FP64, float otherwise);
+ *   state     the compact box (ABI layout, the handle's complex type):
+ *             state(k1, k2) = (1/(N1 N2)) sum_{j1,j2} field[j1][j2]
+ *                             exp(-2 pi i (k1 j1/N1 + k2 j2/N2))
+ *             for |k1| <= K1, 0 <= k2 <= K2, except that the k = 0 slot is
+ *             0 and the k2 = 0 column's k1 < 0 entries are the conjugates of
+ *             its k1 > 0 entries (the step's symmetrisation, Sec. 3);
+ *   mean_mode one FP64 device value, the field's average (the k = 0
+ *             coefficient).
+ * The transform is flame_fft_r2c's (rows, then columns) into the handle's
+ * spectrum workspace, which flame_fft_c2r also uses: calls on one handle
+ * must be ordered (one stream).  EINVAL on null pointers.  Buffers must be
+ * 16-byte aligned. */
+flame_status flame_state_from_field(flame_t h, const void *field, void *state,
+                                    double *mean_mode, void *stream);
+
 /* Advances the state by nsteps explicit Euler steps of eq. (SivCurv1c):
  *   Phi_k <- Phi_k + dt (omega_k(t_n) Phi_k + c(t_n) ghat_k)   (k != 0),
  *   Phi_0 <- Phi_0 + dt c(t_n) ghat_0,

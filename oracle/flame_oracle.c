@@ -196,6 +196,35 @@ int orc_check(const orc_params *p)
     return 0;
 }
 
+/* Retained modes of a real field on the grid, the initial perturbation of
+ * Sec. 2 (Phi(theta, phi, t0) = eps eta, |eta| <= 1 at every grid point):
+ *   Phi_k = (1/(n1 n2)) sum_{j1,j2} field[j1][j2] exp(-2 pi i (k1 j1/n1 + k2 j2/n2))
+ * for |k1| <= K1, 0 <= k2 <= K2 (orc_rfft2, then the box rows k1 mod n1).
+ * On k2 = 0 the k1 < 0 entries are replaced by the conjugates of the k1 > 0
+ * ones (Sec. 3's symmetrisation), the k = 0 slot is 0 and *mean is the k = 0
+ * coefficient, the field's average.  Pinned by fields synthesised from known
+ * coefficients by the definition of the series, and by the grid average. */
+int orc_state_from_field(const orc_params *p, const double *field, cplx *state, double *mean)
+{
+    if (orc_check(p)) return -1;
+    int h2 = p->n2 / 2 + 1;
+    cplx *half = malloc(sizeof(cplx) * (size_t)p->n1 * (size_t)h2);
+    if (!half) return -1;
+    orc_rfft2(p->n1, p->n2, field, half);
+    double inv = 1.0 / ((double)p->n1 * (double)p->n2);
+    for (int k1 = -p->K1; k1 <= p->K1; k1++) {
+        int row = (k1 + p->n1) % p->n1;
+        for (int k2 = 0; k2 <= p->K2; k2++)
+            state[box_index(p, k1, k2)] = half[(size_t)row * h2 + k2] * inv;
+    }
+    for (int k1 = 1; k1 <= p->K1; k1++)
+        state[box_index(p, -k1, 0)] = conj(state[box_index(p, k1, 0)]);
+    *mean = creal(half[0]) * inv;
+    state[box_index(p, 0, 0)] = 0.0;
+    free(half);
+    return 0;
+}
+
 /* Scatters s*i*kappa_i*Phi_k (which = 1: kappa_1 = s1 k1, which = 2:
  * kappa_2 = s2 k2, which = 0: Phi itself with the mean mode) from the compact
  * box into the zero-padded half spectrum n1 x (n2/2+1): the augmented array

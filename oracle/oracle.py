@@ -98,6 +98,7 @@ def _load():
                 "orc_fft": (i, [i, vp, i]),
                 "orc_rfft2": (i, [i, i, vp, vp]),
                 "orc_irfft2": (i, [i, i, vp, vp]),
+                "orc_state_from_field": (i, [P, vp, vp, pd]),
                 "orc_check": (i, [P]),
                 "orc_grad2_hat": (None, [P, vp, vp]),
                 "orc_grad2_brute": (None, [P, vp, vp]),
@@ -168,6 +169,19 @@ def irfft2(X, n2):
 
 
 # --------------------------------------------------------------------- model
+def state_from_field(p: Params, field):
+    """(box, mean): the retained modes of a real (n1, n2) field (Sec. 2's
+    physical-space initial perturbation), box indexed [k1 + K1, k2]."""
+    _check(p)
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    assert f.shape == (p.n1, p.n2)
+    box = np.empty(p.box_shape, dtype=np.complex128)
+    mean = ctypes.c_double()
+    if _load().orc_state_from_field(ctypes.byref(p._c()), _ptr(f), _ptr(box), ctypes.byref(mean)) != 0:
+        raise ValueError("invalid parameters")
+    return box, mean.value
+
+
 def grad2_hat(p: Params, state):
     """Box coefficients of |grad Phi|^2 through the FFT (k = 0 = mean)."""
     _check(p)

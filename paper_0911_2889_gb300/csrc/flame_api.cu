@@ -605,6 +605,29 @@ flame_status flame_fft_r2c(flame_t h, const void *real_in, void *spec_out, void 
     return FLAME_OK;
 }
 
+flame_status flame_state_from_field(flame_t h, const void *field, void *state, double *mean_mode, void *stream) {
+    if (!h || !field || !state || !mean_mode) return fail(FLAME_EINVAL, "flame_state_from_field: null pointer");
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_state_from_field: injected launch fault");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n1 = h->p.n_theta, n2 = h->p.n_phi, M = n2 / 2;
+    if (h->p.prec == FLAME_FP64) {
+        using C = double2;
+        C *spec = static_cast<C *>(h->spec);
+        CUDA_TRY(Ops<double>::rows_r2c(static_cast<const double *>(field), spec, n1, h->logm,
+                                       static_cast<const C *>(h->twm), s));
+        CUDA_TRY(Ops<double>::cols(spec, spec, h->logn1, M + 1, M + 1, -1, static_cast<const C *>(h->tw1), s));
+        CUDA_TRY(Ops<double>::box_from_spec(spec, static_cast<C *>(state), mean_mode, n1, n2, h->p.K1, h->p.K2, s));
+    } else {
+        using C = float2;
+        C *spec = static_cast<C *>(h->spec);
+        CUDA_TRY(Ops<float>::rows_r2c(static_cast<const float *>(field), spec, n1, h->logm,
+                                      static_cast<const C *>(h->twm), s));
+        CUDA_TRY(Ops<float>::cols(spec, spec, h->logn1, M + 1, M + 1, -1, static_cast<const C *>(h->tw1), s));
+        CUDA_TRY(Ops<float>::box_from_spec(spec, static_cast<C *>(state), mean_mode, n1, n2, h->p.K1, h->p.K2, s));
+    }
+    return FLAME_OK;
+}
+
 flame_status flame_fft_c2r(flame_t h, const void *spec_in, void *real_out, void *stream) {
     if (!h || !spec_in || !real_out) return fail(FLAME_EINVAL, "flame_fft_c2r: null pointer");
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_fft_c2r: injected launch fault");

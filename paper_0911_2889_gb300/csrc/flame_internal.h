@@ -101,6 +101,9 @@ template <class R> struct Ops {
     static cudaError_t rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s);
     static cudaError_t cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw,
                             cudaStream_t s);
+    // retained modes of an r2c spectrum -> compact box + FP64 mean
+    static cudaError_t box_from_spec(const C *spec, C *state, double *mean, int n1, int n2, int K1, int K2,
+                                     cudaStream_t s);
     // One step pass for one flame (desc by value) or for nflames flames of
     // the same grid (descs: device array of nflames entries, shape from a).
     // variant: kVariantDefault, or a tuned alternative (pass A: kVariantDirect

@@ -109,6 +109,36 @@ template <class R> __device__ __forceinline__ CplxT<R> lane1(CV<typename VecOf<R
 }
 
 // ----------------------------------------------------------------------------
+// The retained modes of a 2-D real field (Sec. 2's physical-space initial
+// perturbation): spec is the field's unnormalised r2c, N1 x (N2/2+1)
+// row-major; box entry (k1, k2), ABI index k2 (2K1+1) + k1 + K1, is
+// spec[k1 mod N1][k2] / (N1 N2).  On k2 = 0 the k1 < 0 entries are the
+// conjugates of the k1 > 0 ones, the k = 0 slot is 0, and the field's mean
+// (FP64) goes to *mean.
+template <class R>
+__global__ void k_box_from_spec(const CplxT<R> *__restrict__ spec, CplxT<R> *__restrict__ state, double *mean,
+                                int n1, int n2, int K1, int K2) {
+    using C = CplxT<R>;
+    const int ld1 = 2 * K1 + 1, ldm = n2 / 2 + 1;
+    const long total = (long)ld1 * (K2 + 1);
+    const double inv = 1.0 / ((double)n1 * (double)n2);
+    const R rinv = (R)inv;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int k2 = (int)(i / ld1), k1 = (int)(i % ld1) - K1;
+        C v{0, 0};
+        if (k1 == 0 && k2 == 0) {
+            *mean = (double)spec[0].x * inv;
+        } else {
+            const bool mirror = k2 == 0 && k1 < 0;
+            const int row = mirror ? -k1 : (k1 < 0 ? k1 + n1 : k1);
+            const C s = spec[(size_t)row * ldm + k2];
+            v = C{s.x * rinv, (mirror ? -s.y : s.y) * rinv};
+        }
+        state[i] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Twiddle table generation (FP64 sincospi, rounded once)
 // ----------------------------------------------------------------------------
 template <class R> __global__ void k_twiddles(CplxT<R> *tab, int logN, int LE) {

@@ -171,6 +171,14 @@ template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStrea
 }
 
 template <class R>
+cudaError_t Ops<R>::box_from_spec(const C *spec, C *state, double *mean, int n1, int n2, int K1, int K2,
+                                  cudaStream_t s) {
+    const long total = (long)(2 * K1 + 1) * (K2 + 1);
+    const int blocks = (int)std::min<long>((total + 255) / 256, 8L * sm_count());
+    return launch_cl(k_box_from_spec<R>, dim3(blocks), 256, 0, s, 1, spec, state, mean, n1, n2, K1, K2);
+}
+
+template <class R>
 cudaError_t Ops<R>::rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s) {
     Geom g = geom_rows(logm, n1 / 2, 0);
     return launch_cl(k_rows_r2c<R>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, n1, logm, tw);

@@ -57,6 +57,7 @@ SIGNATURES = {
     "flame_fused_steps": (_i, [_vp, ctypes.POINTER(_i)]),
     "flame_fft_r2c": (_i, [_vp, _vp, _vp, _vp]),
     "flame_fft_c2r": (_i, [_vp, _vp, _vp, _vp]),
+    "flame_state_from_field": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "flame_step": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_step_pass": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
@@ -158,6 +159,11 @@ def flame_fft_r2c(h, real_in, spec_out, stream=None):
 def flame_fft_c2r(h, spec_in, real_out, stream=None):
     _check(load().flame_fft_c2r(ctypes.c_void_p(h), _ptr(spec_in, name="spec_in"),
                                 _ptr(real_out, name="real_out"), _stream(stream)))
+
+
+def flame_state_from_field(h, field, state, mean_mode, stream=None):
+    _check(load().flame_state_from_field(ctypes.c_void_p(h), _ptr(field, name="field"), _ptr(state, name="state"),
+                                         _ptr(mean_mode, torch.float64, "mean_mode"), _stream(stream)))
 
 
 def flame_step(h, state, mean_mode, t, nsteps=1, stream=None):
@@ -276,6 +282,17 @@ class Flame:
             out = torch.empty((n1, n2 // 2 + 1), dtype=self.cdtype, device=x.device)
         flame_fft_r2c(self.h, x, out, stream)
         return out
+
+    def state_from_field(self, field, stream=None):
+        """(state, mean_mode) on the field's device: the retained modes of a
+        physical-space perturbation (N1 x N2, the handle's real dtype)."""
+        n1, n2 = self.params.n_theta, self.params.n_phi
+        if field.dtype != self.rdtype or tuple(field.shape) != (n1, n2):
+            raise ValueError(f"field must be {self.rdtype} ({n1}, {n2})")
+        state = torch.empty(self.state_shape, dtype=self.cdtype, device=field.device)
+        mean = torch.empty(1, dtype=torch.float64, device=field.device)
+        flame_state_from_field(self.h, field, state, mean, stream)
+        return state, mean
 
     def fft_c2r(self, X, out=None, stream=None):
         n1, n2 = self.params.n_theta, self.params.n_phi

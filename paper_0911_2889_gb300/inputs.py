@@ -94,6 +94,17 @@ def random_direction(shape, seed, support=None, with_mean=False):
     return z / np.sqrt(np.sum(w * np.abs(z) ** 2))
 
 
+def physical_ic(n1, n2, seed, eps=1e-3):
+    """The paper's initial perturbation in physical space (Sec. 2):
+    Phi(theta, phi, t0) = eps * eta with eta in [-1, 1) drawn for every grid
+    point, float64 (n1, n2), row-major (j1 slowest).  eta = 2 u - 1 with u the
+    top 53 bits of SplitMix64 of the key  seed * 2^32  xor  (j1 * n2 + j2).
+    Its retained modes are the initial state (flame_state_from_field)."""
+    j = np.arange(n1 * n2, dtype=np.uint64).reshape(n1, n2)
+    u = uniform01((np.uint64(seed) << np.uint64(32)) ^ j)
+    return eps * (2.0 * u - 1.0)
+
+
 def real_field(n1, n2, seed):
     """Uniform random real field in [-1, 1), float64 (n1, n2)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n1, n2))

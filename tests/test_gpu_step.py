@@ -375,3 +375,42 @@ def test_ensemble_members_match_oracle(fl, orc):
         assert t.item() == tref
         assert abs(m.item() - mref) <= 1e-6 * abs(mref)
         f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,shape,tol", [
+    ("fp64", (32, 64), 1e-12), ("fp64", (128, 256), 1e-12),
+    ("fp32", (64, 128), 2e-5), ("fp32", (1024, 2048), 2e-5), ("fp32", (4096, 8192), 2e-5)])
+def test_state_from_field_matches_oracle(fl, orc, prec, shape, tol):
+    # Sec. 2's physical-space initial perturbation eps * eta, projected on the
+    # retained modes; both sides take the field rounded to the handle's type
+    n1, n2 = shape
+    f = fl.Flame(n1, n2, prec=prec)
+    field = torch.from_numpy(inputs.physical_ic(n1, n2, seed=11)).to(f.rdtype)
+    state, mean = f.state_from_field(field.cuda())
+    ref, mref = orc.state_from_field(_oparams(orc, f), field.double().numpy())
+    got = _host(fl, state)
+    assert _box_err(got, ref, f.K1) < tol
+    assert got[f.K1, 0] == 0
+    assert np.array_equal(got[:f.K1, 0], np.conj(got[f.K1 + 1:, 0][::-1]))
+    # worst-case rounding of the FFT's k = 0 sum, divided by N1 N2: unit
+    # roundoff x log2(N1 N2) x mean |field| (<= 5e-4): 1e-9 in FP32, 1e-17 in FP64
+    assert abs(mean.item() - mref) <= (1e-17 if prec == "fp64" else 1e-9)
+    f.close()
+
+
+@pytest.mark.gpu
+def test_steps_from_the_physical_initial_perturbation(fl, orc):
+    # the paper's runs: random eps * eta at t0 = 200, gamma = 0.8, FP64
+    n1, n2 = 128, 256
+    f = fl.Flame(n1, n2, prec="fp64")
+    field = inputs.physical_ic(n1, n2, seed=21)
+    state, mean = f.state_from_field(torch.from_numpy(field).cuda())
+    st0, m0 = orc.state_from_field(_oparams(orc, f), field)
+    t = torch.full((1,), float(f.params.t0), dtype=torch.float64, device="cuda")
+    f.step(state, mean, t, 5)
+    ref, mref, tref = orc.step(_oparams(orc, f), st0, m0, f.params.t0, 5)
+    assert _box_err(_host(fl, state), ref, f.K1) < 1e-12
+    assert abs(mean.item() - mref) <= 1e-12 * max(abs(mref), 1e-300) + 1e-18
+    assert t.item() == tref
+    f.close()
