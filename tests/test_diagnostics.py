@@ -1,0 +1,91 @@
+"""The averaged-velocity diagnostics of Sec. 2: the mean-mode update that
+<Phi_t> is read from (pinned on the oracle by Parseval), the power-law fit
+<Phi_t> ~ A (t - t*)^alpha (exact and noisy synthetic data), and the
+recording loop on the GPU against the oracle's trajectory."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_0911_2889_gb300 import diagnostics, inputs
+
+
+def test_mean_mode_rate_is_c_times_mean_squared_gradient():
+    # omega_0 = 0 in eq. (SivCurv1c), so one Euler step moves Phi_0 by
+    # dt c(t) sum_l |kappa_l|^2 |Phi_l|^2 over the full spectrum (Parseval for
+    # the mean of |grad Phi|^2), with c = 1/(2 r0^2) and r0 = t
+    n1, n2 = 32, 64
+    K1, K2 = inputs.default_K(n1), inputs.default_K(n2)
+    p = orc.Params(n1=n1, n2=n2, K1=K1, K2=K2, gamma=0.8, s1=1.0, s2=1.3, t0=200.0, dt=1e-3)
+    box = inputs.spectrum_ic(n1, n2, 6, seed=4, amp=0.05, K1=K1, K2=K2)
+    _, m1, _ = orc.step(p, box, 0.25, p.t0, 1)
+    k1 = np.arange(-K1, K1 + 1)[:, None]
+    k2 = np.arange(0, K2 + 1)[None, :]
+    kap2 = (p.s1 * k1) ** 2 + (p.s2 * k2) ** 2
+    w = np.where(k2 > 0, 2.0, 1.0)  # k2 > 0 entries stand for +-k; the k2 = 0 column is stored whole
+    grad2 = np.sum(w * kap2 * np.abs(box) ** 2)
+    c = 1.0 / (2.0 * p.t0 ** 2)
+    assert (m1 - 0.25) / p.dt == pytest.approx(c * grad2, rel=1e-12)
+
+
+def test_power_law_fit_exact_data():
+    t = np.linspace(200.0, 400.0, 41)
+    v = 2.5 * (t - 150.0) ** 0.76
+    A, alpha, ts, rms = diagnostics.fit_power_law(t, v)
+    assert alpha == pytest.approx(0.76, abs=1e-6)
+    assert ts == pytest.approx(150.0, abs=1e-3)
+    assert A == pytest.approx(2.5, rel=1e-5)
+    assert rms < 1e-8
+
+
+def test_power_law_fit_with_known_origin_is_linear_least_squares():
+    t = np.linspace(10.0, 50.0, 9)
+    v = 0.3 * (t - 4.0) ** 0.25
+    A, alpha, ts, rms = diagnostics.fit_power_law(t, v, t_star=4.0)
+    assert (A, alpha, ts) == (pytest.approx(0.3, rel=1e-12), pytest.approx(0.25, rel=1e-12), 4.0)
+    assert rms < 1e-12
+
+
+def test_power_law_fit_noisy_data():
+    rng = np.random.default_rng(0)
+    t = np.linspace(200.0, 600.0, 200)
+    v = 0.01 * (t - 120.0) ** 0.5 * np.exp(0.01 * rng.standard_normal(t.size))
+    A, alpha, ts, rms = diagnostics.fit_power_law(t, v, t_star=120.0)
+    assert alpha == pytest.approx(0.5, abs=0.02)
+    assert rms == pytest.approx(0.01, rel=0.2)
+
+
+def test_power_law_fit_rejects_bad_input():
+    with pytest.raises(ValueError):
+        diagnostics.fit_power_law([1.0, 2.0, 3.0], [1.0, -1.0, 2.0])
+    with pytest.raises(ValueError):
+        diagnostics.fit_power_law([1.0, 2.0], [1.0, 2.0])
+
+
+@pytest.mark.gpu
+def test_recorded_velocity_matches_oracle(fl, orc):
+    import torch
+    n1, n2 = 128, 256
+    f = fl.Flame(n1, n2, prec="fp64")
+    field = inputs.physical_ic(n1, n2, seed=5, eps=0.05)
+    state, mean = f.state_from_field(torch.from_numpy(field).cuda())
+    t = torch.full((1,), float(f.params.t0), dtype=torch.float64, device="cuda")
+    p = f.params
+    op = orc.Params(p.n_theta, p.n_phi, K1=p.K1, K2=p.K2, gamma=p.gamma, s1=p.s1, s2=p.s2, t0=p.t0, dt=p.dt)
+    st, m = orc.state_from_field(op, field)
+    rec = diagnostics.record(f, state, mean, t, nsteps=12, every=4, area=True)
+    tt = p.t0
+    means, ts = [m], [tt]
+    for _ in range(3):
+        st, m, tt = orc.step(op, st, m, tt, 4)
+        means.append(m)
+        ts.append(tt)
+    assert np.array_equal(rec["t"], np.array(ts))
+    assert np.allclose(rec["mean"], means, rtol=1e-12, atol=0)
+    # <Phi_t> is a difference of means ~1e-5 apart relatively: the increments
+    # agree to ~1e-12 and the FP64 rounding of the running mean adds ~1e-11
+    v_ref = np.diff(means) / np.diff(ts)
+    assert np.all(rec["velocity"] > 0)
+    assert np.allclose(rec["velocity"], v_ref, rtol=1e-9, atol=0)
+    area_ref = orc.area(op, st, m, tt)
+    assert rec["area"][-1] == pytest.approx(area_ref, rel=1e-12)
+    f.close()
