@@ -269,3 +269,42 @@ def half_weights(p: Params):
 def inner(p: Params, a, b) -> float:
     """<a, b> = Re sum over the full spectrum of conj(a) b (Hermitian a, b)."""
     return float(np.sum(half_weights(p) * np.real(np.conj(a) * b)))
+
+
+# ------------------------------------------------------------ circular flame
+def circular_step(K: int, gamma: float, s: float, t0: float, dt: float, phi, mean: float, t: float,
+                  nsteps: int = 1):
+    """The circular (two-dimensional) flame of Sec. 2: eq. (SivCurv1c) with
+    one wavenumber, written out with the literal convolution sum,
+        dPhi_k/dt = (-(s k)^2/r0^2 + gamma |s k|/(2 r0)) Phi_k
+                    - (1/(2 r0^2)) sum_l (s l)(s (k - l)) Phi_l Phi_{k-l},
+    over |l|, |k - l| <= K, r0 = t, with explicit Euler steps at the lattice
+    times t_n = t0 + n dt.  phi holds k = 0..K (phi[0] is ignored; the mean
+    mode Phi_0 is `mean`), Phi_{-k} = conj(Phi_k).  Plain loops, for small K.
+    Returns (phi, mean, t)."""
+    phi = np.array(phi, dtype=np.complex128).copy()
+    for _ in range(nsteps):
+        n = int(round((t - t0) / dt))
+        r0 = t0 + n * dt
+        c = 1.0 / (2.0 * r0 * r0)
+        full = {0: complex(mean)}
+        for k in range(1, K + 1):
+            full[k] = phi[k]
+            full[-k] = np.conj(phi[k])
+
+        def conv(k):
+            acc = 0.0 + 0.0j
+            for l in range(-K, K + 1):
+                if -K <= k - l <= K:
+                    acc += (s * l) * (s * (k - l)) * full[l] * full[k - l]
+            return -c * acc
+
+        new = phi.copy()
+        for k in range(1, K + 1):
+            kap = abs(s * k)
+            om = -kap * kap / (r0 * r0) + gamma * kap / (2.0 * r0)
+            new[k] = phi[k] + dt * (om * phi[k] + conv(k))
+        mean = mean + dt * conv(0).real
+        phi = new
+        t = t0 + (n + 1) * dt
+    return phi, mean, t

@@ -17,14 +17,14 @@ def test_mean_mode_rate_is_c_times_mean_squared_gradient():
     K1, K2 = inputs.default_K(n1), inputs.default_K(n2)
     p = orc.Params(n1=n1, n2=n2, K1=K1, K2=K2, gamma=0.8, s1=1.0, s2=1.3, t0=200.0, dt=1e-3)
     box = inputs.spectrum_ic(n1, n2, 6, seed=4, amp=0.05, K1=K1, K2=K2)
-    _, m1, _ = orc.step(p, box, 0.25, p.t0, 1)
+    _, m1, _ = orc.step(p, box, 0.0, p.t0, 1)  # from Phi_0 = 0: no cancellation in m1 - Phi_0
     k1 = np.arange(-K1, K1 + 1)[:, None]
     k2 = np.arange(0, K2 + 1)[None, :]
     kap2 = (p.s1 * k1) ** 2 + (p.s2 * k2) ** 2
     w = np.where(k2 > 0, 2.0, 1.0)  # k2 > 0 entries stand for +-k; the k2 = 0 column is stored whole
     grad2 = np.sum(w * kap2 * np.abs(box) ** 2)
     c = 1.0 / (2.0 * p.t0 ** 2)
-    assert (m1 - 0.25) / p.dt == pytest.approx(c * grad2, rel=1e-12)
+    assert m1 / p.dt == pytest.approx(c * grad2, rel=1e-12, abs=0)
 
 
 def test_power_law_fit_exact_data():

@@ -414,3 +414,30 @@ def test_steps_from_the_physical_initial_perturbation(fl, orc):
     assert abs(mean.item() - mref) <= 1e-12 * max(abs(mref), 1e-300) + 1e-18
     assert t.item() == tref
     f.close()
+
+
+@pytest.mark.gpu
+def test_circular_flame_through_the_2d_step(fl, orc):
+    # Sec. 2's circular flames (one wavenumber): a theta-independent state,
+    # only the k1 = 0 row of the box, on the smallest theta grid (N1 = 16,
+    # K1 = 1) evolves as the one-dimensional equation, here against its
+    # literal convolution sum
+    n1, n2, K1, K2 = 16, 256, 1, 63
+    f = fl.Flame(n1, n2, K1=K1, K2=K2, prec="fp64")
+    row = inputs.spectrum_ic(n1, n2, 32, 9, amp=1e-2, K1=K1, K2=K2)[K1].copy()
+    row[0] = 0.0
+    box = np.zeros((2 * K1 + 1, K2 + 1), dtype=np.complex128)
+    box[K1] = row
+    state = torch.from_numpy(fl.box_to_abi(box)).cuda()
+    mean = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), float(f.params.t0), dtype=torch.float64, device="cuda")
+    f.step(state, mean, t, 20)
+    p = f.params
+    ref, mref, tref = orc.circular_step(K2, p.gamma, p.s2, p.t0, p.dt, row, 0.0, p.t0, 20)
+    got = _host(fl, state)
+    assert rel_l2(got[K1, 1:], ref[1:]) < 1e-12
+    assert abs(mean.item() - mref) <= 1e-12 * abs(mref)
+    assert t.item() == tref
+    got[K1] = 0
+    assert np.abs(got).max() < 1e-13 * np.abs(ref).max()
+    f.close()
