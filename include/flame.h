@@ -178,6 +178,21 @@ flame_status flame_state_from_field(flame_t h, const void *field, void *state,
 flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
                         int nsteps, void *stream);
 
+/* Advances the state by nsteps steps of Heun's method, the explicit
+ * two-stage Runge-Kutta method of order 2, for eq. (SivCurv1c): a
+ * higher-order alternative to flame_step's explicit Euler (the paper leaves
+ * its integrator to its references).  With F the right-hand side of
+ * flame_step (mean mode included) and t_n = t0 + n dt,
+ *   k1 = F(Phi_n, t_n),  Phi* = Phi_n + dt k1,  k2 = F(Phi*, t_{n+1}),
+ *   Phi_{n+1} = Phi_n + (dt/2) (k1 + k2),  t <- t_{n+1}.
+ * It is computed as (Phi_n + E(E(Phi_n)))/2, E being flame_step's Euler step
+ * (E(Phi*) = Phi* + dt k2): two Euler steps and one combining kernel per
+ * step.  The k2 = 0 column is Hermitian on output when it is on input.
+ * Uses the handle's area workspace and scratch: calls on one handle must be
+ * ordered (one stream).  Arguments and errors as flame_step. */
+flame_status flame_step_heun(flame_t h, void *state, double *mean_mode, double *t,
+                             int nsteps, void *stream);
+
 /* Enqueues one pass of one step: pass 0 = A (derivatives and column
  * inverse FFT), 1 = B (row inverse FFT, |grad Phi|^2, row forward FFT),
  * 2 = C (column forward FFT, linear operator, Euler update, symmetrization,

@@ -308,3 +308,52 @@ def circular_step(K: int, gamma: float, s: float, t0: float, dt: float, phi, mea
         phi = new
         t = t0 + (n + 1) * dt
     return phi, mean, t
+
+
+# ------------------------------------------------------------ Heun's method
+def step_heun(p: Params, state, mean: float, t: float, nsteps: int = 1):
+    """Heun's method, the explicit two-stage Runge-Kutta method of order 2,
+    for eq. (SivCurv1c) (the paper leaves its integrator to its references),
+    written from its definition:
+        k1 = F(Phi_n, t_n),  Phi* = Phi_n + dt k1,  k2 = F(Phi*, t_{n+1}),
+        Phi_{n+1} = Phi_n + (dt/2) (k1 + k2),
+    with F_k = omega_k(t) Phi_k + c(t) ghat_k (k != 0), F_0 = c(t) ghat_0,
+    c = 1/(2 r0^2), r0 = t, ghat from grad2_hat, and each stage's k2 = 0
+    column symmetrised as in the Euler step (Sec. 3).  Returns (state, mean, t)."""
+    _check(p)
+    s = _c128(state).copy()
+    assert s.shape == p.box_shape
+    K1, K2 = p.K1, p.K2
+    lin = not (p.flags & NONLINEAR_ONLY)
+    nl = not (p.flags & LINEAR_ONLY)
+
+    def rhs(x, tn):
+        om = np.array([[omega(p, a, b, tn) for b in range(K2 + 1)] for a in range(-K1, K1 + 1)])
+        g = grad2_hat(p, x)
+        c = 1.0 / (2.0 * tn * tn)
+        F = np.zeros_like(x)
+        if lin:
+            F += om * x
+        if nl:
+            F += c * g
+        F[K1, 0] = 0.0
+        f0 = c * g[K1, 0].real if nl else 0.0
+        return F, f0
+
+    def sym(x):
+        x[:K1, 0] = np.conj(x[K1 + 1:, 0][::-1])
+        x[K1, 0] = 0.0
+
+    m = float(mean)
+    for _ in range(nsteps):
+        n = int(round((t - p.t0) / p.dt))
+        tn, tn1 = p.t0 + n * p.dt, p.t0 + (n + 1) * p.dt
+        F1, f1 = rhs(s, tn)
+        s1 = s + p.dt * F1
+        sym(s1)
+        F2, f2 = rhs(s1, tn1)
+        s = s + 0.5 * p.dt * (F1 + F2)
+        sym(s)
+        m = m + 0.5 * p.dt * (f1 + f2)
+        t = tn1
+    return s, m, t

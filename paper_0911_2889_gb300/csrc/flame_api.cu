@@ -130,7 +130,8 @@ struct flame_ctx {
     void *spec;       // c2r workspace, N1 x (N2/2 + 1)
     void *aw;         // area / adjoint workspace, N1 x ldk pairs
     double *rowsum;   // N1 per-row area sums
-    double *dscal;    // [1]: lambda_0, [2]: dgamma, [3]: dA/dPhi_0 scratch, [8..13]: step coefficients
+    double *dscal;    // [1]: lambda_0, [2]: dgamma, [3]: dA/dPhi_0 scratch, [4..5]: Heun's Phi_0, t;
+                      // [8..13]: step coefficients
     int *status;
     cudaStream_t cap;  // capture stream
     std::vector<GraphEntry> graphs;
@@ -645,6 +646,31 @@ flame_status flame_fft_c2r(flame_t h, const void *spec_in, void *real_out, void 
                                   M + 1, 1, static_cast<const C *>(h->tw1), s));
         CUDA_TRY(Ops<float>::rows_c2r(static_cast<const C *>(h->spec), static_cast<float *>(real_out),
                                       h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+    }
+    return FLAME_OK;
+}
+
+flame_status flame_step_heun(flame_t h, void *state, double *mean_mode, double *t, int nsteps, void *stream) {
+    if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step_heun: null pointer");
+    if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step_heun: nsteps=%d < 0", nsteps);
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_heun: injected launch fault");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long n = (2L * h->p.K1 + 1) * ((long)h->p.K2 + 1);
+    const FlameDesc d = make_desc(h, state, mean_mode, t);
+    double *sc = h->dscal + 4;
+    for (int i = 0; i < nsteps; ++i) {
+        // Phi_n (into the area workspace, which holds N1 ldk pairs >= the box), Phi_0 and t_n
+        CUDA_TRY(cudaMemcpyAsync(h->aw, state, (size_t)n * h->csz, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(sc, mean_mode, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(sc + 1, t, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(enqueue_step(h, d, s));
+        CUDA_TRY(enqueue_step(h, d, s));
+        if (h->p.prec == FLAME_FP64)
+            CUDA_TRY(Ops<double>::heun_combine(static_cast<const double2 *>(h->aw), static_cast<double2 *>(state), n,
+                                               sc, mean_mode, t, h->p.t0, h->p.dt, s));
+        else
+            CUDA_TRY(Ops<float>::heun_combine(static_cast<const float2 *>(h->aw), static_cast<float2 *>(state), n, sc,
+                                              mean_mode, t, h->p.t0, h->p.dt, s));
     }
     return FLAME_OK;
 }

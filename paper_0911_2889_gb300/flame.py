@@ -59,6 +59,7 @@ SIGNATURES = {
     "flame_fft_c2r": (_i, [_vp, _vp, _vp, _vp]),
     "flame_state_from_field": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "flame_step": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "flame_step_heun": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_step_pass": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
     "flame_area": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -172,6 +173,12 @@ def flame_step(h, state, mean_mode, t, nsteps=1, stream=None):
                              _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
 
 
+def flame_step_heun(h, state, mean_mode, t, nsteps=1, stream=None):
+    _check(load().flame_step_heun(ctypes.c_void_p(h), _ptr(state, name="state"),
+                                  _ptr(mean_mode, torch.float64, "mean_mode"),
+                                  _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
+
+
 def flame_step_pass(h, pass_, state, mean_mode, t, stream=None):
     _check(load().flame_step_pass(ctypes.c_void_p(h), int(pass_), _ptr(state, name="state"),
                                   _ptr(mean_mode, torch.float64, "mean_mode"),
@@ -273,6 +280,10 @@ class Flame:
         if state.dtype != self.cdtype or tuple(state.shape) != self.state_shape:
             raise ValueError(f"state must be {self.cdtype} {self.state_shape}")
         flame_step(self.h, state, mean_mode, t, nsteps, stream)
+
+    def step_heun(self, state, mean_mode, t, nsteps=1, stream=None):
+        """nsteps steps of Heun's second-order method (flame_step_heun)."""
+        flame_step_heun(self.h, state, mean_mode, t, nsteps, stream)
 
     def fft_r2c(self, x, out=None, stream=None):
         n1, n2 = self.params.n_theta, self.params.n_phi

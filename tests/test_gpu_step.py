@@ -441,3 +441,21 @@ def test_circular_flame_through_the_2d_step(fl, orc):
     got[K1] = 0
     assert np.abs(got).max() < 1e-13 * np.abs(ref).max()
     f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,shape,kmax,amp,tol,nsteps", [
+    ("fp64", (128, 256), 16, 1e-3, 1e-12, 5), ("fp32", (1024, 2048), 256, 1e-2, 2e-5, 1)])
+def test_heun_step_matches_oracle(fl, orc, prec, shape, kmax, amp, tol, nsteps):
+    # Heun's second-order step (two Euler steps averaged with the start)
+    # against the oracle's step written from the Runge-Kutta definition
+    n1, n2 = shape
+    f, st0, state, mean, t = _setup(fl, n1, n2, prec, kmax, 31, amp=amp)
+    f.step_heun(state, mean, t, nsteps)
+    ref, mref, tref = orc.step_heun(_oparams(orc, f), st0, 0.0, f.params.t0, nsteps)
+    got = _host(fl, state)
+    assert _box_err(got, ref, f.K1) < tol
+    assert np.array_equal(got[:f.K1, 0], np.conj(got[f.K1 + 1:, 0][::-1]))
+    assert abs(mean.item() - mref) <= (1e-12 if prec == "fp64" else 1e-6) * abs(mref)
+    assert t.item() == tref
+    f.close()
