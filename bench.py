@@ -357,7 +357,7 @@ def run_ours(args):
     if os.path.exists(prof):
         try:
             entry = json.load(open(prof)).get(f"{w['workload']}:pass{PASS_NAMES[dom]}")
-            if entry and entry.get("csrc_sha256") == kernel_sources_sha256():
+            if entry and entry.get("step_sources_sha256") == kernel_sources_sha256():
                 traffic = entry["dram_bytes_per_launch"]
         except (OSError, ValueError, KeyError):
             traffic = None
@@ -487,17 +487,25 @@ def run_suite(args):
             f.close()
 
 
+# The sources the FP32 step kernels (passes A, B, C and the fused CA) are
+# compiled from: their bodies, the line FFTs, the launch geometry, the
+# descriptors, and the translation units that instantiate them.  Host code
+# (flame_api.cu) and kernels off the step (adjoint, FP64, Heun, FFT pair)
+# are not in it.
+STEP_SOURCES = ("fft_engine.cuh", "flame_kernels.cuh", "flame_ops.cuh", "flame_internal.h",
+                "flame_f32_a.cu", "flame_f32_b.cu", "flame_f32_c.cu")
+
+
 def kernel_sources_sha256():
-    """Hash of the CUDA sources (csrc/*.cu, *.cuh, *.h), to tell whether an
+    """Hash of the step kernels' sources (STEP_SOURCES), to tell whether an
     ncu traffic figure was taken on the kernels that run now."""
     import hashlib
     d = os.path.join(ROOT, "paper_0911_2889_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as fh:
-                h.update(fh.read())
+    for name in STEP_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 

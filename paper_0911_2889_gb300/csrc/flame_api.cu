@@ -19,10 +19,12 @@
 #include "flame.h"
 #include "flame_internal.h"
 #include "fft_engine.cuh"
+#include "flame_heun.h"
 
 using flame::FlameDesc;
 using flame::Ops;
 using flame::StepArgs;
+using flame::heun_combine;
 
 namespace {
 
@@ -666,11 +668,11 @@ flame_status flame_step_heun(flame_t h, void *state, double *mean_mode, double *
         CUDA_TRY(enqueue_step(h, d, s));
         CUDA_TRY(enqueue_step(h, d, s));
         if (h->p.prec == FLAME_FP64)
-            CUDA_TRY(Ops<double>::heun_combine(static_cast<const double2 *>(h->aw), static_cast<double2 *>(state), n,
-                                               sc, mean_mode, t, h->p.t0, h->p.dt, s));
+            CUDA_TRY(heun_combine(static_cast<const double2 *>(h->aw), static_cast<double2 *>(state), n, sc,
+                                          mean_mode, t, h->p.t0, h->p.dt, s));
         else
-            CUDA_TRY(Ops<float>::heun_combine(static_cast<const float2 *>(h->aw), static_cast<float2 *>(state), n, sc,
-                                              mean_mode, t, h->p.t0, h->p.dt, s));
+            CUDA_TRY(heun_combine(static_cast<const float2 *>(h->aw), static_cast<float2 *>(state), n, sc,
+                                         mean_mode, t, h->p.t0, h->p.dt, s));
     }
     return FLAME_OK;
 }

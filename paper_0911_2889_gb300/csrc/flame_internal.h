@@ -101,9 +101,6 @@ template <class R> struct Ops {
     static cudaError_t rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s);
     static cudaError_t cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw,
                             cudaStream_t s);
-    // Heun's step from Phi_n (s0) and two Euler steps (s, in place)
-    static cudaError_t heun_combine(const C *s0, C *s, long n, const double *sc, double *mean, double *t, double t0,
-                                    double dt, cudaStream_t st);
     // retained modes of an r2c spectrum -> compact box + FP64 mean
     static cudaError_t box_from_spec(const C *spec, C *state, double *mean, int n1, int n2, int K1, int K2,
                                      cudaStream_t s);

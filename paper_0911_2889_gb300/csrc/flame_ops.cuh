@@ -171,13 +171,6 @@ template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStrea
 }
 
 template <class R>
-cudaError_t Ops<R>::heun_combine(const C *s0, C *s, long n, const double *sc, double *mean, double *t, double t0,
-                                 double dt, cudaStream_t st) {
-    const int blocks = (int)std::max<long>(1, std::min<long>((n + 255) / 256, 8L * sm_count()));
-    return launch_cl(k_heun_combine<R>, dim3(blocks), 256, 0, st, 1, s0, s, n, sc, mean, t, t0, dt);
-}
-
-template <class R>
 cudaError_t Ops<R>::box_from_spec(const C *spec, C *state, double *mean, int n1, int n2, int K1, int K2,
                                   cudaStream_t s) {
     const long total = (long)(2 * K1 + 1) * (K2 + 1);
