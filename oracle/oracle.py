@@ -4,7 +4,11 @@ TEST INFRASTRUCTURE ONLY: this module is imported by the test suite, by the
 smoke check and by the CPU-baseline leg of the benchmark, never by the
 product path.  It compiles ``flame_oracle.c`` with the host C compiler on
 first use (or when the source is newer than the built library) and exposes
-numpy-friendly wrappers.  All arrays are float64 / complex128.
+numpy-friendly wrappers.  Two oracle functions are written here in Python
+on top of the C primitives: Heun's step (``step_heun``, two right-hand-side
+evaluations per step from the Runge-Kutta definition) and the circular flame
+(``circular_step``, plain loops over the literal convolution sum).  All arrays
+are float64 / complex128.
 
 State layout (shared convention, not shared code): the compact half spectrum,
 rows k1 = -K1..K1, columns k2 = 0..K2, complex128 of shape (2K1+1, K2+1);
