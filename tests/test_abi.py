@@ -26,7 +26,8 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for need in ("flame_create", "flame_destroy", "flame_fft_r2c", "flame_fft_c2r",
-                 "flame_step", "flame_step_batch", "flame_adjoint", "flame_area"):
+                 "flame_step", "flame_step_batch", "flame_adjoint", "flame_area",
+                 "flame_step_heun", "flame_state_from_field"):
         assert need in names
 
 
@@ -65,6 +66,8 @@ def test_null_pointers_rejected(lib):
     p = _params()
     assert lib.flame_create(ctypes.byref(p), None) == 1
     assert lib.flame_step(None, None, None, None, 1, None) == 1
+    assert lib.flame_step_heun(None, None, None, None, 1, None) == 1
+    assert lib.flame_state_from_field(None, None, None, None, None) == 1
     assert lib.flame_fft_r2c(None, None, None, None) == 1
     assert lib.flame_fft_c2r(None, None, None, None) == 1
     assert lib.flame_step_pass(None, 0, None, None, None, None) == 1
