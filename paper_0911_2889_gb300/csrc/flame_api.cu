@@ -171,7 +171,6 @@ namespace {
 
 template <class R> flame_status alloc_tables(flame_ctx *h) {
     using C = typename Ops<R>::C;
-    CUDA_TRY(Ops<R>::prepare());
     CUDA_TRY(Ops<R>::init_twiddles(static_cast<C *>(h->tw1), h->logn1, h->cap));
     CUDA_TRY(Ops<R>::init_twiddles(static_cast<C *>(h->twm), h->logm, h->cap));
     return FLAME_OK;

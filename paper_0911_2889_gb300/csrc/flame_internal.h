@@ -133,7 +133,6 @@ template <class R> struct Ops {
     // One adjoint step at (d.state, d.t): pass A on the forward state, column
     // synthesis of lambda, row pass, column pass with the lambda update.
     static cudaError_t adj_step(const AdjDesc &d, cudaStream_t s);
-    static cudaError_t prepare();  // opt-in shared memory sizes (idempotent)
 };
 
 // Row pairs per tensor store of the uv write-out of pass A (<= 256).

@@ -17,10 +17,12 @@
 // between them) race on it and give wrong results.  Each call rewrites all of
 // the scratch it reads (tables, workspaces) and clears the status word, so
 // ordered calls of different sizes do not see each other's data.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "flame.h"
 #include "flame_internal.h"
@@ -36,7 +38,11 @@ constexpr size_t kNoAllocScratchBytes = 8u << 20;  // 8 MiB per device
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_ptr[kMaxDevices];  // device address per device, set on first use
+// Device address per device, set on the first call made on that device.
+// Calls may come from several host threads: the lookup is done once per
+// device under a mutex and published through an atomic.
+std::atomic<void *> g_scratch_ptr[kMaxDevices];
+std::mutex g_scratch_mu;
 
 // Errors are reported through flame_last_error(), like every other call.
 flame_status nfail(flame_status s, const char *fmt, ...) {
@@ -56,14 +62,18 @@ flame_status scratch_on_device(void **out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return nfail(FLAME_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return nfail(FLAME_EUNSUPPORTED, "device %d out of range", dev);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return nfail(FLAME_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
+    void *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        p = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            e = cudaGetSymbolAddress(&p, g_scratch);
+            if (e != cudaSuccess || !p)
+                return nfail(FLAME_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+            g_scratch_ptr[dev].store(p, std::memory_order_release);
+        }
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return FLAME_OK;
 }
 
@@ -80,8 +90,7 @@ flame_status run_steps(const flame::StepArgs &a, unsigned char *base, size_t off
                        size_t off_uv, size_t off_gk, size_t off_sc, void *state, double *mean, double *t,
                        int nsteps, cudaStream_t s) {
     using C = typename flame::Ops<R>::C;
-    cudaError_t e = flame::Ops<R>::prepare();
-    if (e == cudaSuccess) e = flame::Ops<R>::init_twiddles(reinterpret_cast<C *>(base + off_tw1), a.logn1, s);
+    cudaError_t e = flame::Ops<R>::init_twiddles(reinterpret_cast<C *>(base + off_tw1), a.logn1, s);
     if (e == cudaSuccess) e = flame::Ops<R>::init_twiddles(reinterpret_cast<C *>(base + off_twm), a.logm, s);
     double *dscal = reinterpret_cast<double *>(base + off_sc);
     int *status = reinterpret_cast<int *>(base + off_sc + 4 * sizeof(double));

@@ -158,10 +158,6 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { return make_geom<R>(logn, nlines, hint); }
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
-// Kernels opt in to large dynamic shared memory at their first launch
-// (opt_in); nothing to do ahead of time.
-template <class R> cudaError_t Ops<R>::prepare() { return cudaSuccess; }
-
 template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStream_t s) {
     // radix-16 table, then the radix-8 table (tw_alloc_len entries in all)
     const int len16 = tw_table_len(logN, 4), len8 = tw_table_len(logN, 3);

@@ -215,9 +215,28 @@ def flame_adjoint(h, state0, mean0, t_start, nsteps, ckpt_every, lambda_T, lambd
                                 _ptr(grad_gamma, f64, "grad_gamma"), _stream(stream)))
 
 
+def noalloc_state_spec(params: flame_params):
+    """(dtype, shape) the state of flame_step_noalloc must have for params:
+    K1, K2 = 0 resolved to floor((N - 1) / 4) as the library does."""
+    K1 = params.K1 if params.K1 > 0 else (params.n_theta - 1) // 4
+    K2 = params.K2 if params.K2 > 0 else (params.n_phi - 1) // 4
+    dtype = torch.complex128 if params.prec == FLAME_FP64 else torch.complex64
+    return dtype, (K2 + 1, 2 * K1 + 1)
+
+
 def flame_step_noalloc(params: flame_params, state, mean_mode, t, nsteps=1, stream=None):
     """flame_step for callers that cannot allocate: scratch is the library's
-    static device array (see include/flame.h)."""
+    static device array (see include/flame.h).  The library receives only
+    raw pointers, so the state's dtype and shape are checked here against
+    params: a buffer of the wrong precision or size would be read and
+    written past its end by the kernels."""
+    dtype, shape = noalloc_state_spec(params)
+    if not isinstance(state, torch.Tensor) or state.dtype != dtype or tuple(state.shape) != shape:
+        got = (state.dtype, tuple(state.shape)) if isinstance(state, torch.Tensor) else type(state)
+        raise ValueError(f"flame_step_noalloc: state must be {dtype} {shape}, got {got}")
+    for name, x in (("mean_mode", mean_mode), ("t", t)):
+        if not isinstance(x, torch.Tensor) or x.numel() < 1:
+            raise ValueError(f"flame_step_noalloc: {name} must be a tensor of at least one element")
     _check(load().flame_step_noalloc(ctypes.byref(params), _ptr(state, name="state"),
                                      _ptr(mean_mode, torch.float64, "mean_mode"),
                                      _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))

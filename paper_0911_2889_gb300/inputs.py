@@ -67,6 +67,28 @@ def spectrum_ic(n1, n2, kmax, seed, amp=1e-3, K1=None, K2=None):
     return z
 
 
+def flat_ic(n1, n2, seed, amp, K1=None, K2=None):
+    """Compact half-spectrum state with every retained mode of the same size:
+    Phi_k = amp * exp(2 pi i u_k) on the whole upper half of the box (the
+    edge row |k1| = K1 and the edge column k2 = K2 included), u_k drawn as in
+    spectrum_ic, the k2 = 0 column mirrored and Phi_0 = 0.  A test input that
+    gives the edges of the box as much weight as its interior."""
+    K1 = default_K(n1) if K1 is None else K1
+    K2 = default_K(n2) if K2 is None else K2
+    k1 = np.arange(-K1, K1 + 1, dtype=np.int64)[:, None]
+    k2 = np.arange(0, K2 + 1, dtype=np.int64)[None, :]
+    k1b, k2b = np.broadcast_arrays(k1, k2)
+    key = ((np.uint64(seed) << np.uint64(32))
+           ^ ((k1b + 2 ** 15).astype(np.uint64) << np.uint64(16))
+           ^ k2b.astype(np.uint64))
+    u = uniform01(key)
+    upper = (k2b > 0) | ((k2b == 0) & (k1b > 0))
+    z = np.where(upper, amp * np.exp(2j * np.pi * u), 0.0).astype(np.complex128)
+    z[:K1, 0] = np.conj(z[K1 + 1:, 0][::-1])
+    z[K1, 0] = 0.0
+    return z
+
+
 def hermitian_fix(z):
     """Returns z with the k2 = 0 column made conjugate-symmetric (k1 > 0 the
     master) and the k = 0 entry left as it is."""
