@@ -361,3 +361,101 @@ def step_heun(p: Params, state, mean: float, t: float, nsteps: int = 1):
         m = m + 0.5 * p.dt * (f1 + f2)
         t = tn1
     return s, m, t
+
+
+# ------------------------------------------- forcing and integrating factor
+def _forcing_terms(p: Params, forcing, forcing0):
+    """(F box, F_0) of the forcing term f_k of eq. (SivCurv1c), constant over
+    a call: F indexed [k1 + K1, k2] like the state (k = 0 entry ignored),
+    F_0 the mean-mode forcing.  None means f = 0 (the paper's runs)."""
+    if forcing is None:
+        F = np.zeros(p.box_shape, dtype=np.complex128)
+    else:
+        F = np.array(forcing, dtype=np.complex128).copy()
+        assert F.shape == p.box_shape
+    F[p.K1, 0] = 0.0
+    return F, float(forcing0)
+
+
+def _sym(p: Params, x):
+    """The symmetrization of Sec. 3 on the k2 = 0 column (k1 > 0 the master)
+    and the k = 0 slot cleared."""
+    K1 = p.K1
+    x[:K1, 0] = np.conj(x[K1 + 1:, 0][::-1])
+    x[K1, 0] = 0.0
+
+
+def step_forced(p: Params, state, mean: float, t: float, nsteps: int, forcing=None, forcing0=0.0):
+    """Explicit Euler steps of eq. (SivCurv1c) with its forcing term:
+        Phi_k <- Phi_k + dt (omega_k(t_n) Phi_k + c(t_n) ghat_k + f_k),
+        Phi_0 <- Phi_0 + dt (c(t_n) ghat_0 + f_0),
+    each step the Euler step of `step` (no forcing) plus dt f, then the
+    k2 = 0 column symmetrised.  Returns (state, mean, t)."""
+    F, f0 = _forcing_terms(p, forcing, forcing0)
+    s = _c128(state).copy()
+    m = float(mean)
+    for _ in range(nsteps):
+        s, m, t = step(p, s, m, t, 1)
+        s = s + p.dt * F
+        _sym(p, s)
+        m = m + p.dt * f0
+    return s, m, t
+
+
+def if_factor(p: Params, ta: float, tb: float):
+    """Exact propagator of the linear part of eq. (SivCurv1c) from ta to tb,
+    E_k = exp(int_ta^tb omega_k(s) ds), per box mode.  With r0 = t,
+        int omega = |kappa|^2 (1/tb - 1/ta) + (gamma |kappa| / 2) ln(tb / ta),
+    kappa = (s1 k1, s2 k2).  E_0 = 1 (omega_0 = 0); LINEAR_ONLY / NONLINEAR_ONLY
+    as in the step (the nonlinear-only flag drops the linear part: E = 1)."""
+    k1 = np.arange(-p.K1, p.K1 + 1, dtype=np.float64)[:, None]
+    k2 = np.arange(0, p.K2 + 1, dtype=np.float64)[None, :]
+    kap = np.hypot(p.s1 * k1, p.s2 * k2)
+    if p.flags & NONLINEAR_ONLY:
+        return np.ones(p.box_shape)
+    return np.exp(kap * kap * (1.0 / tb - 1.0 / ta) + 0.5 * p.gamma * kap * np.log(tb / ta))
+
+
+def step_if(p: Params, state, mean: float, t: float, nsteps: int = 1, forcing=None, forcing0=0.0):
+    """Integrating-factor second-order Runge-Kutta step (Lawson's method with
+    Heun's scheme) for eq. (SivCurv1c), the stiffness-robust integrator (the
+    paper leaves its time integration to its references).  Written from its
+    definition: with E_n = if_factor(t_n, t_{n+1}) the exact propagator of
+    the linear part, v(t) = E(t_n, t)^-1 Phi(t) obeys
+    dv/dt = E(t_n, t)^-1 (c(t) ghat(Phi) + f), and Heun's method on v gives
+        N_n  = c(t_n) ghat(Phi_n) + f,
+        Phi* = E_n (Phi_n + dt N_n),
+        N*   = c(t_{n+1}) ghat(Phi*) + f,
+        Phi_{n+1} = E_n (Phi_n + (dt/2) N_n) + (dt/2) N*,
+    the mean mode with E = 1, each stage's k2 = 0 column symmetrised
+    (Sec. 3), t_n = t0 + n dt.  The linear problem is propagated exactly.
+    Returns (state, mean, t)."""
+    _check(p)
+    F, f0 = _forcing_terms(p, forcing, forcing0)
+    s = _c128(state).copy()
+    assert s.shape == p.box_shape
+    K1 = p.K1
+    nl = not (p.flags & LINEAR_ONLY)
+
+    def nonlinear(x, tn):
+        c = 1.0 / (2.0 * tn * tn)
+        g = grad2_hat(p, x) if nl else np.zeros_like(x)
+        Nk = c * g + F
+        n0 = (c * g[K1, 0].real if nl else 0.0) + f0
+        Nk[K1, 0] = 0.0
+        return Nk, n0
+
+    m = float(mean)
+    for _ in range(nsteps):
+        n = int(round((t - p.t0) / p.dt))
+        tn, tn1 = p.t0 + n * p.dt, p.t0 + (n + 1) * p.dt
+        E = if_factor(p, tn, tn1)
+        N1, n1 = nonlinear(s, tn)
+        s1 = E * (s + p.dt * N1)
+        _sym(p, s1)
+        N2, n2 = nonlinear(s1, tn1)
+        s = E * (s + 0.5 * p.dt * N1) + 0.5 * p.dt * N2
+        _sym(p, s)
+        m = m + 0.5 * p.dt * (n1 + n2)
+        t = tn1
+    return s, m, t
