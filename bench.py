@@ -430,21 +430,25 @@ def run_suite(args):
                           "note": "graph-captured; L2-resident" if n1 * n2 <= 2 ** 21 else "graph-captured"}),
               flush=True)
         f.close()
-    # Heun's second-order step (flame_step_heun: two Euler steps and a
-    # combining kernel per step, launched per step, not graph-captured)
-    f = flame.Flame(4096, 8192, prec="fp32", gamma=0.8, t0=200.0, dt=1e-3)
-    st = torch.from_numpy(flame.box_to_abi(inputs.spectrum_ic(4096, 8192, 256, 0, K1=f.K1, K2=f.K2))).cuda().to(f.cdtype)
-    m = torch.zeros(1, dtype=torch.float64, device="cuda")
-    t = torch.full((1,), 200.0, dtype=torch.float64, device="cuda")
-    f.step_heun(st, m, t, 3)
-    torch.cuda.synchronize()
-    nh = 10
-    ms = _ev_time(lambda: f.step_heun(st, m, t, nh), s)
-    f.sync_status()
-    print(json.dumps({"suite": "heun-step-4096x8192-fp32", "steps": nh, "ms_per_step": ms / nh,
-                      "points_per_s": 4096 * 8192 * nh / (ms * 1e-3),
-                      "note": "two Euler steps + one combining kernel per step; steps back to back"}), flush=True)
-    f.close()
+    # the two-stage integrators (flame_step_heun, flame_step_if: two
+    # right-hand-side evaluations per step, the stage update in pass C's
+    # epilogue), graph-captured, steps back to back
+    for name in ("heun", "if"):
+        f = flame.Flame(4096, 8192, prec="fp32", gamma=0.8, t0=200.0, dt=1e-3)
+        st = torch.from_numpy(flame.box_to_abi(inputs.spectrum_ic(4096, 8192, 256, 0, K1=f.K1, K2=f.K2))).cuda().to(f.cdtype)
+        m = torch.zeros(1, dtype=torch.float64, device="cuda")
+        t = torch.full((1,), 200.0, dtype=torch.float64, device="cuda")
+        fn = f.step_heun if name == "heun" else f.step_if
+        nh = 10
+        fn(st, m, t, nh)  # capture the graph
+        torch.cuda.synchronize()
+        ms = _ev_time(lambda: fn(st, m, t, nh), s)
+        f.sync_status()
+        print(json.dumps({"suite": f"{name}-step-4096x8192-fp32", "steps": nh, "ms_per_step": ms / nh,
+                          "points_per_s": 4096 * 8192 * nh / (ms * 1e-3),
+                          "note": "two right-hand-side evaluations per step; graph-captured, steps back to back"}),
+              flush=True)
+        f.close()
     for (n1, n2, prec) in ((128, 256, "fp64"), (4096, 8192, "fp32")):
         # flame_state_from_field: r2c (rows, columns) into the workspace, then
         # the retained modes.  Bytes: the field read; the N1 x (N2/2+1)

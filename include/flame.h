@@ -165,18 +165,36 @@ flame_status flame_state_from_field(flame_t h, const void *field, void *state,
                                     double *mean_mode, void *stream);
 
 /* Advances the state by nsteps explicit Euler steps of eq. (SivCurv1c):
- *   Phi_k <- Phi_k + dt (omega_k(t_n) Phi_k + c(t_n) ghat_k)   (k != 0),
- *   Phi_0 <- Phi_0 + dt c(t_n) ghat_0,
- * where ghat is the box part of the normalised analysis of |grad Phi|^2,
+ *   Phi_k <- Phi_k + dt (omega_k(t_n) Phi_k + c(t_n) ghat_k + f_k)   (k != 0),
+ *   Phi_0 <- Phi_0 + dt (c(t_n) ghat_0 + f_0),
+ * where ghat is the box part of the normalised analysis of |grad Phi|^2 and
+ * f the forcing set by flame_set_forcing (f = 0 unless set, as in the
+ * paper's runs),
  * followed by the symmetrization of the k2 = 0 column (Sec. 3) and
  * t <- t0 + (n + 1) dt with n = round((t - t0)/dt).
  * state: compact box (see above), in place.  mean_mode, t: one device double
  * each, in place.  nsteps >= 0 (0 is a no-op).  For nsteps > 1 the step
  * sequence is replayed from a captured CUDA graph (captured on first use per
- * (state, mean_mode, t, nsteps) binding).  Non-finite results set
+ * (state, mean_mode, t, nsteps, forcing) binding).  Non-finite results set
  * FLAME_ENONFINITE in the handle's device status word. */
 flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
                         int nsteps, void *stream);
+
+/* Sets the forcing term f_k(t) of eq. (SivCurv1c) (Sec. 2; the paper's runs
+ * have f = 0) for the handle's later step calls (flame_step, flame_step_heun,
+ * flame_step_if, flame_step_batch and the adjoint's forward recomputation):
+ *   forcing   NULL (f_k = 0) or a caller-owned device box in the state's
+ *             layout and precision holding f_k for 0 < |k| in the box (the
+ *             k = 0 entry is ignored; the k2 = 0 column should be Hermitian
+ *             like the state's).  The library keeps the pointer, not a
+ *             copy: the caller keeps the buffer valid while it steps and may
+ *             change its contents between calls (a time-dependent forcing
+ *             is applied that way, constant within a call).
+ *   forcing0  f_0, the mean mode's forcing (FP64).
+ * The term enters the right-hand side additively.  Constant forcing leaves
+ * the step's Jacobian unchanged, so flame_adjoint stays the adjoint of the
+ * forced step.  EINVAL for a null handle or a non-finite forcing0. */
+flame_status flame_set_forcing(flame_t h, const void *forcing, double forcing0);
 
 /* Advances the state by nsteps steps of Heun's method, the explicit
  * two-stage Runge-Kutta method of order 2, for eq. (SivCurv1c): a
@@ -185,13 +203,31 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
  * flame_step (mean mode included) and t_n = t0 + n dt,
  *   k1 = F(Phi_n, t_n),  Phi* = Phi_n + dt k1,  k2 = F(Phi*, t_{n+1}),
  *   Phi_{n+1} = Phi_n + (dt/2) (k1 + k2),  t <- t_{n+1}.
- * It is computed as (Phi_n + E(E(Phi_n)))/2, E being flame_step's Euler step
- * (E(Phi*) = Phi* + dt k2): two Euler steps and one combining kernel per
- * step.  The k2 = 0 column is Hermitian on output when it is on input.
- * Uses the handle's area workspace and scratch: calls on one handle must be
+ * Each stage is one evaluation of the right-hand side (passes A, B) and a
+ * pass C whose epilogue applies the stage: the predictor keeps Phi_n, the
+ * corrector writes (Phi_n + Phi* + dt k2)/2.  Multi-step calls are
+ * graph-captured like flame_step's.  Uses the handle's area workspace and
+ * scratch to carry Phi_n between the stages: calls on one handle must be
  * ordered (one stream).  Arguments and errors as flame_step. */
 flame_status flame_step_heun(flame_t h, void *state, double *mean_mode, double *t,
                              int nsteps, void *stream);
+
+/* Advances the state by nsteps integrating-factor second-order Runge-Kutta
+ * steps (Lawson's method over Heun's scheme) of eq. (SivCurv1c): the
+ * stiffness-robust integrator (the paper leaves its time integration to its
+ * references).  The linear part omega_k(t) Phi_k is propagated exactly by
+ *   E_k = exp(int_{t_n}^{t_{n+1}} omega_k) = exp(-|kappa|^2 (1/t_n - 1/t_{n+1})
+ *         + (gamma |kappa|/2) ln(t_{n+1}/t_n))          (r0 = t),
+ * and the rest, N = c(t) ghat + f, by Heun's method in the propagated frame:
+ *   Phi* = E (Phi_n + dt N(Phi_n, t_n)),
+ *   Phi_{n+1} = E (Phi_n + (dt/2) N(Phi_n, t_n)) + (dt/2) N(Phi*, t_{n+1}),
+ * the mean mode with E = 1, each stage symmetrised (Sec. 3), t <- t_{n+1}.
+ * The linear problem is solved exactly and the step stays stable for
+ * dt |omega|_max well above explicit Euler's bound of 2.  E is evaluated per
+ * mode in the kernel's precision from FP64 step coefficients.  Same
+ * arguments, workspace use and errors as flame_step_heun. */
+flame_status flame_step_if(flame_t h, void *state, double *mean_mode, double *t,
+                           int nsteps, void *stream);
 
 /* Enqueues one pass of one step: pass 0 = A (derivatives and column
  * inverse FFT), 1 = B (row inverse FFT, |grad Phi|^2, row forward FFT),

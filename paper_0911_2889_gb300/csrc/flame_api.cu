@@ -19,12 +19,10 @@
 #include "flame.h"
 #include "flame_internal.h"
 #include "fft_engine.cuh"
-#include "flame_heun.h"
 
 using flame::FlameDesc;
 using flame::Ops;
 using flame::StepArgs;
-using flame::heun_combine;
 
 namespace {
 
@@ -114,10 +112,17 @@ bool flame::encode_uv_map(CUtensorMap *map, void *uv, int n1, int ldk) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Time-integration schemes of the multi-step entry points: explicit Euler,
+// Heun's method and the integrating-factor RK2 (Lawson-Heun) step, as
+// sequences of pass C stages (kStage*).
+enum Scheme { kSchemeEuler = 0, kSchemeHeun = 1, kSchemeIF = 2 };
+
 struct GraphEntry {
     const void *state;
     const double *mean, *t;
-    int n;
+    int n, scheme;
+    const void *forcing;  // the forcing in force when captured
+    double forcing0;
     cudaGraphExec_t exec;
 };
 
@@ -132,8 +137,8 @@ struct flame_ctx {
     void *spec;       // c2r workspace, N1 x (N2/2 + 1)
     void *aw;         // area / adjoint workspace, N1 x ldk pairs
     double *rowsum;   // N1 per-row area sums
-    double *dscal;    // [1]: lambda_0, [2]: dgamma, [3]: dA/dPhi_0 scratch, [4..5]: Heun's Phi_0, t;
-                      // [8..13]: step coefficients
+    double *dscal;    // [1]: lambda_0, [2]: dgamma, [3]: dA/dPhi_0 scratch, [4]: the mean-mode
+                      // term two-stage schemes carry between stages; [8..15]: step coefficients
     int *status;
     cudaStream_t cap;  // capture stream
     std::vector<GraphEntry> graphs;
@@ -165,6 +170,10 @@ struct flame_ctx {
     // L2 persisting window over the caller's state (passes A and C)
     size_t l2_state_bytes = 0;
     float l2_state_hit = 0.f;
+    // forcing term of eq. (SivCurv1c) (flame_set_forcing): caller-owned box
+    // or null, and the mean-mode forcing
+    const void *forcing = nullptr;
+    double forcing0 = 0.0;
 };
 
 namespace {
@@ -211,6 +220,13 @@ FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
     d.t_out = t;
     d.status = h->status;
     if (h->l2_state_bytes) d.l2_state = flame::L2Window{state, h->l2_state_bytes, h->l2_state_hit};
+    d.stage = flame::kStageEuler;
+    // the two-stage schemes carry one box between their stages in the area
+    // workspace (N1 (K2+1) pairs, larger than the box) and one FP64 scalar
+    d.save = h->aw;
+    d.save_mean = h->dscal + 4;
+    d.forcing = h->forcing;
+    d.forcing0 = h->forcing0;
     return d;
 }
 
@@ -226,13 +242,43 @@ cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
     return Ops<float>::passC(d, s);
 }
 
-// n steps with pass C of each step fused with pass A of the next:
-// A, (B, CA) x (n - 1), B, C.  Same arithmetic as n separate steps.
-cudaError_t enqueue_steps_fused(flame_ctx *h, const FlameDesc &d, int n, cudaStream_t s) {
-    cudaError_t e = Ops<float>::passA(d, s, h->var_a, h->map());
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        e = Ops<float>::passB(d, s, h->var_b, h->gmap());
-        if (e == cudaSuccess) e = i + 1 < n ? Ops<float>::passCA(d, s, h->map()) : Ops<float>::passC(d, s);
+// The pass C stages of one step of a scheme.
+int scheme_stages(int scheme, int *stages) {
+    if (scheme == kSchemeHeun) {
+        stages[0] = flame::kStageHeun1;
+        stages[1] = flame::kStageHeun2;
+        return 2;
+    }
+    if (scheme == kSchemeIF) {
+        stages[0] = flame::kStageIF1;
+        stages[1] = flame::kStageIF2;
+        return 2;
+    }
+    stages[0] = flame::kStageEuler;
+    return 1;
+}
+
+// n steps of a scheme: every stage is one evaluation of the right-hand side
+// (passes A and B) and a pass C that applies the stage's update.  With
+// fusion, pass C of each stage runs fused with pass A of the next:
+// A, (B, CA) x (stages - 1), B, C.  Same arithmetic as separate passes.
+cudaError_t enqueue_scheme(flame_ctx *h, FlameDesc d, int scheme, int n, cudaStream_t s) {
+    int st[2];
+    const int ns = scheme_stages(scheme, st);
+    const int total = ns * n;
+    cudaError_t e = cudaSuccess;
+    if (h->fuse && total > 1) {
+        e = Ops<float>::passA(d, s, h->var_a, h->map());
+        for (int i = 0; i < total && e == cudaSuccess; ++i) {
+            d.stage = st[i % ns];
+            e = Ops<float>::passB(d, s, h->var_b, h->gmap());
+            if (e == cudaSuccess) e = i + 1 < total ? Ops<float>::passCA(d, s, h->map()) : Ops<float>::passC(d, s);
+        }
+        return e;
+    }
+    for (int i = 0; i < total && e == cudaSuccess; ++i) {
+        d.stage = st[i % ns];
+        e = enqueue_step(h, d, s);
     }
     return e;
 }
@@ -398,15 +444,11 @@ flame_status autotune(flame_ctx *h) {
     return FLAME_OK;
 }
 
-// Captures n steps of one flame on the handle's capture stream.
-flame_status capture_steps(flame_ctx *h, const FlameDesc &d, int n, cudaGraphExec_t *out) {
+// Captures n steps of a scheme for one flame on the handle's capture stream.
+flame_status capture_steps(flame_ctx *h, const FlameDesc &d, int scheme, int n, cudaGraphExec_t *out) {
     cudaGraph_t graph = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = cudaSuccess;
-    if (h->fuse && n > 1)
-        le = enqueue_steps_fused(h, d, n, h->cap);
-    else
-        for (int i = 0; i < n && le == cudaSuccess; ++i) le = enqueue_step(h, d, h->cap);
+    cudaError_t le = enqueue_scheme(h, d, scheme, n, h->cap);
     cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
     if (le != cudaSuccess || ee != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -419,9 +461,11 @@ flame_status capture_steps(flame_ctx *h, const FlameDesc &d, int n, cudaGraphExe
     return FLAME_OK;
 }
 
-flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int n, cudaGraphExec_t *out) {
+flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int scheme, int n,
+                        cudaGraphExec_t *out) {
     for (auto &g : h->graphs)
-        if (g.state == state && g.mean == mean && g.t == t && g.n == n) {
+        if (g.state == state && g.mean == mean && g.t == t && g.n == n && g.scheme == scheme &&
+            g.forcing == h->forcing && g.forcing0 == h->forcing0) {
             *out = g.exec;
             return FLAME_OK;
         }
@@ -432,10 +476,35 @@ flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int 
         h->graphs.erase(h->graphs.begin());
     }
     cudaGraphExec_t exec;
-    flame_status st = capture_steps(h, make_desc(h, state, mean, t), n, &exec);
+    flame_status st = capture_steps(h, make_desc(h, state, mean, t), scheme, n, &exec);
     if (st != FLAME_OK) return st;
-    h->graphs.push_back(GraphEntry{state, mean, t, n, exec});
+    h->graphs.push_back(GraphEntry{state, mean, t, n, scheme, h->forcing, h->forcing0, exec});
     *out = exec;
+    return FLAME_OK;
+}
+
+// nsteps steps of a scheme: one step directly, more as CUDA graphs of up to
+// kGraphChunk steps (all captured before the first launch, so that a
+// capture failure leaves nothing enqueued).
+flame_status run_scheme(flame_ctx *h, void *state, double *mean, double *t, int scheme, int nsteps,
+                        cudaStream_t s) {
+    if (nsteps == 0) return FLAME_OK;
+    if (nsteps == 1) {
+        CUDA_TRY(enqueue_scheme(h, make_desc(h, state, mean, t), scheme, 1, s));
+        return FLAME_OK;
+    }
+    const int full = nsteps / kGraphChunk, rest = nsteps % kGraphChunk;
+    cudaGraphExec_t gfull = nullptr, grest = nullptr;
+    if (full) {
+        flame_status st = step_graph(h, state, mean, t, scheme, kGraphChunk, &gfull);
+        if (st != FLAME_OK) return st;
+    }
+    if (rest) {
+        flame_status st = step_graph(h, state, mean, t, scheme, rest, &grest);
+        if (st != FLAME_OK) return st;
+    }
+    for (int i = 0; i < full; ++i) CUDA_TRY(cudaGraphLaunch(gfull, s));
+    if (rest) CUDA_TRY(cudaGraphLaunch(grest, s));
     return FLAME_OK;
 }
 
@@ -655,51 +724,28 @@ flame_status flame_step_heun(flame_t h, void *state, double *mean_mode, double *
     if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step_heun: null pointer");
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step_heun: nsteps=%d < 0", nsteps);
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_heun: injected launch fault");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const long n = (2L * h->p.K1 + 1) * ((long)h->p.K2 + 1);
-    const FlameDesc d = make_desc(h, state, mean_mode, t);
-    double *sc = h->dscal + 4;
-    for (int i = 0; i < nsteps; ++i) {
-        // Phi_n (into the area workspace, which holds N1 ldk pairs >= the box), Phi_0 and t_n
-        CUDA_TRY(cudaMemcpyAsync(h->aw, state, (size_t)n * h->csz, cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(sc, mean_mode, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(sc + 1, t, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(enqueue_step(h, d, s));
-        CUDA_TRY(enqueue_step(h, d, s));
-        if (h->p.prec == FLAME_FP64)
-            CUDA_TRY(heun_combine(static_cast<const double2 *>(h->aw), static_cast<double2 *>(state), n, sc,
-                                          mean_mode, t, h->p.t0, h->p.dt, s));
-        else
-            CUDA_TRY(heun_combine(static_cast<const float2 *>(h->aw), static_cast<float2 *>(state), n, sc,
-                                         mean_mode, t, h->p.t0, h->p.dt, s));
-    }
-    return FLAME_OK;
+    return run_scheme(h, state, mean_mode, t, kSchemeHeun, nsteps, static_cast<cudaStream_t>(stream));
+}
+
+flame_status flame_step_if(flame_t h, void *state, double *mean_mode, double *t, int nsteps, void *stream) {
+    if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step_if: null pointer");
+    if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step_if: nsteps=%d < 0", nsteps);
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_if: injected launch fault");
+    return run_scheme(h, state, mean_mode, t, kSchemeIF, nsteps, static_cast<cudaStream_t>(stream));
 }
 
 flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, int nsteps, void *stream) {
     if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step: null pointer");
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step: nsteps=%d < 0", nsteps);
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step: injected launch fault");
-    if (nsteps == 0) return FLAME_OK;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (nsteps == 1) {
-        CUDA_TRY(enqueue_step(h, make_desc(h, state, mean_mode, t), s));
-        return FLAME_OK;
-    }
-    // All graphs are captured before the first one is launched, so that a
-    // capture failure leaves nothing enqueued.
-    const int full = nsteps / kGraphChunk, rest = nsteps % kGraphChunk;
-    cudaGraphExec_t gfull = nullptr, grest = nullptr;
-    if (full) {
-        flame_status st = step_graph(h, state, mean_mode, t, kGraphChunk, &gfull);
-        if (st != FLAME_OK) return st;
-    }
-    if (rest) {
-        flame_status st = step_graph(h, state, mean_mode, t, rest, &grest);
-        if (st != FLAME_OK) return st;
-    }
-    for (int i = 0; i < full; ++i) CUDA_TRY(cudaGraphLaunch(gfull, s));
-    if (rest) CUDA_TRY(cudaGraphLaunch(grest, s));
+    return run_scheme(h, state, mean_mode, t, kSchemeEuler, nsteps, static_cast<cudaStream_t>(stream));
+}
+
+flame_status flame_set_forcing(flame_t h, const void *forcing, double forcing0) {
+    if (!h) return fail(FLAME_EINVAL, "flame_set_forcing: null handle");
+    if (!std::isfinite(forcing0)) return fail(FLAME_EINVAL, "flame_set_forcing: forcing0 is not finite");
+    h->forcing = forcing;
+    h->forcing0 = forcing0;
     return FLAME_OK;
 }
 
@@ -980,8 +1026,13 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, c
         CUDA_TRY(cudaMemsetAsync(grad_gamma, 0, sizeof(double), s));
         return FLAME_OK;
     }
+    // the forward recomputations include the forcing in force (constant
+    // forcing leaves the step's Jacobian, hence the adjoint step, unchanged)
+    size_t f0bits = 0;
+    memcpy(&f0bits, &h->forcing0, sizeof f0bits);
     const std::vector<const void *> key{h->adj, reinterpret_cast<const void *>((size_t)nsteps),
-                                        reinterpret_cast<const void *>((size_t)ckpt_every)};
+                                        reinterpret_cast<const void *>((size_t)ckpt_every), h->forcing,
+                                        reinterpret_cast<const void *>(f0bits)};
     cudaGraphExec_t exec = nullptr;
     for (auto &g : h->adj_graphs)
         if (g.key == key) exec = g.exec;

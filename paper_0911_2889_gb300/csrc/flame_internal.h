@@ -13,6 +13,22 @@ constexpr unsigned kNonlinearOnly = 2u;
 constexpr int kStatusNonfinite = 0;
 constexpr int kStatusTimeout = 1;
 
+// Time-stepping stage of a pass C launch (the update its epilogue applies,
+// with F = omega Phi + N, N = c ghat + f the non-stiff part, E the exact
+// propagator of the linear part over the step):
+//   Euler:  Phi <- Phi + dt F(Phi)
+//   Heun1:  save <- Phi;  Phi <- Phi + dt F(Phi)                 (predictor)
+//   Heun2:  Phi <- (save + Phi + dt F(Phi)) / 2                  (corrector)
+//   IF1:    save <- E (Phi + dt/2 N);  Phi <- E (Phi + dt N)     (Lawson-Heun)
+//   IF2:    Phi <- save + dt/2 N(Phi)
+// The mean mode follows with omega_0 = 0, E_0 = 1.  Stages 1 advance t to
+// t_{n+1}; stages 2 evaluate at t_{n+1} and leave t there.
+constexpr int kStageEuler = 0;
+constexpr int kStageHeun1 = 1;
+constexpr int kStageHeun2 = 2;
+constexpr int kStageIF1 = 3;
+constexpr int kStageIF2 = 4;
+
 // Kernel variants chosen by the autotuner (0 = default shape).
 constexpr int kVariantDefault = 0;
 constexpr int kVariantDirect = 1;   // pass A: direct stores (no cluster write-out)
@@ -58,6 +74,17 @@ struct FlameDesc {
     double *mean;           // caller's mean mode
     double *t_out;          // caller's t (written by pass C)
     int *status;            // handle's device status word
+    // two-stage schemes: the stage of this pass C launch (kStage*) and the
+    // box-layout buffer and FP64 scalar that carry a term from stage 1 to
+    // stage 2 (unused by the Euler stage)
+    int stage;
+    void *save;
+    double *save_mean;
+    // forcing term f_k of eq. (SivCurv1c): a caller-owned box (same layout
+    // and precision as the state, k = 0 entry ignored) or null for f = 0,
+    // and the mean-mode forcing f_0
+    const void *forcing;
+    double forcing0;
     // L2 persisting window over the state for the launches of passes A and
     // C (a launch attribute, not read by the kernels); bytes = 0: none
     L2Window l2_state;

@@ -550,33 +550,44 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
 }
 
 // Step coefficients at t_n, evaluated in FP64 (then rounded for FP32).
+// The integrating factor of the linear part over [t_n, t_{n+1}] (r0 = t) is
+//   E_k = exp(int omega_k) = exp(-|kappa|^2 ia + |kappa| ib),
+//   ia = 1/t_n - 1/t_{n+1} = d/(t_n t_{n+1}),  ib = (gamma/2) ln(1 + d/t_n),
+// with d = t_{n+1} - t_n (exact in FP64), written without cancellation.
 struct Coef {
     double tn, a, b, c;  // a = 1/r0^2, b = gamma/(2 r0), c = 1/(2 r0^2)
+    double ia, ib;       // integrating-factor exponent coefficients
 };
 __device__ __forceinline__ Coef step_coef(const StepArgs &s, double t) {
     long n = __double2ll_rn((t - s.t0) / s.dt);
     double tn = s.t0 + (double)n * s.dt;
+    double tn1 = s.t0 + (double)(n + 1) * s.dt;
+    double dd = tn1 - tn;
     Coef k;
     k.tn = tn;
     k.a = 1.0 / (tn * tn);
     k.b = s.gamma / (2.0 * tn);
     k.c = 0.5 * k.a;
+    k.ia = dd / (tn * tn1);
+    k.ib = 0.5 * s.gamma * log1p(dd / tn);
     return k;
 }
 
 // The step coefficients in the kernel's precision: 1/r0^2, gamma/(2 r0),
-// c/(N1 N2) (c = 1/(2 r0^2) with the inverse transform's scale folded in)
-// and dt.  One thread of pass B derives them in FP64 for the whole step and
-// pass C loads them: GB300's FP64 pipe is narrow, and the divisions cost a
-// column-pass CTA more than its loads when every CTA derives them.
+// c/(N1 N2) (c = 1/(2 r0^2) with the inverse transform's scale folded in),
+// dt and the integrating-factor coefficients.  One thread of pass B derives
+// them in FP64 for the whole step and pass C loads them: GB300's FP64 pipe
+// is narrow, and the divisions cost a column-pass CTA more than its loads
+// when every CTA derives them.
 template <class R> struct CoefR {
-    R a, b, cs, dt;
+    R a, b, cs, dt, ia, ib;
 };
 template <class R> __device__ __forceinline__ CoefR<R> coef_r(const Coef &cf, const StepArgs &s) {
     const double inv = 1.0 / ((double)s.n1 * (double)s.n2);
-    return CoefR<R>{(R)cf.a, (R)cf.b, (R)(cf.c * inv), (R)s.dt};
+    return CoefR<R>{(R)cf.a, (R)cf.b, (R)(cf.c * inv), (R)s.dt, (R)cf.ia, (R)cf.ib};
 }
-// Layout of FlameDesc::coef: t_n, c, then CoefR<R> from byte 16.
+// Layout of FlameDesc::coef: t_n, c, then CoefR<R> from byte 16 (64 bytes
+// in all for FP64).
 template <class R> __device__ __forceinline__ void store_coef(double *coef, const StepArgs &s, double t) {
     const Coef cf = step_coef(s, t);
     coef[0] = cf.tn;
@@ -857,6 +868,9 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
     const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
     const R s1 = scale1<R>(a), s2 = scale2<R>(a);
+    const int stage = d.stage;  // block-uniform
+    const C *fa = d.forcing ? static_cast<const C *>(d.forcing) + (size_t)c0 * ld1 + a.K1 : nullptr;
+    C *va_save = d.save ? static_cast<C *>(d.save) + (size_t)c0 * ld1 + a.K1 : nullptr;
     int bad = 0;
     C nphi[E / 2][2];  // the updated entries (kept for the fused pass A of the next step)
 #pragma unroll
@@ -882,7 +896,35 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             const R kap = kappa_norm<R>(s1 * (R)k1, s2 * (R)k2);
             const R om = lin ? kap * (rb - kap * ra) : (R)0;
             const R cn = nl ? rcs : (R)0;
-            C nw{ph.x + rdt * (om * ph.x + cn * gh.x), ph.y + rdt * (om * ph.y + cn * gh.y)};
+            // the non-stiff part: c ghat (+ the forcing f_k)
+            C nt{cn * gh.x, cn * gh.y};
+            if (fa) {
+                const C f = fa[(side ? ld1 : 0) + k1];
+                nt = C{nt.x + f.x, nt.y + f.y};
+            }
+            C nw;
+            if (stage == kStageEuler || stage == kStageHeun1) {
+                nw = C{ph.x + rdt * (om * ph.x + nt.x), ph.y + rdt * (om * ph.y + nt.y)};
+                if (stage == kStageHeun1) va_save[(side ? ld1 : 0) + k1] = ph;
+            } else if (stage == kStageHeun2) {
+                const C sv = va_save[(side ? ld1 : 0) + k1];
+                const R h = (R)0.5;
+                nw = C{h * (sv.x + ph.x + rdt * (om * ph.x + nt.x)), h * (sv.y + ph.y + rdt * (om * ph.y + nt.y))};
+            } else if (stage == kStageIF1) {
+                // exact propagator of the linear part over the step
+                R ef = (R)1;
+                if (lin) {
+                    if constexpr (std::is_same<R, float>::value) ef = expf(kap * (cfs.ib - kap * cfs.ia));
+                    else ef = exp(kap * (cfs.ib - kap * cfs.ia));
+                }
+                const R hdt = (R)0.5 * rdt;
+                nw = C{ef * (ph.x + rdt * nt.x), ef * (ph.y + rdt * nt.y)};
+                va_save[(side ? ld1 : 0) + k1] = C{ef * (ph.x + hdt * nt.x), ef * (ph.y + hdt * nt.y)};
+            } else {  // kStageIF2
+                const C sv = va_save[(side ? ld1 : 0) + k1];
+                const R hdt = (R)0.5 * rdt;
+                nw = C{sv.x + hdt * nt.x, sv.y + hdt * nt.y};
+            }
             bad |= !(isfinite(nw.x) && isfinite(nw.y));
             col[k1] = nw;
             nphi[i][side] = nw;
@@ -894,9 +936,21 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         double rs = 0.0;
         for (int w = 0; w < (int)blockDim.x; w += span) rs += red[w];
         const double mg = rs / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
-        if (nl) *d.mean += a.dt * d.coef[1] * mg;
+        // dt times the mean mode's right-hand side (omega_0 = 0): c mg + f_0
+        double inc = nl ? a.dt * d.coef[1] * mg : 0.0;
+        if (d.forcing0 != 0.0) inc += a.dt * d.forcing0;
+        const double m = *d.mean;
         long n = __double2ll_rn((d.coef[0] - a.t0) / a.dt);
-        *d.t_out = a.t0 + (double)(n + 1) * a.dt;
+        if (stage == kStageEuler || stage == kStageHeun1 || stage == kStageIF1) {
+            if (stage == kStageHeun1) *d.save_mean = m;
+            if (stage == kStageIF1) *d.save_mean = m + 0.5 * inc;
+            *d.mean = m + inc;
+            *d.t_out = a.t0 + (double)(n + 1) * a.dt;
+        } else {
+            // second stages are evaluated at t_{n+1} and leave t there
+            *d.mean = stage == kStageHeun2 ? 0.5 * (*d.save_mean + m + inc) : *d.save_mean + 0.5 * inc;
+            *d.t_out = a.t0 + (double)n * a.dt;
+        }
     }
     if constexpr (FUSE_A && std::is_same<R, float>::value && LOG > 0) {
         // Pass A of the next step (a1, a2) on the two updated columns, from

@@ -60,6 +60,8 @@ SIGNATURES = {
     "flame_state_from_field": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "flame_step": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_step_heun": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "flame_step_if": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "flame_set_forcing": (_i, [_vp, _vp, ctypes.c_double]),
     "flame_step_pass": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
     "flame_area": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -177,6 +179,18 @@ def flame_step_heun(h, state, mean_mode, t, nsteps=1, stream=None):
     _check(load().flame_step_heun(ctypes.c_void_p(h), _ptr(state, name="state"),
                                   _ptr(mean_mode, torch.float64, "mean_mode"),
                                   _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
+
+
+def flame_step_if(h, state, mean_mode, t, nsteps=1, stream=None):
+    _check(load().flame_step_if(ctypes.c_void_p(h), _ptr(state, name="state"),
+                                _ptr(mean_mode, torch.float64, "mean_mode"),
+                                _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
+
+
+def flame_set_forcing(h, forcing=None, forcing0=0.0):
+    """forcing: None (f = 0) or a device box in the state's layout; the
+    library keeps the pointer, so the tensor must outlive the steps."""
+    _check(load().flame_set_forcing(ctypes.c_void_p(h), _optr(forcing, name="forcing"), float(forcing0)))
 
 
 def flame_step_pass(h, pass_, state, mean_mode, t, stream=None):
@@ -300,9 +314,28 @@ class Flame:
             raise ValueError(f"state must be {self.cdtype} {self.state_shape}")
         flame_step(self.h, state, mean_mode, t, nsteps, stream)
 
+    def _check_state(self, state):
+        if state.dtype != self.cdtype or tuple(state.shape) != self.state_shape:
+            raise ValueError(f"state must be {self.cdtype} {self.state_shape}")
+
     def step_heun(self, state, mean_mode, t, nsteps=1, stream=None):
         """nsteps steps of Heun's second-order method (flame_step_heun)."""
+        self._check_state(state)
         flame_step_heun(self.h, state, mean_mode, t, nsteps, stream)
+
+    def step_if(self, state, mean_mode, t, nsteps=1, stream=None):
+        """nsteps integrating-factor RK2 steps (flame_step_if)."""
+        self._check_state(state)
+        flame_step_if(self.h, state, mean_mode, t, nsteps, stream)
+
+    def set_forcing(self, forcing=None, forcing0=0.0):
+        """Forcing term f_k of eq. (SivCurv1c) for later steps (None: f = 0).
+        The handle keeps a reference to the tensor (the library keeps its
+        pointer)."""
+        if forcing is not None:
+            self._check_state(forcing)
+        flame_set_forcing(self.h, forcing, forcing0)
+        self._forcing = forcing
 
     def fft_r2c(self, x, out=None, stream=None):
         n1, n2 = self.params.n_theta, self.params.n_phi
