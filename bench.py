@@ -185,10 +185,13 @@ def _ev_time(fn, stream, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def measure_batched(flame, inputs, nflames=256, steps=20, warmup=3):
+def measure_batched(flame, inputs, nflames=256, steps=500, plain_steps=20):
     """Ensemble of uneven FP32 flames (grids uniform over 256x512, 512x1024,
-    1024x2048, size seed 1234, spectrum seeds 1000+i): one graph of grouped
-    launches per call, against the same flames stepped one by one."""
+    1024x2048, size seed 1234, spectrum seeds 1000+i), `steps` steps in one
+    flame_step_batch call (grouped launches, replayed 8-step graphs), against
+    the same flames stepped one by one (plain_steps steps each, graph-captured
+    flame_step calls).  Effective GB/s counts the 3-pass algorithmic bytes of
+    every flame's steps."""
     import torch
     grids = inputs.batch_grids(nflames)
     fl, ss, ms, ts = [], [], [], []
@@ -205,18 +208,60 @@ def measure_batched(flame, inputs, nflames=256, steps=20, warmup=3):
     torch.cuda.synchronize()
     t_batch = _ev_time(lambda: flame.flame_step_batch(hs, ss, ms, ts, nsteps=steps), s)
     for f, st, m, t in zip(fl, ss, ms, ts):
-        f.step(st, m, t, steps)  # capture each flame's graph
+        f.step(st, m, t, plain_steps)  # capture each flame's graph
     torch.cuda.synchronize()
-    t_plain = _ev_time(lambda: [f.step(st, m, t, steps) for f, st, m, t in zip(fl, ss, ms, ts)], s)
+    t_plain = _ev_time(lambda: [f.step(st, m, t, plain_steps) for f, st, m, t in zip(fl, ss, ms, ts)], s)
     for f in fl:
         f.sync_status()
-    pts = sum(n1 * n2 for n1, n2 in grids) * steps
+    pts_step = sum(n1 * n2 for n1, n2 in grids)
+    bytes_step = sum(sum(pass_bytes(n1, n2, f.K1, f.K2, 8)) for (n1, n2), f in zip(grids, fl))
     for f in fl:
         f.close()
+    rate = pts_step * steps / (t_batch * 1e-3)
+    plain = pts_step * plain_steps / (t_plain * 1e-3)
+    peak, kind = _peaks()
+    gbs = bytes_step * steps / (t_batch * 1e-3) / 1e9
     return {"workload": f"ensemble-{nflames}-uneven-fp32mixed", "steps": steps,
-            "value": pts / (t_batch * 1e-3), "unit": "points/s",
-            "plain_value": pts / (t_plain * 1e-3), "vs_plain": t_plain / t_batch,
-            "ms_per_step": t_batch / steps}
+            "value": rate, "unit": "points/s", "plain_value": plain, "plain_steps": plain_steps,
+            "vs_plain": rate / plain, "ms_per_step": t_batch / steps,
+            "effective_gbs": gbs, "frac_of_hbm": gbs / peak, "peak_kind": kind}
+
+
+def step_model_flops(n1, n2):
+    """Model flops of one step per grid point: three real 2-D transforms
+    (two inverse, one forward) at 2.5 N log2 N each (N = N1 N2) and about 5
+    pointwise flops (the product, the linear operator and the update)."""
+    import math
+    return 7.5 * math.log2(n1 * n2) + 5.0
+
+
+def measure_trajectory(flame, inputs, n1, n2, prec, kmax, nsteps, fp64_peak=None):
+    """A graph-captured nsteps-step flame_step call on one flame (seed 0,
+    gamma 0.8, t0 200, dt 1e-3): grid-point updates per second; FP64 also
+    against the measured FP64 FMA rate (model flops of step_model_flops)."""
+    import torch
+    s = torch.cuda.current_stream()
+    f = flame.Flame(n1, n2, prec=prec, gamma=0.8, t0=200.0, dt=1e-3)
+    st = torch.from_numpy(flame.box_to_abi(inputs.spectrum_ic(n1, n2, kmax, 0, K1=f.K1, K2=f.K2))).cuda().to(f.cdtype)
+    m = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), 200.0, dtype=torch.float64, device="cuda")
+    f.step(st, m, t, nsteps)  # capture the graphs
+    torch.cuda.synchronize()
+    ms = min(_ev_time(lambda: f.step(st, m, t, nsteps), s) for _ in range(3))
+    f.sync_status()
+    esz = 16 if prec == "fp64" else 8
+    bytes_step = sum(pass_bytes(n1, n2, f.K1, f.K2, esz)[:3])
+    f.close()
+    out = {"workload": f"trajectory-{n1}x{n2}-{prec}-{nsteps}steps", "steps": nsteps,
+           "value": n1 * n2 * nsteps / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms / nsteps,
+           "effective_gbs": bytes_step / (ms * 1e-3 / nsteps) / 1e9,
+           "note": "graph-captured steps; the working set is L2-resident"}
+    if prec == "fp64" and fp64_peak:
+        fl_rate = step_model_flops(n1, n2) * n1 * n2 / (ms * 1e-3 / nsteps)
+        out.update({"model_flops_per_point": step_model_flops(n1, n2), "achieved_gflops": fl_rate / 1e9,
+                    "fp64_peak_gflops": fp64_peak / 1e9, "peak_kind": "measured (flame_fma_peak)",
+                    "frac_of_fp64_peak": fl_rate / fp64_peak})
+    return out
 
 
 def measure_adjoint(flame, inputs, nsteps=200, ckpt=20, reps=2):
@@ -362,10 +407,14 @@ def run_ours(args):
         except (OSError, ValueError, KeyError):
             traffic = None
 
-    batched = adjoint = None
+    batched = adjoint = traj64 = traj32 = None
+    fp64_peak = None
     if not args.no_extras:
         batched = measure_batched(flame, inputs)
         adjoint = measure_adjoint(flame, inputs)
+        fp64_peak = flame.flame_fma_peak("fp64")
+        traj64 = measure_trajectory(flame, inputs, 128, 256, "fp64", 16, 100, fp64_peak)
+        traj32 = measure_trajectory(flame, inputs, 1024, 2048, "fp32", 256, 1000)
     clk.__exit__(None, None, None)
 
     if rank == 0:
@@ -397,6 +446,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "batched": batched,
             "adjoint": adjoint,
+            "fp64_128x256": traj64,
+            "fp32_1024x2048": traj32,
         }
         print(json.dumps(line), flush=True)
     f.close()

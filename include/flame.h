@@ -180,6 +180,23 @@ flame_status flame_state_from_field(flame_t h, const void *field, void *state,
 flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
                         int nsteps, void *stream);
 
+/* Records the averaged diagnostics of Sec. 2 on the device at every step of
+ * the handle's later step calls (flame_step, flame_step_heun, flame_step_if,
+ * flame_step_batch), from the mean-mode work of the column pass at no extra
+ * pass over memory.  rec: caller-owned device array of 4 * capacity doubles
+ * (NULL stops recording); the step with lattice index n (t_n -> t_{n+1},
+ * n = round((t_n - t0)/dt)) writes entry n mod capacity:
+ *   rec[4e + 0] = t_n,
+ *   rec[4e + 1] = Phi_0(t_n), the mean mode (mean radius = t_n + Phi_0),
+ *   rec[4e + 2] = <Phi_t>(t_n) = c(t_n) mean(|grad Phi_n|^2) + f_0, the
+ *                 averaged front velocity dPhi_0/dt of eq. (SivCurv1c),
+ *   rec[4e + 3] = NaN (reserved for the surface area).
+ * The values describe the state entering the step (for two-stage schemes,
+ * the first stage's).  The library keeps the pointer; graphs are captured
+ * per record binding.  EINVAL for a null handle or capacity < 1 with a
+ * non-NULL rec. */
+flame_status flame_set_record(flame_t h, double *rec, int capacity);
+
 /* Sets the forcing term f_k(t) of eq. (SivCurv1c) (Sec. 2; the paper's runs
  * have f = 0) for the handle's later step calls (flame_step, flame_step_heun,
  * flame_step_if, flame_step_batch and the adjoint's forward recomputation):
@@ -244,9 +261,15 @@ flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode
 /* Advances nflames independent flames (each with its own handle, state,
  * mean mode and time; grids may differ; all handles must have the same
  * precision) by nsteps steps.  Flames of equal grid size are grouped so that
- * each pass is one launch per size class; the nsteps loop is one captured
- * CUDA graph.  Results equal nflames separate flame_step calls.  hs, states,
- * mean_modes and ts are HOST arrays of nflames entries (device pointers). */
+ * each pass is one launch per size class; the steps run as a captured CUDA
+ * graph of 8 steps (fewer for a shorter call) replayed, one per binding of
+ * (handles, states, mean modes, times).  A new binding uploads its
+ * descriptors asynchronously on `stream` (from a pinned staging buffer of
+ * the first handle); only growing the first handle's descriptor buffers
+ * synchronises that stream.  Results equal nflames separate flame_step
+ * calls.  hs, states, mean_modes and ts are HOST arrays of nflames entries
+ * (device pointers).  Calls with the same first handle must be ordered
+ * (one stream). */
 flame_status flame_step_batch(const flame_t *hs, void *const *states,
                               double *const *mean_modes, double *const *ts,
                               int nflames, int nsteps, void *stream);
@@ -303,6 +326,15 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0,
  * values are not reported (there is no handle to read them from). */
 flame_status flame_step_noalloc(const flame_params *params, void *state, double *mean_mode,
                                 double *t, int nsteps, void *stream);
+
+/* Measured FMA throughput of the current device (the paper has no
+ * counterpart: a measurement utility for reporting the FP64 step against the
+ * FP64 rate it is bound by).  prec: FLAME_FP64 or FLAME_FP32_MIXED (scalar
+ * FP32 FMA).  Runs a calibration kernel of 8 independent FMA chains per
+ * thread on every SM, best of 3 timed runs, and writes the rate in FLOP/s
+ * (2 per FMA) to *flops_per_s (host).  Allocates a scratch buffer and a
+ * stream and synchronises.  EINVAL on a bad argument, ECUDA on a CUDA error. */
+flame_status flame_fma_peak(int prec, double *flops_per_s);
 
 /* Synchronises the handle's device status word and returns it
  * (FLAME_OK, FLAME_ENONFINITE or FLAME_ETIMEOUT); clears it. */

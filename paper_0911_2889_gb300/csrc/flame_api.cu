@@ -60,6 +60,7 @@ int ilog2(int n) {
 }
 
 constexpr int kGraphChunk = 256;  // steps per captured graph
+constexpr int kBatchChunk = 8;    // ensemble steps per captured graph
 constexpr int kGraphCache = 8;
 
 }  // namespace
@@ -123,6 +124,8 @@ struct GraphEntry {
     int n, scheme;
     const void *forcing;  // the forcing in force when captured
     double forcing0;
+    double *rec;          // the record in force when captured
+    int rec_cap;
     cudaGraphExec_t exec;
 };
 
@@ -146,9 +149,12 @@ struct flame_ctx {
     // descriptors, then the flames' uv maps and gk maps (FP32)
     void *batch_desc = nullptr;
     size_t batch_cap = 0;
+    void *batch_host = nullptr;  // pinned staging of the descriptors' upload
+    size_t batch_host_cap = 0;
+    cudaEvent_t batch_up = nullptr;  // recorded after the last upload from the staging
     std::vector<FlameDesc> batch_key;
-    int batch_n = 0;
-    cudaGraphExec_t batch_exec = nullptr;
+    // graphs of the current binding: (steps per launch, executable)
+    std::vector<std::pair<int, cudaGraphExec_t>> batch_graphs;
     // adjoint arena (grown on demand by flame_adjoint) and the graphs of its
     // calls, keyed by every pointer and size of the call
     void *adj = nullptr;
@@ -174,6 +180,10 @@ struct flame_ctx {
     // or null, and the mean-mode forcing
     const void *forcing = nullptr;
     double forcing0 = 0.0;
+    // per-step diagnostics record (flame_set_record): caller-owned device
+    // array of 4 rec_cap doubles, or null
+    double *rec = nullptr;
+    int rec_cap = 0;
 };
 
 namespace {
@@ -189,8 +199,10 @@ void free_ctx(flame_ctx *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     for (auto &g : h->adj_graphs) cudaGraphExecDestroy(g.exec);
-    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+    for (auto &g : h->batch_graphs) cudaGraphExecDestroy(g.second);
     cudaFree(h->batch_desc);
+    cudaFreeHost(h->batch_host);
+    if (h->batch_up) cudaEventDestroy(h->batch_up);
     cudaFree(h->tw1);
     cudaFree(h->twm);
     cudaFree(h->uv);
@@ -227,6 +239,8 @@ FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
     d.save_mean = h->dscal + 4;
     d.forcing = h->forcing;
     d.forcing0 = h->forcing0;
+    d.rec = h->rec;
+    d.rec_cap = h->rec_cap;
     return d;
 }
 
@@ -465,7 +479,7 @@ flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int 
                         cudaGraphExec_t *out) {
     for (auto &g : h->graphs)
         if (g.state == state && g.mean == mean && g.t == t && g.n == n && g.scheme == scheme &&
-            g.forcing == h->forcing && g.forcing0 == h->forcing0) {
+            g.forcing == h->forcing && g.forcing0 == h->forcing0 && g.rec == h->rec && g.rec_cap == h->rec_cap) {
             *out = g.exec;
             return FLAME_OK;
         }
@@ -478,7 +492,7 @@ flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int 
     cudaGraphExec_t exec;
     flame_status st = capture_steps(h, make_desc(h, state, mean, t), scheme, n, &exec);
     if (st != FLAME_OK) return st;
-    h->graphs.push_back(GraphEntry{state, mean, t, n, scheme, h->forcing, h->forcing0, exec});
+    h->graphs.push_back(GraphEntry{state, mean, t, n, scheme, h->forcing, h->forcing0, h->rec, h->rec_cap, exec});
     *out = exec;
     return FLAME_OK;
 }
@@ -741,6 +755,14 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, in
     return run_scheme(h, state, mean_mode, t, kSchemeEuler, nsteps, static_cast<cudaStream_t>(stream));
 }
 
+flame_status flame_set_record(flame_t h, double *rec, int capacity) {
+    if (!h) return fail(FLAME_EINVAL, "flame_set_record: null handle");
+    if (rec && capacity < 1) return fail(FLAME_EINVAL, "flame_set_record: capacity=%d < 1", capacity);
+    h->rec = rec;
+    h->rec_cap = rec ? capacity : 0;
+    return FLAME_OK;
+}
+
 flame_status flame_set_forcing(flame_t h, const void *forcing, double forcing0) {
     if (!h) return fail(FLAME_EINVAL, "flame_set_forcing: null handle");
     if (!std::isfinite(forcing0)) return fail(FLAME_EINVAL, "flame_set_forcing: forcing0 is not finite");
@@ -829,71 +851,108 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
     const size_t mofs = (dbytes + 127) & ~(size_t)127;  // maps: 64-byte aligned
     const size_t bytes = mofs + maps.size() * sizeof(CUtensorMap);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const bool same = h0->batch_exec && h0->batch_n == nsteps && h0->batch_key.size() == flat.size() &&
-                      memcmp(h0->batch_key.data(), flat.data(), dbytes) == 0;
+    const bool same = h0->batch_key.size() == flat.size() && memcmp(h0->batch_key.data(), flat.data(), dbytes) == 0;
     if (!same) {
-        if (h0->batch_exec) {
-            CUDA_TRY(cudaDeviceSynchronize());
-            cudaGraphExecDestroy(h0->batch_exec);
-            h0->batch_exec = nullptr;
-        }
-        if (h0->batch_cap < bytes) {
-            CUDA_TRY(cudaDeviceSynchronize());
-            cudaFree(h0->batch_desc);
-            h0->batch_desc = nullptr;
-            h0->batch_cap = 0;
-            if (cudaMalloc(&h0->batch_desc, bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(FLAME_ENOMEM, "flame_step_batch: descriptor allocation failed");
+        // A new binding: its graphs replace the old ones (an executable graph
+        // still in flight is freed when it completes) and its descriptors
+        // are uploaded on the caller's stream, after the work already
+        // enqueued there.  Only growing the buffers waits for that stream.
+        for (auto &g : h0->batch_graphs) cudaGraphExecDestroy(g.second);
+        h0->batch_graphs.clear();
+        h0->batch_key.clear();
+        if (h0->batch_cap < bytes || h0->batch_host_cap < bytes) {
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (h0->batch_cap < bytes) {
+                cudaFree(h0->batch_desc);
+                h0->batch_desc = nullptr;
+                h0->batch_cap = 0;
+                if (cudaMalloc(&h0->batch_desc, bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(FLAME_ENOMEM, "flame_step_batch: descriptor allocation failed");
+                }
+                h0->batch_cap = bytes;
             }
-            h0->batch_cap = bytes;
+            if (h0->batch_host_cap < bytes) {
+                cudaFreeHost(h0->batch_host);
+                h0->batch_host = nullptr;
+                h0->batch_host_cap = 0;
+                if (cudaMallocHost(&h0->batch_host, bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(FLAME_ENOMEM, "flame_step_batch: staging allocation failed");
+                }
+                h0->batch_host_cap = bytes;
+            }
+        } else if (h0->batch_up) {
+            // the staging buffer may still feed the previous upload: wait
+            // for that copy only
+            CUDA_TRY(cudaEventSynchronize(h0->batch_up));
         }
-        CUDA_TRY(cudaMemcpy(h0->batch_desc, flat.data(), dbytes, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(static_cast<char *>(h0->batch_desc) + mofs, maps.data(), maps.size() * sizeof(CUtensorMap),
-                            cudaMemcpyHostToDevice));
-        const FlameDesc *dev = static_cast<const FlameDesc *>(h0->batch_desc);
-        const CUtensorMap *dmaps = reinterpret_cast<const CUtensorMap *>(static_cast<char *>(h0->batch_desc) + mofs);
-        cudaGraph_t graph = nullptr;
-        CUDA_TRY(cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal));
+        if (!h0->batch_up) CUDA_TRY(cudaEventCreateWithFlags(&h0->batch_up, cudaEventDisableTiming));
+        char *hb = static_cast<char *>(h0->batch_host);
+        memcpy(hb, flat.data(), dbytes);
+        memcpy(hb + mofs, maps.data(), maps.size() * sizeof(CUtensorMap));
+        CUDA_TRY(cudaMemcpyAsync(h0->batch_desc, hb, bytes, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaEventRecord(h0->batch_up, s));
+        h0->batch_key = flat;
+    }
+    const FlameDesc *dev = static_cast<const FlameDesc *>(h0->batch_desc);
+    const CUtensorMap *dmaps = reinterpret_cast<const CUtensorMap *>(static_cast<char *>(h0->batch_desc) + mofs);
+    // one step of every flame: per pass, one grouped launch per size class
+    auto enqueue_steps = [&](int n, cudaStream_t q) -> cudaError_t {
         cudaError_t le = cudaSuccess;
-        for (int st = 0; st < nsteps && le == cudaSuccess; ++st) {
+        for (int st = 0; st < n && le == cudaSuccess; ++st) {
             for (int pass = 0; pass < 3 && le == cudaSuccess; ++pass) {
                 for (auto &rg : ranges) {
                     const StepArgs &a = flat[rg.first].a;
                     const FlameDesc *d = dev + rg.first;
-                    const int n = (int)rg.second;
+                    const int nf = (int)rg.second;
                     const size_t ci = &rg - &ranges[0];
                     const flame_ctx *hc = class_handle[ci];
                     const CUtensorMap *um = class_maps[ci] ? dmaps + rg.first : nullptr;
                     const CUtensorMap *gm = class_maps[ci] ? dmaps + flat.size() + rg.first : nullptr;
                     if (h0->p.prec == FLAME_FP64)
-                        le = pass == 0 ? Ops<double>::passA_batch(d, n, a, h0->cap, hc->var_a)
-                           : pass == 1 ? Ops<double>::passB_batch(d, n, a, h0->cap, hc->var_b)
-                                       : Ops<double>::passC_batch(d, n, a, h0->cap);
+                        le = pass == 0 ? Ops<double>::passA_batch(d, nf, a, q, hc->var_a)
+                           : pass == 1 ? Ops<double>::passB_batch(d, nf, a, q, hc->var_b)
+                                       : Ops<double>::passC_batch(d, nf, a, q);
                     else
-                        le = pass == 0 ? Ops<float>::passA_batch(d, n, a, h0->cap, hc->var_a, um)
-                           : pass == 1 ? Ops<float>::passB_batch(d, n, a, h0->cap, hc->var_b, gm)
-                                       : Ops<float>::passC_batch(d, n, a, h0->cap);
+                        le = pass == 0 ? Ops<float>::passA_batch(d, nf, a, q, hc->var_a, um)
+                           : pass == 1 ? Ops<float>::passB_batch(d, nf, a, q, hc->var_b, gm)
+                                       : Ops<float>::passC_batch(d, nf, a, q);
                     if (le != cudaSuccess) break;
                 }
             }
         }
-        cudaError_t ee = cudaStreamEndCapture(h0->cap, &graph);
+        return le;
+    };
+    // graphs of kBatchChunk steps (fewer for a short call), replayed
+    auto graph_of = [&](int n, cudaGraphExec_t *out) -> flame_status {
+        for (auto &g : h0->batch_graphs)
+            if (g.first == n) {
+                *out = g.second;
+                return FLAME_OK;
+            }
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = enqueue_steps(n, h0->cap);
+        const cudaError_t ee = cudaStreamEndCapture(h0->cap, &graph);
         if (le != cudaSuccess || ee != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return fail(FLAME_ECUDA, "flame_step_batch capture: %s",
-                        cudaGetErrorString(le != cudaSuccess ? le : ee));
+            return fail(FLAME_ECUDA, "flame_step_batch capture: %s", cudaGetErrorString(le != cudaSuccess ? le : ee));
         }
-        cudaError_t ie = cudaGraphInstantiate(&h0->batch_exec, graph, 0);
+        const cudaError_t ie = cudaGraphInstantiate(out, graph, 0);
         cudaGraphDestroy(graph);
-        if (ie != cudaSuccess) {
-            h0->batch_exec = nullptr;
-            return fail(FLAME_ECUDA, "flame_step_batch instantiate: %s", cudaGetErrorString(ie));
-        }
-        h0->batch_key = flat;
-        h0->batch_n = nsteps;
-    }
-    CUDA_TRY(cudaGraphLaunch(h0->batch_exec, s));
+        if (ie != cudaSuccess) return fail(FLAME_ECUDA, "flame_step_batch instantiate: %s", cudaGetErrorString(ie));
+        h0->batch_graphs.emplace_back(n, *out);
+        return FLAME_OK;
+    };
+    const int chunk = nsteps < kBatchChunk ? nsteps : kBatchChunk;
+    const int full = nsteps / chunk, rest = nsteps % chunk;
+    cudaGraphExec_t gfull = nullptr, grest = nullptr;
+    flame_status st = graph_of(chunk, &gfull);
+    if (st == FLAME_OK && rest) st = graph_of(rest, &grest);
+    if (st != FLAME_OK) return st;
+    for (int i = 0; i < full; ++i) CUDA_TRY(cudaGraphLaunch(gfull, s));
+    if (rest) CUDA_TRY(cudaGraphLaunch(grest, s));
     return FLAME_OK;
 }
 
@@ -964,7 +1023,10 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, c
     double *lam0 = h->dscal + 1, *dgam = h->dscal + 2;
     const bool f64 = h->p.prec == FLAME_FP64;
     auto step1 = [&](void *st, double *m, double *t, cudaStream_t q) -> cudaError_t {
-        return enqueue_step(h, make_desc(h, st, m, t), q);
+        FlameDesc d = make_desc(h, st, m, t);
+        d.rec = nullptr;  // the recomputed steps are not recorded
+        d.rec_cap = 0;
+        return enqueue_step(h, d, q);
     };
     // The forward sweep, the recomputations and the adjoint steps run on the
     // handle's arena only (the caller's inputs are copied in before, the

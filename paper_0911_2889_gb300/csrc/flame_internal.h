@@ -85,6 +85,12 @@ struct FlameDesc {
     // and the mean-mode forcing f_0
     const void *forcing;
     double forcing0;
+    // per-step record of the averaged diagnostics (Sec. 2), or null: entry
+    // n mod rec_cap (4 doubles) of the step t_n -> t_{n+1} gets t_n, Phi_0(t_n)
+    // and <Phi_t>(t_n) = c(t_n) mean |grad Phi_n|^2 + f_0 (the mean mode's
+    // right-hand side), and a NaN area slot; written by the first stage
+    double *rec;
+    int rec_cap;
     // L2 persisting window over the state for the launches of passes A and
     // C (a launch attribute, not read by the kernels); bytes = 0: none
     L2Window l2_state;

@@ -941,6 +941,13 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         if (d.forcing0 != 0.0) inc += a.dt * d.forcing0;
         const double m = *d.mean;
         long n = __double2ll_rn((d.coef[0] - a.t0) / a.dt);
+        if (d.rec && stage != kStageHeun2 && stage != kStageIF2) {
+            double *e = d.rec + 4 * (size_t)(((n % d.rec_cap) + d.rec_cap) % d.rec_cap);
+            e[0] = d.coef[0];
+            e[1] = m;
+            e[2] = (nl ? d.coef[1] * mg : 0.0) + d.forcing0;
+            e[3] = __longlong_as_double(0x7ff8000000000000LL);  // no area in this record
+        }
         if (stage == kStageEuler || stage == kStageHeun1 || stage == kStageIF1) {
             if (stage == kStageHeun1) *d.save_mean = m;
             if (stage == kStageIF1) *d.save_mean = m + 0.5 * inc;

@@ -10,8 +10,11 @@ the explicit step advances Phi_0 by dt c(t_n) mean(|grad Phi|^2) (FP64, in
 the step's column pass), and the velocity between two records is the change
 of Phi_0 over the elapsed time.
 
-The recording loop drives the C ABI (flame_step, flame_area) and reads two
-FP64 scalars back per record; the power-law fit is host-side least squares.
+Two ways to record: `record` drives the C ABI in chunks (flame_step,
+flame_area) and reads FP64 scalars back per chunk; `record_steps` lets the
+step kernels write t, Phi_0 and <Phi_t> for every step into a device array
+(flame_set_record) during one multi-step call.  The power-law fit is
+host-side least squares.
 """
 from __future__ import annotations
 
@@ -56,6 +59,31 @@ def record(flame, state, mean_mode, t, nsteps, every, area=False, stream=None):
     if area:
         out["area"] = np.array(As)
     return out
+
+
+def record_steps(flame, state, mean_mode, t, nsteps, scheme="euler", stream=None):
+    """Runs nsteps steps in one call (flame_step, flame_step_heun or
+    flame_step_if) with the per-step device record on (flame_set_record):
+    the step kernels write t_n, Phi_0(t_n) and <Phi_t>(t_n) for every step,
+    so the run needs no host read-back until it ends.  Returns a dict of
+    host float64 arrays over the nsteps states entering the steps: t, mean,
+    radius (= t + Phi_0), velocity (<Phi_t>)."""
+    import torch
+
+    if nsteps < 1:
+        raise ValueError("nsteps must be >= 1")
+    rec = torch.full((nsteps, 4), float("nan"), dtype=torch.float64, device=state.device)
+    flame.set_record(rec)
+    try:
+        step = {"euler": flame.step, "heun": flame.step_heun, "if": flame.step_if}[scheme]
+        step(state, mean_mode, t, nsteps, stream)
+    finally:
+        flame.set_record(None)
+    r = rec.cpu().numpy()
+    # entry n mod nsteps belongs to lattice step n: put them in time order
+    order = np.argsort(r[:, 0])
+    r = r[order]
+    return {"t": r[:, 0], "mean": r[:, 1], "radius": r[:, 0] + r[:, 1], "velocity": r[:, 2]}
 
 
 def _loglinear(t, v, t_star):

@@ -62,11 +62,13 @@ SIGNATURES = {
     "flame_step_heun": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_step_if": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_set_forcing": (_i, [_vp, _vp, ctypes.c_double]),
+    "flame_set_record": (_i, [_vp, _vp, _i]),
     "flame_step_pass": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
     "flame_area": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "flame_adjoint": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "flame_step_noalloc": (_i, [ctypes.POINTER(flame_params), _vp, _vp, _vp, _i, _vp]),
+    "flame_fma_peak": (_i, [_i, ctypes.POINTER(ctypes.c_double)]),
     "flame_sync_status": (_i, [_vp]),
     "flame_status_str": (ctypes.c_char_p, [_i]),
     "flame_last_error": (ctypes.c_char_p, []),
@@ -193,6 +195,14 @@ def flame_set_forcing(h, forcing=None, forcing0=0.0):
     _check(load().flame_set_forcing(ctypes.c_void_p(h), _optr(forcing, name="forcing"), float(forcing0)))
 
 
+def flame_set_record(h, rec=None):
+    """rec: None or a float64 CUDA tensor of shape (capacity, 4)."""
+    if rec is not None and (rec.dim() != 2 or rec.shape[1] != 4):
+        raise ValueError("flame_set_record: rec must have shape (capacity, 4)")
+    cap = 0 if rec is None else int(rec.shape[0])
+    _check(load().flame_set_record(ctypes.c_void_p(h), _optr(rec, torch.float64, "rec"), cap))
+
+
 def flame_step_pass(h, pass_, state, mean_mode, t, stream=None):
     _check(load().flame_step_pass(ctypes.c_void_p(h), int(pass_), _ptr(state, name="state"),
                                   _ptr(mean_mode, torch.float64, "mean_mode"),
@@ -254,6 +264,13 @@ def flame_step_noalloc(params: flame_params, state, mean_mode, t, nsteps=1, stre
     _check(load().flame_step_noalloc(ctypes.byref(params), _ptr(state, name="state"),
                                      _ptr(mean_mode, torch.float64, "mean_mode"),
                                      _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
+
+
+def flame_fma_peak(prec="fp64") -> float:
+    """Measured FMA rate of the current device in FLOP/s (flame_fma_peak)."""
+    out = ctypes.c_double(0.0)
+    _check(load().flame_fma_peak({"fp64": FLAME_FP64, "fp32": FLAME_FP32_MIXED}[prec], ctypes.byref(out)))
+    return out.value
 
 
 def flame_sync_status(h):
@@ -327,6 +344,13 @@ class Flame:
         """nsteps integrating-factor RK2 steps (flame_step_if)."""
         self._check_state(state)
         flame_step_if(self.h, state, mean_mode, t, nsteps, stream)
+
+    def set_record(self, rec=None):
+        """Per-step diagnostics record on the device (flame_set_record):
+        rec is None or a float64 CUDA tensor (capacity, 4) of rows (t_n,
+        Phi_0(t_n), <Phi_t>(t_n), area or NaN).  The handle keeps a reference."""
+        flame_set_record(self.h, rec)
+        self._rec = rec
 
     def set_forcing(self, forcing=None, forcing0=0.0):
         """Forcing term f_k of eq. (SivCurv1c) for later steps (None: f = 0).

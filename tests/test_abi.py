@@ -96,3 +96,22 @@ def test_binding_loads_without_gpu_and_fails_loudly():
     from paper_0911_2889_gb300 import flame
     with pytest.raises(ValueError):
         flame._ptr(torch.zeros(4), name="x")
+
+
+def test_new_entry_points_reject_bad_arguments(lib):
+    # null handles and bad arguments are refused before any device work
+    assert lib.flame_step_if(None, None, None, None, 1, None) == 1
+    assert lib.flame_set_forcing(None, None, 0.0) == 1
+    assert lib.flame_set_record(None, None, 0) == 1
+    out = ctypes.c_double(0.0)
+    assert lib.flame_fma_peak(7, ctypes.byref(out)) == 1
+    assert lib.flame_fma_peak(0, None) == 1
+
+
+@pytest.mark.gpu
+def test_fma_peak_is_plausible(lib):
+    from paper_0911_2889_gb300 import flame
+    f64 = flame.flame_fma_peak("fp64")
+    f32 = flame.flame_fma_peak("fp32")
+    # GB300: about 1.2 TFLOP/s FP64 and 80 TFLOP/s FP32 (scalar FMA) nominal
+    assert 1e11 < f64 < 1e13 and 1e13 < f32 < 2e14 and f32 > 10 * f64

@@ -89,3 +89,51 @@ def test_recorded_velocity_matches_oracle(fl, orc):
     area_ref = orc.area(op, st, m, tt)
     assert rec["area"][-1] == pytest.approx(area_ref, rel=1e-12)
     f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-12), ("fp32", 1e-6)])
+@pytest.mark.parametrize("scheme", ["euler", "heun", "if"])
+def test_device_record_matches_oracle_every_step(fl, prec, rtol, scheme):
+    # the per-step record written by the column pass: t_n, Phi_0(t_n) and
+    # <Phi_t>(t_n) = c(t_n) mean |grad Phi_n|^2 against the oracle's trajectory
+    import torch
+    n1, n2, nsteps = 128, 256, 12
+    f = fl.Flame(n1, n2, prec=prec, gamma=0.8, t0=20.0, dt=1e-2)
+    st0 = inputs.spectrum_ic(n1, n2, 32, 51, amp=2e-2, K1=f.K1, K2=f.K2)
+    state = torch.from_numpy(fl.box_to_abi(st0)).cuda().to(f.cdtype)
+    st0 = fl.abi_to_box(state.cpu().numpy()).astype(np.complex128)
+    mean = torch.full((1,), 0.01, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), 20.0, dtype=torch.float64, device="cuda")
+    out = diagnostics.record_steps(f, state, mean, t, nsteps, scheme=scheme)
+    p = orc.Params(n1, n2, K1=f.K1, K2=f.K2, gamma=0.8, t0=20.0, dt=1e-2)
+    s, m, tt = st0, 0.01, 20.0
+    stepper = {"euler": orc.step, "heun": orc.step_heun, "if": orc.step_if}[scheme]
+    for n in range(nsteps):
+        rate = 1.0 / (2.0 * tt * tt) * orc.grad2_hat(p, s)[p.K1, 0].real
+        assert out["t"][n] == tt
+        assert out["mean"][n] == pytest.approx(m, rel=1e-12 if prec == "fp64" else 1e-7)
+        assert out["velocity"][n] == pytest.approx(rate, rel=rtol)
+        s, m, tt = stepper(p, s, m, tt, 1)
+    assert np.allclose(out["radius"], out["t"] + out["mean"], rtol=0, atol=0)
+    f.close()
+
+
+@pytest.mark.gpu
+def test_device_record_wraps_around(fl):
+    # a record of capacity 5 over 12 steps keeps the last 5 (entry n mod 5)
+    import torch
+    f = fl.Flame(64, 128, prec="fp64", gamma=0.8, t0=20.0, dt=1e-2)
+    st0 = inputs.spectrum_ic(64, 128, 16, 52, amp=2e-2, K1=f.K1, K2=f.K2)
+    state = torch.from_numpy(fl.box_to_abi(st0)).cuda()
+    mean = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), 20.0, dtype=torch.float64, device="cuda")
+    rec = torch.full((5, 4), float("nan"), dtype=torch.float64, device="cuda")
+    f.set_record(rec)
+    f.step(state, mean, t, 12)
+    f.set_record(None)
+    r = rec.cpu().numpy()
+    for n in range(7, 12):
+        assert r[n % 5, 0] == pytest.approx(20.0 + n * 1e-2, rel=1e-15)
+    assert np.all(np.isnan(r[:, 3]))
+    f.close()
