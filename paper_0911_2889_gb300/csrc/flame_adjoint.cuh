@@ -395,7 +395,7 @@ template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>
     __shared__ CoefR<R> cfs;
     Coef cf{};  // thread 0 only
     if (threadIdx.x == 0) {
-        cf = step_coef(a, *d.t);
+        cf = step_coef(a, *d.t, false);
         cfs = coef_r<R>(cf, a);
     }
     fft_line<-1, LOG>(x, a.logn1, t, sm, static_cast<const C *>(d.tw1));

@@ -558,18 +558,23 @@ struct Coef {
     double tn, a, b, c;  // a = 1/r0^2, b = gamma/(2 r0), c = 1/(2 r0^2)
     double ia, ib;       // integrating-factor exponent coefficients
 };
-__device__ __forceinline__ Coef step_coef(const StepArgs &s, double t) {
+// (ia, ib are derived only for the integrating-factor stage: the FP64 log
+// costs the deriving thread microseconds on GB300's narrow FP64 pipe.)
+__device__ __forceinline__ Coef step_coef(const StepArgs &s, double t, bool if_stage) {
     long n = __double2ll_rn((t - s.t0) / s.dt);
     double tn = s.t0 + (double)n * s.dt;
-    double tn1 = s.t0 + (double)(n + 1) * s.dt;
-    double dd = tn1 - tn;
     Coef k;
     k.tn = tn;
     k.a = 1.0 / (tn * tn);
     k.b = s.gamma / (2.0 * tn);
     k.c = 0.5 * k.a;
-    k.ia = dd / (tn * tn1);
-    k.ib = 0.5 * s.gamma * log1p(dd / tn);
+    k.ia = k.ib = 0.0;
+    if (if_stage) {
+        const double tn1 = s.t0 + (double)(n + 1) * s.dt;
+        const double dd = tn1 - tn;
+        k.ia = dd / (tn * tn1);
+        k.ib = 0.5 * s.gamma * log1p(dd / tn);
+    }
     return k;
 }
 
@@ -588,8 +593,9 @@ template <class R> __device__ __forceinline__ CoefR<R> coef_r(const Coef &cf, co
 }
 // Layout of FlameDesc::coef: t_n, c, then CoefR<R> from byte 16 (64 bytes
 // in all for FP64).
-template <class R> __device__ __forceinline__ void store_coef(double *coef, const StepArgs &s, double t) {
-    const Coef cf = step_coef(s, t);
+template <class R> __device__ __forceinline__ void store_coef(double *coef, const StepArgs &s, double t,
+                                                              bool if_stage) {
+    const Coef cf = step_coef(s, t, if_stage);
     coef[0] = cf.tn;
     coef[1] = cf.c;
     *reinterpret_cast<CoefR<R> *>(coef + 2) = coef_r<R>(cf, s);
@@ -628,7 +634,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len_e<E>(M) + M);
     auto sm = make_planes_e<E>(base, M);  // (E = 8 pads one slot every 8: st_raw/ld_raw)
     const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
-    if (tile == 0 && threadIdx.x == 0) store_coef<R>(d.coef, a, *d.t_in);
+    if (tile == 0 && threadIdx.x == 0) store_coef<R>(d.coef, a, *d.t_in, d.stage == kStageIF1);
     constexpr bool STW = kSharedTw<R, LOG, E>;
     constexpr int LS = STW ? LOG : 8;
     C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * (2 * plane_len_e<E>(M) + M));
@@ -780,7 +786,10 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
 // is written from its k1 > 0 half and its conjugate mirror; the block owning
 // column 0 sums G[j1][0] in FP64 for the mean mode and advances t.  The state
 // entries of the epilogue are loaded after the transform.
-template <class R, int LOG, bool FUSE_A = false, int E = 16>
+// GEN = false compiles the plain Euler step without forcing or record (the
+// hot path); GEN = true reads the stage, forcing and record from the
+// descriptor.
+template <class R, int LOG, bool FUSE_A = false, int E = 16, bool GEN = true>
 __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
@@ -868,9 +877,9 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
     const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
     const R s1 = scale1<R>(a), s2 = scale2<R>(a);
-    const int stage = d.stage;  // block-uniform
-    const C *fa = d.forcing ? static_cast<const C *>(d.forcing) + (size_t)c0 * ld1 + a.K1 : nullptr;
-    C *va_save = d.save ? static_cast<C *>(d.save) + (size_t)c0 * ld1 + a.K1 : nullptr;
+    const int stage = GEN ? d.stage : kStageEuler;  // block-uniform
+    const C *fa = GEN && d.forcing ? static_cast<const C *>(d.forcing) + (size_t)c0 * ld1 + a.K1 : nullptr;
+    C *va_save = GEN && d.save ? static_cast<C *>(d.save) + (size_t)c0 * ld1 + a.K1 : nullptr;
     int bad = 0;
     C nphi[E / 2][2];  // the updated entries (kept for the fused pass A of the next step)
 #pragma unroll
@@ -938,14 +947,14 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         const double mg = rs / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
         // dt times the mean mode's right-hand side (omega_0 = 0): c mg + f_0
         double inc = nl ? a.dt * d.coef[1] * mg : 0.0;
-        if (d.forcing0 != 0.0) inc += a.dt * d.forcing0;
+        if (GEN && d.forcing0 != 0.0) inc += a.dt * d.forcing0;
         const double m = *d.mean;
         long n = __double2ll_rn((d.coef[0] - a.t0) / a.dt);
-        if (d.rec && stage != kStageHeun2 && stage != kStageIF2) {
+        if (GEN && d.rec && stage != kStageHeun2 && stage != kStageIF2) {
             double *e = d.rec + 4 * (size_t)(((n % d.rec_cap) + d.rec_cap) % d.rec_cap);
             e[0] = d.coef[0];
             e[1] = m;
-            e[2] = (nl ? d.coef[1] * mg : 0.0) + d.forcing0;
+            e[2] = (nl ? d.coef[1] * mg : 0.0) + (GEN ? d.forcing0 : 0.0);
             e[3] = __longlong_as_double(0x7ff8000000000000LL);  // no area in this record
         }
         if (stage == kStageEuler || stage == kStageHeun1 || stage == kStageIF1) {
@@ -1082,15 +1091,16 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBt(FlameDesc d, int 
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passB8(FlameDesc d, int pf) {
     passB_body<R, LOG, 8>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
-    passC_body<R, LOG>(d, blockIdx.x, gridDim.x, pf);
+template <class R, int LOG, bool GEN = true>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
+    passC_body<R, LOG, false, 16, GEN>(d, blockIdx.x, gridDim.x, pf);
 }
 // pass C of one step fused with pass A of the next (FP32, compile-time
 // lengths): the updated column pair is transformed back and written to uv
 // by tensor stores (the uv map of k_passAt)
-template <class R, int LOG>
+template <class R, int LOG, bool GEN = true>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passCA(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
-    passC_body<R, LOG, true>(d, blockIdx.x, gridDim.x, pf, &tm);
+    passC_body<R, LOG, true, 16, GEN>(d, blockIdx.x, gridDim.x, pf, &tm);
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA_n(const FlameDesc *__restrict__ ds, int pf) {

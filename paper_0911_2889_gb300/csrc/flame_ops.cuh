@@ -155,6 +155,12 @@ template <class R, int L> static constexpr int cluster_of() {
 }
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Whether pass C needs its general epilogue (a two-stage scheme's stage,
+// forcing or the per-step record) or the plain Euler one.
+static bool general_epilogue(const FlameDesc &d) {
+    return d.stage != kStageEuler || d.forcing != nullptr || d.forcing0 != 0.0 || d.rec != nullptr;
+}
+
 template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { return make_geom<R>(logn, nlines, hint); }
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
@@ -320,10 +326,16 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
     }
     Geom g = geom_cols(d.a.logn1, (d.a.K2 + 2) / 2, 0);
     cudaError_t err = cudaSuccess;
+    const bool gen = general_epilogue(d);
     with_log<R>(d.a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        const int pf = resident_ctas((const void *)k_passC<R, L>, g);
-        err = launch_w(d.l2_state, k_passC<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+        if (gen) {
+            const int pf = resident_ctas((const void *)k_passC<R, L, true>, g);
+            err = launch_w(d.l2_state, k_passC<R, L, true>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+        } else {
+            const int pf = resident_ctas((const void *)k_passC<R, L, false>, g);
+            err = launch_w(d.l2_state, k_passC<R, L, false>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+        }
     });
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
@@ -336,8 +348,15 @@ cudaError_t Ops<R>::passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap
     with_log<R>(d.a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         if constexpr (sizeof(R) == 4 && L > 0) {
-            const int pf = resident_ctas((const void *)k_passCA<R, L>, g);
-            err = launch_w(d.l2_state, k_passCA<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
+            if (general_epilogue(d)) {
+                const int pf = resident_ctas((const void *)k_passCA<R, L, true>, g);
+                err = launch_w(d.l2_state, k_passCA<R, L, true>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf,
+                               *uv_map);
+            } else {
+                const int pf = resident_ctas((const void *)k_passCA<R, L, false>, g);
+                err = launch_w(d.l2_state, k_passCA<R, L, false>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf,
+                               *uv_map);
+            }
         }
     });
     if (err != cudaSuccess) return err;
