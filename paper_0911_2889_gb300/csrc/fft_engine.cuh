@@ -33,15 +33,18 @@ template <class R> struct VecOf;
 template <> struct VecOf<float> { using type = float2; using c = float2; };
 template <> struct VecOf<double> { using type = double2; using c = double2; };
 
+// A negated operand of the paired instructions is free on sm_100+ (it is an
+// operand modifier): vsub and the complex multiply below use it instead of
+// a multiplication by a {-1, -1} constant.
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
-    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 vbc(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 vzero(float2) { return make_float2(0.f, 0.f); }
 
+__device__ __forceinline__ double2 vneg(double2 a) { return make_double2(-a.x, -a.y); }
 __device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
@@ -68,10 +71,11 @@ template <int S, class V> __device__ __forceinline__ CV<V> cadd_rot(CV<V> a, CV<
 template <int S, class V> __device__ __forceinline__ CV<V> csub_rot(CV<V> a, CV<V> b) {
     return cadd_rot<-S>(a, b);
 }
-// a * (wr + i wi) with the same scalar twiddle on both lines
+// a * (wr + i wi) with the same scalar twiddle on both lines: two paired
+// multiplies and two paired FMAs (the subtraction is a negated addend)
 template <class V, class R> __device__ __forceinline__ CV<V> cmul_s(CV<V> a, R wr, R wi) {
     V vr = vbc(wr), vi = vbc(wi);
-    return {vsub(vmul(a.re, vr), vmul(a.im, vi)), vfma(a.re, vi, vmul(a.im, vr))};
+    return {vfma(a.re, vr, vneg(vmul(a.im, vi))), vfma(a.re, vi, vmul(a.im, vr))};
 }
 template <class V, class R> __device__ __forceinline__ CV<V> cscale(CV<V> a, R s) {
     V v = vbc(s);
@@ -105,11 +109,11 @@ template <int E, int R, int DIR, class V> __device__ __forceinline__ CV<V> tw_co
     constexpr double ci = DIR * Roots16::s[e];
     if constexpr (ci == 0.0) {
         if constexpr (cr > 0) return a;
-        else return {vsub(vzero(a.re), a.re), vsub(vzero(a.im), a.im)};
+        else return {vneg(a.re), vneg(a.im)};  // folds into the consumer
     } else if constexpr (cr == 0.0) {
         // multiply by +-i
-        if constexpr (ci > 0) return {vsub(vzero(a.re), a.im), a.re};
-        else return {a.im, vsub(vzero(a.im), a.re)};
+        if constexpr (ci > 0) return {vneg(a.im), a.re};
+        else return {a.im, vneg(a.re)};
     } else if constexpr (cr == ci || cr == -ci) {
         // (cr + i ci) a = cr (a + i (ci/cr) a)
         constexpr int sg = (cr == ci) ? 1 : -1;

@@ -368,6 +368,41 @@ __device__ __forceinline__ void fft_line_e(CV<V> (&x)[E], int logn, int t, const
 constexpr int kTwSmemBytes = 6144;  // >= (480 + 64 + 4096/64) * 8
 template <class R, int LOG, int E> constexpr bool kSharedTw = std::is_same<R, float>::value && LOG >= 8 && E == 16;
 
+// cos and sin of k pi / 16, k = 0..15: the factors exp(i pi r / E) (E = 16,
+// or E = 8 at every second k) that relate the real-transform twiddles of
+// the E points of one thread (see passB_body).
+struct Roots32 {
+    static constexpr double c[16] = {1.0, 0.980785280403230449126182236134239037, 0.923879532511286756128183189396788933,
+                                     0.831469612302545237078788377617905756, 0.707106781186547524400844362104849039,
+                                     0.555570233019602224742830813948532874, 0.382683432365089771728459984030398866,
+                                     0.195090322016128267848284868477022240, 0.0, -0.195090322016128267848284868477022240,
+                                     -0.382683432365089771728459984030398866, -0.555570233019602224742830813948532874,
+                                     -0.707106781186547524400844362104849039, -0.831469612302545237078788377617905756,
+                                     -0.923879532511286756128183189396788933, -0.980785280403230449126182236134239037};
+    static constexpr double s[16] = {0.0, 0.195090322016128267848284868477022240, 0.382683432365089771728459984030398866,
+                                     0.555570233019602224742830813948532874, 0.707106781186547524400844362104849039,
+                                     0.831469612302545237078788377617905756, 0.923879532511286756128183189396788933,
+                                     0.980785280403230449126182236134239037, 1.0, 0.980785280403230449126182236134239037,
+                                     0.923879532511286756128183189396788933, 0.831469612302545237078788377617905756,
+                                     0.707106781186547524400844362104849039, 0.555570233019602224742830813948532874,
+                                     0.382683432365089771728459984030398866, 0.195090322016128267848284868477022240};
+};
+
+// a * b + c with one rounding, in the precision of the arguments (explicit,
+// so that every kernel built from the same body rounds alike)
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// b * exp(i pi r / E) * sgn with the factor a compile-time constant
+template <int R_, int E, int SGN, class C> __device__ __forceinline__ C mul_root(C b) {
+    using Real = decltype(C::x);
+    constexpr int k = R_ * (16 / E);
+    constexpr Real cr = (Real)(SGN * Roots32::c[k]), ci = (Real)(SGN * Roots32::s[k]);
+    if constexpr (k == 0) return SGN > 0 ? b : C{-b.x, -b.y};
+    else if constexpr (k == 8) return C{-ci * b.y, ci * b.x};
+    else return C{fma_rn(b.x, cr, -(b.y * ci)), fma_rn(b.x, ci, b.y * cr)};
+}
+
 template <class C> struct RealTw {
     const C *lo, *hi;
     __device__ __forceinline__ C operator()(int k) const {
@@ -687,9 +722,14 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     // the full spectrum Z of one row (Z[k] = U[k] + i V[k], U[-k] = conj
     // U[k]) split into the inputs of the two half-length inverse FFTs:
     // lane 0 Z[k], lane 1 Z[k] exp(2 pi i k/N2)
+    // Real-transform twiddles of this thread's points: w^k, w = exp(2 pi i /
+    // N2), for k = n = t + r T (r < E/2) and k = n - M (r >= E/2) are
+    // w^t exp(i pi r / E) and -conj(w^t exp(i pi r / E)) (w^M = -1, T = M/E):
+    // one table entry per thread, the rest compile-time roots.
+    const C wt = realtw(t);
     auto build = [&](auto own, const UV<R> *stage, CV<V>(&x)[E]) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
+        static_for<0, E>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
             const int n = t + r * T;
             // r < E/2: k = n >= 0 (n < M/2); r >= E/2: k = n - M < 0
             const int kk = (r < E / 2) ? n : M - n;
@@ -702,11 +742,11 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
             }
             C z = (r < E / 2) ? C{e.u.x - e.v.y, e.u.y + e.v.x}     // U + iV
                               : C{e.u.x + e.v.y, e.v.x - e.u.y};    // conj U + i conj V
-            C w = realtw(kk);                                       // exp(2 pi i |k|/N2)
-            C z1 = (r < E / 2) ? C{z.x * w.x - z.y * w.y, z.x * w.y + z.y * w.x}
-                               : C{z.x * w.x + z.y * w.y, z.y * w.x - z.x * w.y};
+            // exp(2 pi i k/N2) for this point's signed k
+            const C w = mul_root<r, E, (r < E / 2 ? 1 : -1)>(wt);
+            C z1 = C{fma_rn(z.x, w.x, -(z.y * w.y)), fma_rn(z.x, w.y, z.y * w.x)};
             x[r] = pack2<R>(z, z1);
-        }
+        });
     };
     CV<V> x[E];
     build(std::true_type{}, stage0, x);
@@ -726,8 +766,11 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     }
     fft(std::integral_constant<int, -1>{}, x);
     __syncthreads();
+    // the post-processing of k in [0, M/2) reads H[M - k]: only H[0] and the
+    // upper half (registers r >= E/2) go to shared memory
 #pragma unroll
-    for (int r = 0; r < E; ++r) sm.st_raw(spad_e<E>(t + r * T), x[r]);
+    for (int r = E / 2; r < E; ++r) sm.st_raw(spad_e<E>(t + r * T), x[r]);
+    if (t == 0) sm.st_raw(0, x[0]);
     __syncthreads();
     // Tensor-store write-out (FP32, compile-time lengths): G of the row pair
     // is staged in the h region (free again: the forward transform has read
@@ -737,22 +780,22 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     // pairs.  Other cases store directly.
     constexpr bool kTma = TMA && std::is_same<R, float>::value && LOG > 0;
     const bool staged = kTma && (__cvta_generic_to_shared(smraw) & 127) == 0;
-#pragma unroll
-    for (int r = 0; r < E / 2; ++r) {
+    static_for<0, E / 2>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
         const int k = t + r * T;
         if (valid && k <= a.K2) {
             CV<V> h = x[r], hc = sm.ld_raw(spad_e<E>((M - k) & (M - 1)));
             const R hf = (R)0.5;
-            CV<V> E{vmul(vadd(h.re, hc.re), vbc(hf)), vmul(vsub(h.im, hc.im), vbc(hf))};
-            CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
-            C w = realtw(k);
-            CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
+            const C w = mul_root<r, E, 1>(wt);  // exp(2 pi i k/N2)
+            CV<V> Ev{vmul(vadd(h.re, hc.re), vbc(hf)), vmul(vsub(h.im, hc.im), vbc(hf))};
+            CV<V> Ov{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
+            CV<V> Y = cadd(Ev, cmul_s(Ov, w.x, -w.y));
             C *dst = staged ? h_first + 4 * (k >> 1) + (k & 1)
                             : gk + gk_index(2 * pair, k, a.n1);  // row 2p+1 two slots further
             dst[0] = lane0<R>(Y);
             dst[2] = lane1<R>(Y);
         }
-    }
+    });
     if constexpr (kTma) {
         if (staged) {
             fence_async_smem();
@@ -767,6 +810,17 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
         }
     }
 }
+
+// Explicitly rounded scalar arithmetic: the update of pass C is compiled in
+// several kernels (plain and general epilogues, single flames and
+// ensembles) that must give identical bits, so no product may be left to
+// the compiler's choice of contraction.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // |kappa| = sqrt((s1 k1)^2 + (s2 k2)^2) for (k1, k2) != 0.  FP32: x times the
 // hardware reciprocal square root (within a few ulp, far inside the FP32
@@ -902,37 +956,40 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             }
             C gh = side == 0 ? lane0<R>(x[r]) : lane1<R>(x[r]);
             C ph = phi[i][side];
-            const R kap = kappa_norm<R>(s1 * (R)k1, s2 * (R)k2);
-            const R om = lin ? kap * (rb - kap * ra) : (R)0;
+            const R kap = kappa_norm<R>(rmul(s1, (R)k1), rmul(s2, (R)k2));
+            const R om = lin ? rmul(kap, rfma(-kap, ra, rb)) : (R)0;
             const R cn = nl ? rcs : (R)0;
             // the non-stiff part: c ghat (+ the forcing f_k)
-            C nt{cn * gh.x, cn * gh.y};
+            C nt{rmul(cn, gh.x), rmul(cn, gh.y)};
             if (fa) {
                 const C f = fa[(side ? ld1 : 0) + k1];
-                nt = C{nt.x + f.x, nt.y + f.y};
+                nt = C{radd(nt.x, f.x), radd(nt.y, f.y)};
             }
+            // dt F = dt (omega Phi + nt)
+            const C df{rmul(rdt, rfma(om, ph.x, nt.x)), rmul(rdt, rfma(om, ph.y, nt.y))};
             C nw;
             if (stage == kStageEuler || stage == kStageHeun1) {
-                nw = C{ph.x + rdt * (om * ph.x + nt.x), ph.y + rdt * (om * ph.y + nt.y)};
+                nw = C{radd(ph.x, df.x), radd(ph.y, df.y)};
                 if (stage == kStageHeun1) va_save[(side ? ld1 : 0) + k1] = ph;
             } else if (stage == kStageHeun2) {
                 const C sv = va_save[(side ? ld1 : 0) + k1];
                 const R h = (R)0.5;
-                nw = C{h * (sv.x + ph.x + rdt * (om * ph.x + nt.x)), h * (sv.y + ph.y + rdt * (om * ph.y + nt.y))};
+                nw = C{rmul(h, radd(radd(sv.x, ph.x), df.x)), rmul(h, radd(radd(sv.y, ph.y), df.y))};
             } else if (stage == kStageIF1) {
                 // exact propagator of the linear part over the step
                 R ef = (R)1;
                 if (lin) {
-                    if constexpr (std::is_same<R, float>::value) ef = expf(kap * (cfs.ib - kap * cfs.ia));
-                    else ef = exp(kap * (cfs.ib - kap * cfs.ia));
+                    const R ex = rmul(kap, rfma(-kap, cfs.ia, cfs.ib));
+                    if constexpr (std::is_same<R, float>::value) ef = expf(ex);
+                    else ef = exp(ex);
                 }
-                const R hdt = (R)0.5 * rdt;
-                nw = C{ef * (ph.x + rdt * nt.x), ef * (ph.y + rdt * nt.y)};
-                va_save[(side ? ld1 : 0) + k1] = C{ef * (ph.x + hdt * nt.x), ef * (ph.y + hdt * nt.y)};
+                const R hdt = rmul((R)0.5, rdt);
+                nw = C{rmul(ef, rfma(rdt, nt.x, ph.x)), rmul(ef, rfma(rdt, nt.y, ph.y))};
+                va_save[(side ? ld1 : 0) + k1] = C{rmul(ef, rfma(hdt, nt.x, ph.x)), rmul(ef, rfma(hdt, nt.y, ph.y))};
             } else {  // kStageIF2
                 const C sv = va_save[(side ? ld1 : 0) + k1];
-                const R hdt = (R)0.5 * rdt;
-                nw = C{sv.x + hdt * nt.x, sv.y + hdt * nt.y};
+                const R hdt = rmul((R)0.5, rdt);
+                nw = C{rfma(hdt, nt.x, sv.x), rfma(hdt, nt.y, sv.y)};
             }
             bad |= !(isfinite(nw.x) && isfinite(nw.y));
             col[k1] = nw;
