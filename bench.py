@@ -500,6 +500,24 @@ def run_suite(args):
                           "note": "two right-hand-side evaluations per step; graph-captured, steps back to back"}),
               flush=True)
         f.close()
+    # the per-step record of the diagnostics (t, Phi_0, <Phi_t>) and with
+    # the surface area (the row pass's area variant), against plain steps
+    f = flame.Flame(4096, 8192, prec="fp32", gamma=0.8, t0=200.0, dt=1e-3)
+    st = torch.from_numpy(flame.box_to_abi(inputs.spectrum_ic(4096, 8192, 256, 0, K1=f.K1, K2=f.K2))).cuda().to(f.cdtype)
+    m = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), 200.0, dtype=torch.float64, device="cuda")
+    nr = 20
+    rec = torch.zeros((nr, 4), dtype=torch.float64, device="cuda")
+    for mode in ("plain", "record", "record+area"):
+        f.set_record(None if mode == "plain" else rec, with_area=mode == "record+area")
+        f.step(st, m, t, nr)  # capture
+        torch.cuda.synchronize()
+        ms = _ev_time(lambda: f.step(st, m, t, nr), s)
+        print(json.dumps({"suite": f"step-4096x8192-fp32-{mode}", "steps": nr, "ms_per_step": ms / nr,
+                          "points_per_s": 4096 * 8192 * nr / (ms * 1e-3)}), flush=True)
+    f.set_record(None)
+    f.sync_status()
+    f.close()
     for (n1, n2, prec) in ((128, 256, "fp64"), (4096, 8192, "fp32")):
         # flame_state_from_field: r2c (rows, columns) into the workspace, then
         # the retained modes.  Bytes: the field read; the N1 x (N2/2+1)

@@ -190,12 +190,18 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
  *   rec[4e + 1] = Phi_0(t_n), the mean mode (mean radius = t_n + Phi_0),
  *   rec[4e + 2] = <Phi_t>(t_n) = c(t_n) mean(|grad Phi_n|^2) + f_0, the
  *                 averaged front velocity dPhi_0/dt of eq. (SivCurv1c),
- *   rec[4e + 3] = NaN (reserved for the surface area).
+ *   rec[4e + 3] = the surface area A(t_n) of flame_area's definition when
+ *                 with_area != 0 (else NaN).
  * The values describe the state entering the step (for two-stage schemes,
- * the first stage's).  The library keeps the pointer; graphs are captured
- * per record binding.  EINVAL for a null handle or capacity < 1 with a
- * non-NULL rec. */
-flame_status flame_set_record(flame_t h, double *rec, int capacity);
+ * the first stage's).  With the area, the first stage's row pass runs a
+ * variant that also synthesises Phi on its rows and sums R sqrt(R^2 +
+ * |grad Phi|^2) there (one more inverse row transform, one CTA per SM),
+ * and the column pass adds the row sums; FP64 rows too long for that
+ * variant's shared memory (N2 = 8192) use the separate area kernels before
+ * the step.  flame_step_batch records no area (NaN).  The library keeps the
+ * pointer; graphs are captured per record binding.  EINVAL for a null handle
+ * or capacity < 1 with a non-NULL rec. */
+flame_status flame_set_record(flame_t h, double *rec, int capacity, int with_area);
 
 /* Sets the forcing term f_k(t) of eq. (SivCurv1c) (Sec. 2; the paper's runs
  * have f = 0) for the handle's later step calls (flame_step, flame_step_heun,

@@ -126,6 +126,7 @@ struct GraphEntry {
     double forcing0;
     double *rec;          // the record in force when captured
     int rec_cap;
+    bool rec_area;
     cudaGraphExec_t exec;
 };
 
@@ -184,6 +185,7 @@ struct flame_ctx {
     // array of 4 rec_cap doubles, or null
     double *rec = nullptr;
     int rec_cap = 0;
+    bool rec_area = false;  // the record includes the surface area
 };
 
 namespace {
@@ -244,8 +246,55 @@ FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
     return d;
 }
 
+bool first_stage(int stage) {
+    return stage == flame::kStageEuler || stage == flame::kStageHeun1 || stage == flame::kStageIF1;
+}
+
+// A recorded step with the surface area: pass B's area variant sums the
+// area of the rows it transforms (rec_area = 1); where that variant does not
+// fit in shared memory (FP64 rows of 8192 points) the separate area kernels
+// compute it first, into handle scratch (rec_area = 2).
+cudaError_t enqueue_step_area(flame_ctx *h, FlameDesc d, cudaStream_t s) {
+    cudaError_t e;
+    d.rec_area = 1;
+    d.arow = h->rowsum;
+    const bool f64 = h->p.prec == FLAME_FP64;
+    if ((e = f64 ? Ops<double>::passA(d, s, h->var_a) : Ops<float>::passA(d, s, h->var_a, h->map())) != cudaSuccess)
+        return e;
+    e = f64 ? Ops<double>::passB_area(d, s) : Ops<float>::passB_area(d, s);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        flame::AdjDesc ad;
+        memset(&ad, 0, sizeof ad);
+        ad.a = h->sa;
+        ad.state = d.state;
+        ad.mean = d.mean;
+        ad.t = d.t_in;
+        ad.uv = h->uv;
+        ad.gk = h->gk;
+        ad.aw = h->aw;
+        ad.rowsum = h->rowsum;
+        ad.area = h->dscal + 6;
+        ad.dmean = h->dscal + 3;
+        ad.tw1 = h->tw1;
+        ad.twm = h->twm;
+        // the area kernels use the step's workspaces: run them, then the
+        // step's passes from the start
+        if ((e = f64 ? Ops<double>::area(ad, s) : Ops<float>::area(ad, s)) != cudaSuccess) return e;
+        d.rec_area = 2;
+        d.aval = h->dscal + 6;
+        if ((e = f64 ? Ops<double>::passA(d, s, h->var_a) : Ops<float>::passA(d, s, h->var_a, h->map())) !=
+            cudaSuccess)
+            return e;
+        e = f64 ? Ops<double>::passB(d, s, h->var_b) : Ops<float>::passB(d, s, h->var_b, h->gmap());
+    }
+    if (e != cudaSuccess) return e;
+    return f64 ? Ops<double>::passC(d, s) : Ops<float>::passC(d, s);
+}
+
 cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
     cudaError_t e;
+    if (d.rec && h->rec_area && first_stage(d.stage)) return enqueue_step_area(h, d, s);
     if (h->p.prec == FLAME_FP64) {
         if ((e = Ops<double>::passA(d, s, h->var_a)) != cudaSuccess) return e;
         if ((e = Ops<double>::passB(d, s, h->var_b)) != cudaSuccess) return e;
@@ -285,8 +334,15 @@ cudaError_t enqueue_scheme(flame_ctx *h, FlameDesc d, int scheme, int n, cudaStr
         e = Ops<float>::passA(d, s, h->var_a, h->map());
         for (int i = 0; i < total && e == cudaSuccess; ++i) {
             d.stage = st[i % ns];
-            e = Ops<float>::passB(d, s, h->var_b, h->gmap());
-            if (e == cudaSuccess) e = i + 1 < total ? Ops<float>::passCA(d, s, h->map()) : Ops<float>::passC(d, s);
+            FlameDesc dc = d;
+            if (d.rec && h->rec_area && first_stage(d.stage)) {
+                dc.rec_area = 1;
+                dc.arow = h->rowsum;
+                e = Ops<float>::passB_area(dc, s);
+            } else {
+                e = Ops<float>::passB(d, s, h->var_b, h->gmap());
+            }
+            if (e == cudaSuccess) e = i + 1 < total ? Ops<float>::passCA(dc, s, h->map()) : Ops<float>::passC(dc, s);
         }
         return e;
     }
@@ -479,7 +535,8 @@ flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int 
                         cudaGraphExec_t *out) {
     for (auto &g : h->graphs)
         if (g.state == state && g.mean == mean && g.t == t && g.n == n && g.scheme == scheme &&
-            g.forcing == h->forcing && g.forcing0 == h->forcing0 && g.rec == h->rec && g.rec_cap == h->rec_cap) {
+            g.forcing == h->forcing && g.forcing0 == h->forcing0 && g.rec == h->rec && g.rec_cap == h->rec_cap &&
+            g.rec_area == h->rec_area) {
             *out = g.exec;
             return FLAME_OK;
         }
@@ -492,7 +549,8 @@ flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int 
     cudaGraphExec_t exec;
     flame_status st = capture_steps(h, make_desc(h, state, mean, t), scheme, n, &exec);
     if (st != FLAME_OK) return st;
-    h->graphs.push_back(GraphEntry{state, mean, t, n, scheme, h->forcing, h->forcing0, h->rec, h->rec_cap, exec});
+    h->graphs.push_back(
+        GraphEntry{state, mean, t, n, scheme, h->forcing, h->forcing0, h->rec, h->rec_cap, h->rec_area, exec});
     *out = exec;
     return FLAME_OK;
 }
@@ -755,11 +813,12 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, in
     return run_scheme(h, state, mean_mode, t, kSchemeEuler, nsteps, static_cast<cudaStream_t>(stream));
 }
 
-flame_status flame_set_record(flame_t h, double *rec, int capacity) {
+flame_status flame_set_record(flame_t h, double *rec, int capacity, int with_area) {
     if (!h) return fail(FLAME_EINVAL, "flame_set_record: null handle");
     if (rec && capacity < 1) return fail(FLAME_EINVAL, "flame_set_record: capacity=%d < 1", capacity);
     h->rec = rec;
     h->rec_cap = rec ? capacity : 0;
+    h->rec_area = rec && with_area;
     return FLAME_OK;
 }
 

@@ -91,6 +91,12 @@ struct FlameDesc {
     // right-hand side), and a NaN area slot; written by the first stage
     double *rec;
     int rec_cap;
+    // area in the record: 0 = none (NaN), 1 = summed by pass C from the
+    // per-row-pair sums arow[N1/2] that the area variant of pass B writes,
+    // 2 = the scalar *aval computed by the separate area kernels
+    int rec_area;
+    double *arow;
+    const double *aval;
     // L2 persisting window over the state for the launches of passes A and
     // C (a launch attribute, not read by the kernels); bytes = 0: none
     L2Window l2_state;
@@ -148,6 +154,10 @@ template <class R> struct Ops {
     static cudaError_t passB(const FlameDesc &d, cudaStream_t s, int variant = 0,
                              const CUtensorMap *gk_map = nullptr);
     static cudaError_t passC(const FlameDesc &d, cudaStream_t s);
+    // Pass B that also sums the surface area of its rows (area variant,
+    // arow[pair]); cudaErrorNotSupported when its shared memory exceeds the
+    // device's limit.
+    static cudaError_t passB_area(const FlameDesc &d, cudaStream_t s);
     // Pass C of one step fused with pass A of the next (FP32, 256 <= N1 <=
     // 4096, uv written through uv_map); cudaErrorNotSupported otherwise.
     static cudaError_t passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap *uv_map);

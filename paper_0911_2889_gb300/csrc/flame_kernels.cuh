@@ -646,7 +646,26 @@ template <class R> __device__ __forceinline__ CoefR<R> load_coef(const double *c
 // u + iv; then g = u^2 + v^2 and h[m] = g[2m] + i g[2m+1] is transformed
 // forward with the real-input post-processing; G[k], k <= K2, is written
 // (column-major gk).  G[j1][0] is the row sum of g used for the FP64 mean mode.
-template <class R, int LOG, int E, bool TMA = false, bool GMAP = false>
+// Sum over the T threads of one line group (T a power of two; groups are
+// aligned to T threads).  Groups of up to 32 threads reduce by shuffles;
+// larger ones add one CTA barrier and `scratch` (one slot per warp of the
+// CTA).  Every thread of the CTA calls it; the group's sum is returned to
+// all its threads.
+template <class F> __device__ __forceinline__ F group_sum(F v, int T, F *scratch) {
+    const int w = min(T, 32);
+    for (int o = w >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (T <= 32) return v;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();  // the scratch's previous use has been read
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    const int first = (threadIdx.x / T) * (T >> 5);
+    F s = 0;
+    for (int i = 0; i < (T >> 5); ++i) s += scratch[first + i];
+    return s;
+}
+
+template <class R, int LOG, int E, bool TMA = false, bool GMAP = false, bool AREA = false>
 __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
@@ -665,14 +684,17 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     const int pair = tile * G + g;
     const bool valid = pair < (a.n1 >> 1);
     // per group: the exchange buffer, then M entries of C (sizeof(C) ==
-    // sizeof(V) in both precisions)
-    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * (2 * plane_len_e<E>(M) + M);
+    // sizeof(V) in both precisions); the area variant adds the synthesis of
+    // Phi on the two rows (M two-line points) and its own staging of row 2p
+    // (M/2 (U, V) entries)
+    const int gstride = 2 * plane_len_e<E>(M) + M + (AREA ? 3 * M : 0);
+    V *base = reinterpret_cast<V *>(smraw) + (size_t)g * gstride;
     auto sm = make_planes_e<E>(base, M);  // (E = 8 pads one slot every 8: st_raw/ld_raw)
     const C *P = twm + tw_real_offset(a.logm);  // exp(+2 pi i k/N2), k < M
     if (tile == 0 && threadIdx.x == 0) store_coef<R>(d.coef, a, *d.t_in, d.stage == kStageIF1);
     constexpr bool STW = kSharedTw<R, LOG, E>;
     constexpr int LS = STW ? LOG : 8;
-    C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * (2 * plane_len_e<E>(M) + M));
+    C *stw = reinterpret_cast<C *>(reinterpret_cast<V *>(smraw) + (size_t)G * gstride);
     RealTw<C> Pt{stw + 480, stw + 544};
     if constexpr (STW) {
         TwShared<C>::template fill<LS>(stw, twm);
@@ -700,7 +722,10 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
     // (M entries per group) while row 2p+1 is transformed; row 2p+1's stays
     // in registers.
     C *h_first = reinterpret_cast<C *>(base + 2 * plane_len_e<E>(M));
-    UV<R> *stage0 = reinterpret_cast<UV<R> *>(base), *stage1 = reinterpret_cast<UV<R> *>(h_first);
+    CV<V> *phi_park = reinterpret_cast<CV<V> *>(base + 2 * plane_len_e<E>(M) + M);  // area variant
+    UV<R> *stage0 = AREA ? reinterpret_cast<UV<R> *>(base + 2 * plane_len_e<E>(M) + 3 * M)
+                         : reinterpret_cast<UV<R> *>(base),
+          *stage1 = reinterpret_cast<UV<R> *>(h_first);
     const int half = M >> 1;
     UV<R> e0[E / 2];
     {
@@ -749,16 +774,89 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
         });
     };
     CV<V> x[E];
+    // Area variant: Phi on rows 2p, 2p+1 (without the mean mode), as the
+    // inverse row transform of S[k] = P_2p[k] + i P_2p+1[k], P the column
+    // synthesis of Phi: for k2 >= 1, P = V / (i s2 k2) (pass A wrote V =
+    // i s2 k2 P); for k2 = 0, P(j1) = 2 Re sum_{k1 = 1..K1} Phi_{k1,0}
+    // exp(2 pi i k1 j1 / N1), summed here.  Parked for the area terms.
+    __shared__ R ared[32];
+    R apart = 0;  // this thread's share of the rows' area sums
+    R rr = 0;     // r0 + Phi_0
+    if constexpr (AREA) {
+        rr = (R)(*d.t_in + *d.mean);
+        const C *st0 = static_cast<const C *>(d.state) + a.K1;  // column k2 = 0, index k1
+        const C *t1r = static_cast<const C *>(d.tw1) + tw_real_offset(a.logn1);  // exp(2 pi i k / 2 N1), k < N1
+        R p0[2] = {0, 0};
+        for (int k1 = 1 + t; k1 <= a.K1; k1 += T) {
+            const C ph = st0[k1];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int m = (int)(((long)k1 * (2 * pair + q)) % a.n1);
+                C w = __ldg(t1r + ((2 * m < a.n1) ? 2 * m : 2 * m - a.n1));
+                if (2 * m >= a.n1) w = C{-w.x, -w.y};
+                p0[q] += 2 * (ph.x * w.x - ph.y * w.y);
+            }
+        }
+        p0[0] = group_sum<R>(p0[0], T, ared);
+        p0[1] = group_sum<R>(p0[1], T, ared);
+        const R is2 = (R)1 / scale2<R>(a);
+        static_for<0, E>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            const int n = t + r * T;
+            const int kk = (r < E / 2) ? n : M - n;
+            C P0{0, 0}, P1{0, 0};
+            if (kk == 0) {
+                P0 = C{p0[0], 0};
+                P1 = C{p0[1], 0};
+            } else if (kk < half) {
+                const C v0 = ld_uv_s<R>(stage0 + kk).v, v1 = ld_uv_s<R>(stage1 + kk).v;
+                const R f = is2 / (R)kk;  // P = V / (i s2 k) = (V.y, -V.x) / (s2 k)
+                P0 = C{v0.y * f, -v0.x * f};
+                P1 = C{v1.y * f, -v1.x * f};
+            }
+            // S[k] (r < E/2, k = kk) or S[-kk] = conj P0 + i conj P1
+            const C S = (r < E / 2) ? C{P0.x - P1.y, P0.y + P1.x} : C{P0.x + P1.y, P1.x - P0.y};
+            const C w = mul_root<r, E, (r < E / 2 ? 1 : -1)>(wt);
+            x[r] = pack2<R>(S, C{fma_rn(S.x, w.x, -(S.y * w.y)), fma_rn(S.x, w.y, S.y * w.x)});
+        });
+        fft(std::integral_constant<int, 1>{}, x);
+#pragma unroll
+        for (int r = 0; r < E; ++r) phi_park[t + r * T] = x[r];
+    }
+    // area terms R sqrt(R^2 + g), R = r0 + Phi_0 + phi, at the points 2m + q of
+    // one row (q = 0, 1 the lanes), phi from the parked synthesis (re: row 2p,
+    // im: row 2p+1)
+    auto area_terms = [&](const V(&gv)[E], bool second) {
+        if constexpr (AREA) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const CV<V> ph = phi_park[t + r * T];
+                const V pv = second ? ph.im : ph.re;
+                const R R0 = rr + pv.x, R1 = rr + pv.y;
+                apart += R0 * sqrt(fma_rn(R0, R0, gv[r].x)) + R1 * sqrt(fma_rn(R1, R1, gv[r].y));
+            }
+        }
+    };
     build(std::true_type{}, stage0, x);
     fft(std::integral_constant<int, 1>{}, x);
     V sq0[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) sq0[r] = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));  // g at 2m, 2m+1
+    area_terms(sq0, false);
     build(std::false_type{}, stage1, x);
     __syncthreads();  // stage1 fully read: the h region takes row 2p's g
 #pragma unroll
     for (int r = 0; r < E; ++r) h_first[t + r * T] = C{sq0[r].x, sq0[r].y};
     fft(std::integral_constant<int, 1>{}, x);
+    if constexpr (AREA) {
+        V sq1[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) sq1[r] = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
+        area_terms(sq1, true);
+        // the row pair's area sum (FP64 across the group's threads)
+        const double tot = group_sum<double>((double)apart, T, reinterpret_cast<double *>(phi_park));
+        if (t == 0 && valid) d.arow[pair] = tot;
+    }
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         V sq = vfma(x[r].re, x[r].re, vmul(x[r].im, x[r].im));
@@ -998,6 +1096,28 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         }
     }
     if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
+    // the surface area of the state entering the step, for the record: the
+    // area variant of pass B left one FP64 sum per row pair (summed here by
+    // block 0's threads), or the separate area kernels left the total
+    double area = __longlong_as_double(0x7ff8000000000000LL);
+    if (GEN && tile == 0 && d.rec && stage != kStageHeun2 && stage != kStageIF2) {
+        if (d.rec_area == 1) {
+            __shared__ double asum[32];
+            double v = 0.0;
+            for (int i = threadIdx.x; i < (a.n1 >> 1); i += blockDim.x) v += d.arow[i];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) asum[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += asum[w];
+                const double two_pi = 6.283185307179586476925286766559;
+                area = tot * (two_pi * two_pi / ((double)N1 * (double)a.n2 * a.s1 * a.s2));
+            }
+        } else if (d.rec_area == 2) {
+            area = *d.aval;
+        }
+    }
     if (tile == 0 && threadIdx.x == 0) {
         double rs = 0.0;
         for (int w = 0; w < (int)blockDim.x; w += span) rs += red[w];
@@ -1012,7 +1132,7 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             e[0] = d.coef[0];
             e[1] = m;
             e[2] = (nl ? d.coef[1] * mg : 0.0) + (GEN ? d.forcing0 : 0.0);
-            e[3] = __longlong_as_double(0x7ff8000000000000LL);  // no area in this record
+            e[3] = area;
         }
         if (stage == kStageEuler || stage == kStageHeun1 || stage == kStageIF1) {
             if (stage == kStageHeun1) *d.save_mean = m;
@@ -1143,6 +1263,12 @@ template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBt(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
     passB_body<R, LOG, 16, true>(d, blockIdx.x, gridDim.x, pf, &tm);
+}
+// pass B that also sums the rows' surface area (the per-step record); its
+// shared memory (three more row-length buffers) allows one CTA per SM
+template <class R, int LOG, int E>
+__global__ void __launch_bounds__(E == 16 ? 256 : 128, 1) k_passB_area(FlameDesc d) {
+    passB_body<R, LOG, E, false, false, true>(d, blockIdx.x, gridDim.x, 0);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passB8(FlameDesc d, int pf) {

@@ -314,6 +314,41 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
+template <class R> cudaError_t Ops<R>::passB_area(const FlameDesc &d, cudaStream_t s) {
+    using Vt = typename VecOf<R>::type;
+    const int M = 1 << d.a.logm;
+    cudaError_t err = cudaErrorNotSupported;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaErrorNotSupported;
+    }
+    const size_t area_extra = 3 * (size_t)M * sizeof(Vt);
+    if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logm)) {
+        Geom g = geom_small_fp64<R>(d.a.logm, d.a.n1 / 2, (size_t)M * sizeof(typename VecOf<R>::c) + area_extra);
+        if (g.smem + 4096 > (size_t)optin) return cudaErrorNotSupported;
+        static_for<4, 8>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (d.a.logm == L) err = launch_cl(k_passB_area<R, L, 8>, dim3(g.blocks), g.threads, g.smem, s, 1, d);
+        });
+        return err;
+    }
+    Geom g = make_geom<R>(d.a.logm, d.a.n1 / 2, 0, (size_t)M * sizeof(typename VecOf<R>::c) + area_extra);
+    with_log<R>(d.a.logm, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        Geom ga = g;
+        if (kSharedTw<R, L, 16>) ga.smem += kTwSmemBytes;
+        if (ga.smem + 4096 > (size_t)optin) {
+            err = cudaErrorNotSupported;
+            return;
+        }
+        err = launch_cl(k_passB_area<R, L, 16>, dim3(ga.blocks), ga.threads, ga.smem, s, 1, d);
+    });
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logn1)) {
         const Geom g = geom_small_fp64<R>(d.a.logn1, (d.a.K2 + 2) / 2, 0);

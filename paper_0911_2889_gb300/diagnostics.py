@@ -61,19 +61,20 @@ def record(flame, state, mean_mode, t, nsteps, every, area=False, stream=None):
     return out
 
 
-def record_steps(flame, state, mean_mode, t, nsteps, scheme="euler", stream=None):
+def record_steps(flame, state, mean_mode, t, nsteps, scheme="euler", area=False, stream=None):
     """Runs nsteps steps in one call (flame_step, flame_step_heun or
     flame_step_if) with the per-step device record on (flame_set_record):
-    the step kernels write t_n, Phi_0(t_n) and <Phi_t>(t_n) for every step,
-    so the run needs no host read-back until it ends.  Returns a dict of
-    host float64 arrays over the nsteps states entering the steps: t, mean,
-    radius (= t + Phi_0), velocity (<Phi_t>)."""
+    the step kernels write t_n, Phi_0(t_n), <Phi_t>(t_n) and, with area=True,
+    the surface area for every step, so the run needs no host read-back
+    until it ends.  Returns a dict of host float64 arrays over the nsteps
+    states entering the steps: t, mean, radius (= t + Phi_0), velocity
+    (<Phi_t>) and area (NaN without area=True)."""
     import torch
 
     if nsteps < 1:
         raise ValueError("nsteps must be >= 1")
     rec = torch.full((nsteps, 4), float("nan"), dtype=torch.float64, device=state.device)
-    flame.set_record(rec)
+    flame.set_record(rec, with_area=area)
     try:
         step = {"euler": flame.step, "heun": flame.step_heun, "if": flame.step_if}[scheme]
         step(state, mean_mode, t, nsteps, stream)
@@ -83,7 +84,7 @@ def record_steps(flame, state, mean_mode, t, nsteps, scheme="euler", stream=None
     # entry n mod nsteps belongs to lattice step n: put them in time order
     order = np.argsort(r[:, 0])
     r = r[order]
-    return {"t": r[:, 0], "mean": r[:, 1], "radius": r[:, 0] + r[:, 1], "velocity": r[:, 2]}
+    return {"t": r[:, 0], "mean": r[:, 1], "radius": r[:, 0] + r[:, 1], "velocity": r[:, 2], "area": r[:, 3]}
 
 
 def _loglinear(t, v, t_star):

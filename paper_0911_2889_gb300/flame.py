@@ -62,7 +62,7 @@ SIGNATURES = {
     "flame_step_heun": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_step_if": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_set_forcing": (_i, [_vp, _vp, ctypes.c_double]),
-    "flame_set_record": (_i, [_vp, _vp, _i]),
+    "flame_set_record": (_i, [_vp, _vp, _i, _i]),
     "flame_step_pass": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
     "flame_area": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -195,12 +195,12 @@ def flame_set_forcing(h, forcing=None, forcing0=0.0):
     _check(load().flame_set_forcing(ctypes.c_void_p(h), _optr(forcing, name="forcing"), float(forcing0)))
 
 
-def flame_set_record(h, rec=None):
+def flame_set_record(h, rec=None, with_area=False):
     """rec: None or a float64 CUDA tensor of shape (capacity, 4)."""
     if rec is not None and (rec.dim() != 2 or rec.shape[1] != 4):
         raise ValueError("flame_set_record: rec must have shape (capacity, 4)")
     cap = 0 if rec is None else int(rec.shape[0])
-    _check(load().flame_set_record(ctypes.c_void_p(h), _optr(rec, torch.float64, "rec"), cap))
+    _check(load().flame_set_record(ctypes.c_void_p(h), _optr(rec, torch.float64, "rec"), cap, int(bool(with_area))))
 
 
 def flame_step_pass(h, pass_, state, mean_mode, t, stream=None):
@@ -345,11 +345,12 @@ class Flame:
         self._check_state(state)
         flame_step_if(self.h, state, mean_mode, t, nsteps, stream)
 
-    def set_record(self, rec=None):
+    def set_record(self, rec=None, with_area=False):
         """Per-step diagnostics record on the device (flame_set_record):
         rec is None or a float64 CUDA tensor (capacity, 4) of rows (t_n,
-        Phi_0(t_n), <Phi_t>(t_n), area or NaN).  The handle keeps a reference."""
-        flame_set_record(self.h, rec)
+        Phi_0(t_n), <Phi_t>(t_n), area A(t_n) or NaN).  The handle keeps a
+        reference."""
+        flame_set_record(self.h, rec, with_area)
         self._rec = rec
 
     def set_forcing(self, forcing=None, forcing0=0.0):

@@ -102,7 +102,7 @@ def test_new_entry_points_reject_bad_arguments(lib):
     # null handles and bad arguments are refused before any device work
     assert lib.flame_step_if(None, None, None, None, 1, None) == 1
     assert lib.flame_set_forcing(None, None, 0.0) == 1
-    assert lib.flame_set_record(None, None, 0) == 1
+    assert lib.flame_set_record(None, None, 0, 0) == 1
     out = ctypes.c_double(0.0)
     assert lib.flame_fma_peak(7, ctypes.byref(out)) == 1
     assert lib.flame_fma_peak(0, None) == 1

@@ -137,3 +137,39 @@ def test_device_record_wraps_around(fl):
         assert r[n % 5, 0] == pytest.approx(20.0 + n * 1e-2, rel=1e-15)
     assert np.all(np.isnan(r[:, 3]))
     f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,shape,scheme,rtol", [
+    ("fp64", (128, 256), "euler", 1e-12),    # short FP64 rows (8 points per thread)
+    ("fp64", (64, 1024), "if", 1e-12),       # FP64 runtime-length rows
+    ("fp64", (16, 8192), "euler", 1e-12),    # FP64 rows too long for the fused variant
+    ("fp32", (1024, 2048), "heun", 1e-6),
+    ("fp32", (4096, 8192), "euler", 1e-6),   # the fused column passes
+])
+def test_device_record_area_matches_oracle(fl, monkeypatch, prec, shape, scheme, rtol):
+    # the surface area of every state entering a step, summed by the row
+    # pass's area variant (or the separate area kernels), against the
+    # oracle's area of its own trajectory
+    import torch
+    monkeypatch.delenv("FLAME_FUSE", raising=False)
+    n1, n2 = shape
+    nsteps = 4
+    f = fl.Flame(n1, n2, prec=prec, gamma=0.8, t0=20.0, dt=1e-2)
+    st0 = inputs.spectrum_ic(n1, n2, min(32, f.K1), 53, amp=2e-2, K1=f.K1, K2=f.K2)
+    state = torch.from_numpy(fl.box_to_abi(st0)).cuda().to(f.cdtype)
+    st0 = fl.abi_to_box(state.cpu().numpy()).astype(np.complex128)
+    mean = torch.full((1,), 0.05, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), 20.0, dtype=torch.float64, device="cuda")
+    out = diagnostics.record_steps(f, state, mean, t, nsteps, scheme=scheme, area=True)
+    p = orc.Params(n1, n2, K1=f.K1, K2=f.K2, gamma=0.8, t0=20.0, dt=1e-2)
+    stepper = {"euler": orc.step, "heun": orc.step_heun, "if": orc.step_if}[scheme]
+    s, m, tt = st0, 0.05, 20.0
+    for n in range(nsteps):
+        A = orc.area(p, s, m, tt)
+        assert out["area"][n] == pytest.approx(A, rel=rtol), (n, out["area"][n], A)
+        s, m, tt = stepper(p, s, m, tt, 1)
+    # a record without the area leaves NaN there
+    out2 = diagnostics.record_steps(f, state, mean, t, 2, scheme=scheme, area=False)
+    assert np.all(np.isnan(out2["area"]))
+    f.close()
