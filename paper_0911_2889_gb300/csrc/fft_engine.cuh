@@ -205,9 +205,14 @@ __host__ __device__ constexpr int tw_real_offset(int logN, int LE = 4) {
     return tw_final_offset(logN, LE) + ((1 << (logN % LE)) - 1) * ((1 << logN) >> (logN % LE));
 }
 __host__ __device__ constexpr int tw_table_len(int logN, int LE = 4) { return tw_real_offset(logN, LE) + (1 << logN); }
-// A line's twiddle allocation: the radix-16 table followed by the radix-8
-// table (used by the 8-point-per-thread kernels).
-__host__ __device__ constexpr int tw_alloc_len(int logN) { return tw_table_len(logN, 4) + tw_table_len(logN, 3); }
+// A line's twiddle allocation: the radix-16 table, then the radix-8 table
+// (8-point-per-thread kernels), then the radix-4 table (4 points per thread,
+// the FP64 short-line kernels).
+__host__ __device__ constexpr int tw_alloc_len(int logN) {
+    return tw_table_len(logN, 4) + tw_table_len(logN, 3) + tw_table_len(logN, 2);
+}
+// log2 of the points per thread E (16, 8 or 4)
+template <int E> __host__ __device__ constexpr int log2_e() { return E == 16 ? 4 : E == 8 ? 3 : 2; }
 
 // ----------------------------------------------------------------------------
 // Shared-memory exchange
@@ -215,8 +220,8 @@ __host__ __device__ constexpr int tw_alloc_len(int logN) { return tw_table_len(l
 __host__ __device__ constexpr int spad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int plane_len(int N) { return N + (N >> 4); }
 // radix-E exchanges pad one slot every E (E = 8 or 16)
-template <int E> __host__ __device__ constexpr int spad_e(int i) { return i + (i >> (E == 16 ? 4 : 3)); }
-template <int E> __host__ __device__ constexpr int plane_len_e(int N) { return N + (N >> (E == 16 ? 4 : 3)); }
+template <int E> __host__ __device__ constexpr int spad_e(int i) { return i + (i >> log2_e<E>()); }
+template <int E> __host__ __device__ constexpr int plane_len_e(int N) { return N + (N >> log2_e<E>()); }
 
 // Barrier over the threads that share the exchange buffers.
 struct CtaBarrier {
@@ -397,7 +402,7 @@ template <int DIR, int LOGN, int E, class V, class C, class Bar, class TW = TwGl
 __device__ __forceinline__ void line_fft_ct(CV<V> (&x)[E], int t, const Planes<V> &sm,
                                             const C *__restrict__ tw, Bar bar, TW twp = TW{nullptr}) {
     using Real = decltype(C::x);
-    constexpr int LE = E == 16 ? 4 : 3;
+    constexpr int LE = log2_e<E>();
     constexpr int N = 1 << LOGN, T = N / E, P = LOGN / LE, LR = LOGN % LE;
     static_for<0, P>([&](auto sc) {
         constexpr int s = decltype(sc)::value;

@@ -357,6 +357,8 @@ template <> struct Shape<0> {
 template <int DIR, int LOG, int E, class V, class C>
 __device__ __forceinline__ void fft_line_e(CV<V> (&x)[E], int logn, int t, const Planes<V> &sm, const C *tw) {
     if constexpr (E == 8) line_fft_ct<DIR, LOG, 8>(x, t, sm, tw + tw_table_len(LOG, 4), CtaBarrier{});
+    else if constexpr (E == 4)
+        line_fft_ct<DIR, LOG, 4>(x, t, sm, tw + tw_table_len(LOG, 4) + tw_table_len(LOG, 3), CtaBarrier{});
     else fft_line<DIR, LOG>(x, logn, t, sm, tw);
 }
 
@@ -946,7 +948,8 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
                                            const CUtensorMap *tm = nullptr) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
-    static_assert(E == 16 || (E == 8 && !FUSE_A), "E points per thread: 16, or 8 without the fused pass A");
+    static_assert(E == 16 || ((E == 8 || E == 4) && !FUSE_A),
+                  "E points per thread: 16, or 8 and 4 without the fused pass A");
     constexpr int QE = E / 4;  // band registers: r < QE (k1 >= 0) and r >= E - QE (k1 < 0)
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[256];  // one per thread (blockDim <= 256)
@@ -1226,29 +1229,29 @@ template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAt(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
     passA_body<R, LOG, 16, false, true>(d, blockIdx.x, gridDim.x, pf, &tm);
 }
-// FP64, 8 points per thread at short compile-time lengths (2^4 .. 2^7): one
-// line pair per CTA of 2^LOG / 8 threads, twice the threads of the runtime
-// kernels for the latency-bound small FP64 grids
-template <class R, int LOG> __global__ void __launch_bounds__(128, 1) k_passA8d(FlameDesc d, int pf) {
-    passA_body<R, LOG, 8, false>(d, blockIdx.x, gridDim.x, pf);
+// FP64 at short compile-time lengths (2^4 .. 2^7), E = 8 or 4 points per
+// thread: one line pair per CTA of 2^LOG / E threads (up to a warp at 128
+// points with E = 4), for the latency-bound small FP64 grids
+template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passAsd(FlameDesc d, int pf) {
+    passA_body<R, LOG, E, false>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R, int LOG> __global__ void __launch_bounds__(128, 1) k_passB8d(FlameDesc d, int pf) {
-    passB_body<R, LOG, 8>(d, blockIdx.x, gridDim.x, pf);
+template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passBsd(FlameDesc d, int pf) {
+    passB_body<R, LOG, E>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R, int LOG> __global__ void __launch_bounds__(128, 1) k_passC8d(FlameDesc d, int pf) {
-    passC_body<R, LOG, false, 8>(d, blockIdx.x, gridDim.x, pf);
+template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passCsd(FlameDesc d, int pf) {
+    passC_body<R, LOG, false, E>(d, blockIdx.x, gridDim.x, pf);
 }
-template <class R, int LOG>
-__global__ void __launch_bounds__(128, 1) k_passC8d_n(const FlameDesc *__restrict__ ds, int pf) {
-    passC_body<R, LOG, false, 8>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+template <class R, int LOG, int E>
+__global__ void __launch_bounds__(128, 1) k_passCsd_n(const FlameDesc *__restrict__ ds, int pf) {
+    passC_body<R, LOG, false, E>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
-template <class R, int LOG>
-__global__ void __launch_bounds__(128, 1) k_passA8d_n(const FlameDesc *__restrict__ ds, int pf) {
-    passA_body<R, LOG, 8, false>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+template <class R, int LOG, int E>
+__global__ void __launch_bounds__(128, 1) k_passAsd_n(const FlameDesc *__restrict__ ds, int pf) {
+    passA_body<R, LOG, E, false>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
-template <class R, int LOG>
-__global__ void __launch_bounds__(128, 1) k_passB8d_n(const FlameDesc *__restrict__ ds, int pf) {
-    passB_body<R, LOG, 8>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+template <class R, int LOG, int E>
+__global__ void __launch_bounds__(128, 1) k_passBsd_n(const FlameDesc *__restrict__ ds, int pf) {
+    passB_body<R, LOG, E>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(FlameDesc d, int pf) {

@@ -165,10 +165,12 @@ template <class R> Geom Ops<R>::geom_cols(int logn, int nlines, int hint) { retu
 template <class R> Geom Ops<R>::geom_rows(int logm, int nlines, int hint) { return make_geom<R>(logm, nlines, hint); }
 
 template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStream_t s) {
-    // radix-16 table, then the radix-8 table (tw_alloc_len entries in all)
-    const int len16 = tw_table_len(logN, 4), len8 = tw_table_len(logN, 3);
+    // radix-16 table, then the radix-8 and radix-4 tables (tw_alloc_len entries in all)
+    const int len16 = tw_table_len(logN, 4), len8 = tw_table_len(logN, 3), len4 = tw_table_len(logN, 2);
     cudaError_t e = launch_cl(k_twiddles<R>, dim3((len16 + 255) / 256), 256, 0, s, 1, tab, logN, 4);
     if (e == cudaSuccess) e = launch_cl(k_twiddles<R>, dim3((len8 + 255) / 256), 256, 0, s, 1, tab + len16, logN, 3);
+    if (e == cudaSuccess)
+        e = launch_cl(k_twiddles<R>, dim3((len4 + 255) / 256), 256, 0, s, 1, tab + len16 + len8, logN, 2);
     return e;
 }
 
@@ -217,22 +219,40 @@ template <class R, int L> static Geom geom_passA8(int ncols) {
 // CTA (the runtime kernels give such lines 2^LOG/16 threads, a quarter warp
 // at 128 points, and are bound by the latency of their FP64 chains)
 template <class R> static bool small_fp64(int logn) { return sizeof(R) == 8 && logn >= 4 && logn <= 7; }
-template <class R> static Geom geom_small_fp64(int logn, int nlines, size_t extra) {
+// Points per thread of the FP64 short-line kernels: 4 (a warp per 128-point
+// line pair), or 8 with FLAME_FP64_POINTS=8 (read at every launch, so tests
+// can run both).  Measured on the 128 x 256 FP64 trajectory: 46.1 us per
+// step with 4, 78.4 us with 8: the lines' FP64 chains are latency-bound,
+// and a full warp per line pair halves each thread's chain.
+static int fp64_points() {
+    const char *v = getenv("FLAME_FP64_POINTS");
+    return (v && strcmp(v, "8") == 0) ? 8 : 4;
+}
+template <class R, int E> static Geom geom_small_fp64(int logn, int nlines, size_t extra) {
     Geom g;
-    g.threads = (1 << logn) / 8;
+    g.threads = (1 << logn) / E;
     g.blocks = nlines;
-    g.smem = 2 * (size_t)plane_len_e<8>(1 << logn) * sizeof(typename VecOf<R>::type) + extra;
+    g.smem = 2 * (size_t)plane_len_e<E>(1 << logn) * sizeof(typename VecOf<R>::type) + extra;
     return g;
+}
+// calls f(integral_constant<E>) with the chosen points per thread
+template <class F> static void with_fp64_points(F &&f) {
+    if (fp64_points() == 4) f(std::integral_constant<int, 4>{});
+    else f(std::integral_constant<int, 8>{});
 }
 
 template <class R>
 cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *uv_map) {
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logn1)) {
-        const Geom g = geom_small_fp64<R>(d.a.logn1, d.a.K2 + 1, 0);
         cudaError_t err = cudaErrorInvalidValue;
-        static_for<4, 8>([&](auto lc) {
-            constexpr int L = decltype(lc)::value;
-            if (d.a.logn1 == L) err = launch_w(d.l2_state, k_passA8d<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+        with_fp64_points([&](auto ec) {
+            constexpr int E = decltype(ec)::value;
+            const Geom g = geom_small_fp64<R, E>(d.a.logn1, d.a.K2 + 1, 0);
+            static_for<4, 8>([&](auto lc) {
+                constexpr int L = decltype(lc)::value;
+                if (d.a.logn1 == L)
+                    err = launch_w(d.l2_state, k_passAsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+            });
         });
         return err;
     }
@@ -283,11 +303,14 @@ template <class R> static Geom geom_passB8(int logm, int nlines) {
 template <class R>
 cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const CUtensorMap *gk_map) {
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logm)) {  // + M entries of the parked |z|^2 per row pair
-        const Geom g = geom_small_fp64<R>(d.a.logm, d.a.n1 / 2, (size_t)(1 << d.a.logm) * sizeof(typename VecOf<R>::c));
         cudaError_t err = cudaErrorInvalidValue;
-        static_for<4, 8>([&](auto lc) {
-            constexpr int L = decltype(lc)::value;
-            if (d.a.logm == L) err = launch_cl(k_passB8d<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+        with_fp64_points([&](auto ec) {
+            constexpr int E = decltype(ec)::value;
+            const Geom g = geom_small_fp64<R, E>(d.a.logm, d.a.n1 / 2, (size_t)(1 << d.a.logm) * sizeof(typename VecOf<R>::c));
+            static_for<4, 8>([&](auto lc) {
+                constexpr int L = decltype(lc)::value;
+                if (d.a.logm == L) err = launch_cl(k_passBsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+            });
         });
         return err;
     }
@@ -326,11 +349,14 @@ template <class R> cudaError_t Ops<R>::passB_area(const FlameDesc &d, cudaStream
     }
     const size_t area_extra = 3 * (size_t)M * sizeof(Vt);
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logm)) {
-        Geom g = geom_small_fp64<R>(d.a.logm, d.a.n1 / 2, (size_t)M * sizeof(typename VecOf<R>::c) + area_extra);
-        if (g.smem + 4096 > (size_t)optin) return cudaErrorNotSupported;
-        static_for<4, 8>([&](auto lc) {
-            constexpr int L = decltype(lc)::value;
-            if (d.a.logm == L) err = launch_cl(k_passB_area<R, L, 8>, dim3(g.blocks), g.threads, g.smem, s, 1, d);
+        with_fp64_points([&](auto ec) {
+            constexpr int E = decltype(ec)::value;
+            Geom g = geom_small_fp64<R, E>(d.a.logm, d.a.n1 / 2, (size_t)M * sizeof(typename VecOf<R>::c) + area_extra);
+            if (g.smem + 4096 > (size_t)optin) return;
+            static_for<4, 8>([&](auto lc) {
+                constexpr int L = decltype(lc)::value;
+                if (d.a.logm == L) err = launch_cl(k_passB_area<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d);
+            });
         });
         return err;
     }
@@ -351,11 +377,15 @@ template <class R> cudaError_t Ops<R>::passB_area(const FlameDesc &d, cudaStream
 
 template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s) {
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(d.a.logn1)) {
-        const Geom g = geom_small_fp64<R>(d.a.logn1, (d.a.K2 + 2) / 2, 0);
         cudaError_t err = cudaErrorInvalidValue;
-        static_for<4, 8>([&](auto lc) {
-            constexpr int L = decltype(lc)::value;
-            if (d.a.logn1 == L) err = launch_w(d.l2_state, k_passC8d<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+        with_fp64_points([&](auto ec) {
+            constexpr int E = decltype(ec)::value;
+            const Geom g = geom_small_fp64<R, E>(d.a.logn1, (d.a.K2 + 2) / 2, 0);
+            static_for<4, 8>([&](auto lc) {
+                constexpr int L = decltype(lc)::value;
+                if (d.a.logn1 == L)
+                    err = launch_w(d.l2_state, k_passCsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+            });
         });
         return err;
     }
@@ -401,11 +431,14 @@ template <class R>
 cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
                                 const CUtensorMap *maps) {
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(a.logn1)) {  // the kernels of passA, so that a flame's ensemble step equals its own
-        const Geom g = geom_small_fp64<R>(a.logn1, a.K2 + 1, 0);
         cudaError_t err = cudaErrorInvalidValue;
-        static_for<4, 8>([&](auto lc) {
-            constexpr int L = decltype(lc)::value;
-            if (a.logn1 == L) err = launch_cl(k_passA8d_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        with_fp64_points([&](auto ec) {
+            constexpr int E = decltype(ec)::value;
+            const Geom g = geom_small_fp64<R, E>(a.logn1, a.K2 + 1, 0);
+            static_for<4, 8>([&](auto lc) {
+                constexpr int L = decltype(lc)::value;
+                if (a.logn1 == L) err = launch_cl(k_passAsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+            });
         });
         return err;
     }
@@ -434,11 +467,14 @@ template <class R>
 cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, int variant,
                                 const CUtensorMap *maps) {
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(a.logm)) {
-        const Geom g = geom_small_fp64<R>(a.logm, a.n1 / 2, (size_t)(1 << a.logm) * sizeof(typename VecOf<R>::c));
         cudaError_t err = cudaErrorInvalidValue;
-        static_for<4, 8>([&](auto lc) {
-            constexpr int L = decltype(lc)::value;
-            if (a.logm == L) err = launch_cl(k_passB8d_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        with_fp64_points([&](auto ec) {
+            constexpr int E = decltype(ec)::value;
+            const Geom g = geom_small_fp64<R, E>(a.logm, a.n1 / 2, (size_t)(1 << a.logm) * sizeof(typename VecOf<R>::c));
+            static_for<4, 8>([&](auto lc) {
+                constexpr int L = decltype(lc)::value;
+                if (a.logm == L) err = launch_cl(k_passBsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+            });
         });
         return err;
     }
@@ -463,11 +499,14 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
 template <class R>
 cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(a.logn1)) {
-        const Geom g = geom_small_fp64<R>(a.logn1, (a.K2 + 2) / 2, 0);
         cudaError_t err = cudaErrorInvalidValue;
-        static_for<4, 8>([&](auto lc) {
-            constexpr int L = decltype(lc)::value;
-            if (a.logn1 == L) err = launch_cl(k_passC8d_n<R, L>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        with_fp64_points([&](auto ec) {
+            constexpr int E = decltype(ec)::value;
+            const Geom g = geom_small_fp64<R, E>(a.logn1, (a.K2 + 2) / 2, 0);
+            static_for<4, 8>([&](auto lc) {
+                constexpr int L = decltype(lc)::value;
+                if (a.logn1 == L) err = launch_cl(k_passCsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+            });
         });
         return err;
     }

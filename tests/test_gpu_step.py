@@ -459,3 +459,20 @@ def test_heun_step_matches_oracle(fl, orc, prec, shape, kmax, amp, tol, nsteps):
     assert abs(mean.item() - mref) <= (1e-12 if prec == "fp64" else 1e-6) * abs(mref)
     assert t.item() == tref
     f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("points", ["4", "8"])
+def test_fp64_short_line_kernels_both_shapes(fl, orc, monkeypatch, points):
+    # the FP64 short-line kernels with 4 (default) or 8 points per thread,
+    # 10 steps of the 128 x 256 trajectory at 1e-12 every step
+    monkeypatch.setenv("FLAME_FP64_POINTS", points)
+    f, st0, state, mean, t = _setup(fl, 128, 256, "fp64", 16, 7)
+    p = _oparams(orc, f)
+    ref, mref, tref = st0.copy(), 0.0, p.t0
+    for n in range(10):
+        f.step(state, mean, t, 1)
+        ref, mref, tref = orc.step(p, ref, mref, tref, 1)
+        assert _box_err(_host(fl, state), ref, f.K1) < 1e-12, n
+        assert t.item() == tref
+    f.close()
