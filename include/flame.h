@@ -203,6 +203,25 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
  * or capacity < 1 with a non-NULL rec. */
 flame_status flame_set_record(flame_t h, double *rec, int capacity, int with_area);
 
+/* flame_step on HOST buffers: copies the state in, advances it by nsteps
+ * explicit Euler steps (flame_step's arithmetic and kernels) and copies it
+ * back, overlapping the copies with the step: the state goes in by column
+ * chunks on a copy stream of the handle and the first pass A runs on each
+ * chunk as it lands; the last pass C runs by column-pair chunks, each copied
+ * out as soon as it is done.
+ *   host_state  the compact box (ABI layout, the handle's complex type) in
+ *               host memory, in place; pinned memory (cudaHostAlloc or
+ *               cudaHostRegister) lets the copies run asynchronously and
+ *               overlap (pageable memory works but serialises them);
+ *   host_mean, host_t  one host double each, in place.
+ * The host buffers may be read or written until the stream reaches the end
+ * of the call (synchronise the stream before using them).  The handle
+ * allocates a device copy of the state and a copy stream on the first call.
+ * The per-step record and forcing apply as in flame_step.  EINVAL on null
+ * pointers or nsteps < 0; ENOMEM if the device copy cannot be allocated. */
+flame_status flame_step_host(flame_t h, void *host_state, double *host_mean, double *host_t,
+                             int nsteps, void *stream);
+
 /* Sets the forcing term f_k(t) of eq. (SivCurv1c) (Sec. 2; the paper's runs
  * have f = 0) for the handle's later step calls (flame_step, flame_step_heun,
  * flame_step_if, flame_step_batch and the adjoint's forward recomputation):

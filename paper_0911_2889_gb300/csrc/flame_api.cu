@@ -186,6 +186,11 @@ struct flame_ctx {
     double *rec = nullptr;
     int rec_cap = 0;
     bool rec_area = false;  // the record includes the surface area
+    // flame_step_host: device copies of the state, mean mode and time, the
+    // copy stream and the chunk events (created on first use)
+    void *io = nullptr;
+    cudaStream_t cpy = nullptr;
+    std::vector<cudaEvent_t> io_ev;
 };
 
 namespace {
@@ -215,6 +220,9 @@ void free_ctx(flame_ctx *h) {
     cudaFree(h->adj);
     cudaFree(h->dscal);
     cudaFree(h->status);
+    cudaFree(h->io);
+    for (auto e : h->io_ev) cudaEventDestroy(e);
+    if (h->cpy) cudaStreamDestroy(h->cpy);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -811,6 +819,99 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, in
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step: nsteps=%d < 0", nsteps);
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step: injected launch fault");
     return run_scheme(h, state, mean_mode, t, kSchemeEuler, nsteps, static_cast<cudaStream_t>(stream));
+}
+
+flame_status flame_step_host(flame_t h, void *host_state, double *host_mean, double *host_t, int nsteps,
+                             void *stream) {
+    if (!h || !host_state || !host_mean || !host_t) return fail(FLAME_EINVAL, "flame_step_host: null pointer");
+    if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step_host: nsteps=%d < 0", nsteps);
+    if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_host: injected launch fault");
+    if (nsteps == 0) return FLAME_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t ld1 = 2 * (size_t)h->p.K1 + 1, ncol = (size_t)h->p.K2 + 1, colb = ld1 * h->csz;
+    const size_t boxb = (ncol * colb + 255) & ~(size_t)255;
+    constexpr int kChunks = 8;
+    if (!h->io) {
+        if (cudaMalloc(&h->io, boxb + 256) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FLAME_ENOMEM, "flame_step_host: device allocation failed");
+        }
+    }
+    if (!h->cpy) CUDA_TRY(cudaStreamCreateWithFlags(&h->cpy, cudaStreamNonBlocking));
+    while (h->io_ev.size() < 2 * kChunks + 2) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->io_ev.push_back(e);
+    }
+    cudaEvent_t *ev_in = h->io_ev.data(), *ev_out = ev_in + kChunks, ev_start = ev_in[2 * kChunks],
+                ev_done = ev_in[2 * kChunks + 1];
+    char *dstate = static_cast<char *>(h->io);
+    double *dm = reinterpret_cast<double *>(dstate + boxb), *dtm = dm + 1;
+    char *hstate = static_cast<char *>(host_state);
+    const bool f64 = h->p.prec == FLAME_FP64;
+    int colsA = 1, quantA = 1, pairsC = 1;
+    if (f64) Ops<double>::tiles(h->sa, h->var_a, &colsA, &quantA, &pairsC);
+    else Ops<float>::tiles(h->sa, h->var_a, &colsA, &quantA, &pairsC);
+    const int tilesA = (int)((ncol + colsA - 1) / colsA), unitsA = (tilesA + quantA - 1) / quantA;
+    const int tilesC = (int)((((ncol + 1) / 2) + pairsC - 1) / pairsC);
+    const int KA = std::min(kChunks, unitsA), KC = std::min(kChunks, tilesC);
+    FlameDesc d = make_desc(h, dstate, dm, dtm);
+    auto passA = [&](const FlameDesc &x) {
+        return f64 ? Ops<double>::passA(x, s, h->var_a) : Ops<float>::passA(x, s, h->var_a, h->map());
+    };
+    auto passB = [&](const FlameDesc &x) {
+        return f64 ? Ops<double>::passB(x, s, h->var_b) : Ops<float>::passB(x, s, h->var_b, h->gmap());
+    };
+    auto passC = [&](const FlameDesc &x) { return f64 ? Ops<double>::passC(x, s) : Ops<float>::passC(x, s); };
+    // the copy stream starts after the work already on the caller's stream
+    CUDA_TRY(cudaEventRecord(ev_start, s));
+    CUDA_TRY(cudaStreamWaitEvent(h->cpy, ev_start, 0));
+    CUDA_TRY(cudaMemcpyAsync(dm, host_mean, sizeof(double), cudaMemcpyHostToDevice, h->cpy));
+    CUDA_TRY(cudaMemcpyAsync(dtm, host_t, sizeof(double), cudaMemcpyHostToDevice, h->cpy));
+    // state in by column chunks, pass A of the first step on each as it lands
+    for (int i = 0; i < KA; ++i) {
+        const int u0 = (int)((long)unitsA * i / KA), u1 = (int)((long)unitsA * (i + 1) / KA);
+        const int a0 = u0 * quantA, a1 = std::min(u1 * quantA, tilesA + quantA - 1);
+        const size_t c0 = (size_t)a0 * colsA, c1 = std::min((size_t)a1 * colsA, ncol);
+        if (c1 > c0)
+            CUDA_TRY(cudaMemcpyAsync(dstate + c0 * colb, hstate + c0 * colb, (c1 - c0) * colb, cudaMemcpyHostToDevice,
+                                     h->cpy));
+        CUDA_TRY(cudaEventRecord(ev_in[i], h->cpy));
+        CUDA_TRY(cudaStreamWaitEvent(s, ev_in[i], 0));
+        FlameDesc di = d;
+        di.tile0 = a0;
+        di.tiles = a1 - a0;
+        CUDA_TRY(passA(di));
+    }
+    CUDA_TRY(passB(d));
+    if (nsteps > 1) {
+        CUDA_TRY(passC(d));
+        for (int k = 1; k + 1 < nsteps; ++k) CUDA_TRY(enqueue_step(h, d, s));
+        CUDA_TRY(passA(d));
+        CUDA_TRY(passB(d));
+    }
+    // the last pass C by column-pair chunks, each copied out as it is done;
+    // tile 0 (first chunk) also finishes the mean mode and t
+    for (int j = 0; j < KC; ++j) {
+        const int q0 = (int)((long)tilesC * j / KC), q1 = (int)((long)tilesC * (j + 1) / KC);
+        FlameDesc dj = d;
+        dj.tile0 = q0;
+        dj.tiles = q1 - q0;
+        CUDA_TRY(passC(dj));
+        CUDA_TRY(cudaEventRecord(ev_out[j], s));
+        CUDA_TRY(cudaStreamWaitEvent(h->cpy, ev_out[j], 0));
+        const size_t c0 = (size_t)q0 * pairsC * 2, c1 = std::min((size_t)q1 * pairsC * 2, ncol);
+        if (c1 > c0)
+            CUDA_TRY(cudaMemcpyAsync(hstate + c0 * colb, dstate + c0 * colb, (c1 - c0) * colb, cudaMemcpyDeviceToHost,
+                                     h->cpy));
+        if (j == 0) {
+            CUDA_TRY(cudaMemcpyAsync(host_mean, dm, sizeof(double), cudaMemcpyDeviceToHost, h->cpy));
+            CUDA_TRY(cudaMemcpyAsync(host_t, dtm, sizeof(double), cudaMemcpyDeviceToHost, h->cpy));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(ev_done, h->cpy));
+    CUDA_TRY(cudaStreamWaitEvent(s, ev_done, 0));
+    return FLAME_OK;
 }
 
 flame_status flame_set_record(flame_t h, double *rec, int capacity, int with_area) {

@@ -10,4 +10,5 @@ template cudaError_t Ops<float>::cols(const float2 *, float2 *, int, int, int, i
 template cudaError_t Ops<float>::box_from_spec(const float2 *, float2 *, double *, int, int, int, int, cudaStream_t);
 template Geom Ops<float>::geom_cols(int, int, int);
 template Geom Ops<float>::geom_rows(int, int, int);
+template void Ops<float>::tiles(const StepArgs &, int, int *, int *, int *);
 }  // namespace flame

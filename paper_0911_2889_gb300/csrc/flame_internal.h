@@ -97,6 +97,9 @@ struct FlameDesc {
     int rec_area;
     double *arow;
     const double *aval;
+    // a launch over part of the tiles (pass A and C of one flame): tiles
+    // [tile0, tile0 + tiles) of the full grid; tiles = 0: all
+    int tile0, tiles;
     // L2 persisting window over the state for the launches of passes A and
     // C (a launch attribute, not read by the kernels); bytes = 0: none
     L2Window l2_state;
@@ -168,6 +171,10 @@ template <class R> struct Ops {
     static cudaError_t passB_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
                                    int variant = 0, const CUtensorMap *maps = nullptr);
     static cudaError_t passC_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
+    // Tiles (CTAs) of passes A and C: columns per pass-A tile, the tile
+    // multiple a partial pass-A launch must use (clusters), column pairs per
+    // pass-C tile
+    static void tiles(const StepArgs &a, int variant, int *colsA, int *quantA, int *pairsC);
     // geometry used by the step passes (for the autotuner and the tests)
     static Geom geom_cols(int logn, int nlines, int groups_hint);
     static Geom geom_rows(int logm, int nlines, int groups_hint);

@@ -1217,29 +1217,29 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
 // equal-size flames (descriptor array, flame = blockIdx.y).  LOG > 0: line
 // length 2^LOG fixed at compile time; LOG = 0: any length.
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passA(FlameDesc d, int pf) {
-    passA_body<R, LOG, 16>(d, blockIdx.x, gridDim.x, pf);
+    passA_body<R, LOG, 16>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
 }
 // compile-time length, direct (scattered) stores instead of the cluster write-out
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAd(FlameDesc d, int pf) {
-    passA_body<R, LOG, 16, false>(d, blockIdx.x, gridDim.x, pf);
+    passA_body<R, LOG, 16, false>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
 }
 // compile-time length, column written out by tensor stores (FP32); the
 // tensor map describes uv as (8 floats of a row pair) x k2 x row pair
 template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAt(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
-    passA_body<R, LOG, 16, false, true>(d, blockIdx.x, gridDim.x, pf, &tm);
+    passA_body<R, LOG, 16, false, true>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf, &tm);
 }
 // FP64 at short compile-time lengths (2^4 .. 2^7), E = 8 or 4 points per
 // thread: one line pair per CTA of 2^LOG / E threads (up to a warp at 128
 // points with E = 4), for the latency-bound small FP64 grids
 template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passAsd(FlameDesc d, int pf) {
-    passA_body<R, LOG, E, false>(d, blockIdx.x, gridDim.x, pf);
+    passA_body<R, LOG, E, false>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
 }
 template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passBsd(FlameDesc d, int pf) {
     passB_body<R, LOG, E>(d, blockIdx.x, gridDim.x, pf);
 }
 template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passCsd(FlameDesc d, int pf) {
-    passC_body<R, LOG, false, E>(d, blockIdx.x, gridDim.x, pf);
+    passC_body<R, LOG, false, E>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
 }
 template <class R, int LOG, int E>
 __global__ void __launch_bounds__(128, 1) k_passCsd_n(const FlameDesc *__restrict__ ds, int pf) {
@@ -1255,7 +1255,7 @@ __global__ void __launch_bounds__(128, 1) k_passBsd_n(const FlameDesc *__restric
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(FlameDesc d, int pf) {
-    passA_body<R, LOG, 8>(d, blockIdx.x, gridDim.x, pf);
+    passA_body<R, LOG, 8>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
 }
 template <class R, int LOG> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passB(FlameDesc d, int pf) {
     passB_body<R, LOG, 16>(d, blockIdx.x, gridDim.x, pf);
@@ -1279,7 +1279,7 @@ template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passB8(F
 }
 template <class R, int LOG, bool GEN = true>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passC(FlameDesc d, int pf) {
-    passC_body<R, LOG, false, 16, GEN>(d, blockIdx.x, gridDim.x, pf);
+    passC_body<R, LOG, false, 16, GEN>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
 }
 // pass C of one step fused with pass A of the next (FP32, compile-time
 // lengths): the updated column pair is transformed back and written to uv

@@ -251,7 +251,7 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
-                    err = launch_w(d.l2_state, k_passAsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+                    err = launch_w(d.l2_state, k_passAsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, 0);
             });
         });
         return err;
@@ -263,21 +263,21 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
         constexpr int cl = cluster_of<R, L>();
         if (sizeof(R) == 4 && L > 0 && variant == kVariantTma && uv_map) {  // tensor-store write-out
             const int pf = resident_ctas((const void *)k_passAt<R, L>, g);
-            err = launch_w(d.l2_state, k_passAt<R, L>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
+            err = launch_w(d.l2_state, k_passAt<R, L>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
         } else if (cl > 1 && (variant == kVariantDirect || variant == kVariantTma)) {  // direct stores
             Geom gd = g;
             const int pf = resident_ctas((const void *)k_passAd<R, L>, gd);
-            err = launch_w(d.l2_state, k_passAd<R, L>, dim3(gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
+            err = launch_w(d.l2_state, k_passAd<R, L>, dim3(d.tiles ? d.tiles : gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
             const Geom g8 = geom_passA8<R, L>(d.a.K2 + 1);
             constexpr int cl8 = ShapeE<L, 8>::CL;
             const int pf = resident_ctas((const void *)k_passA8<R, L>, g8);
-            err = launch_w(d.l2_state, k_passA8<R, L>, dim3(round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
+            err = launch_w(d.l2_state, k_passA8<R, L>, dim3(d.tiles ? d.tiles : round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
         } else {
             // the compile-time kernels assume Shape<L>::G groups per CTA
             Geom gl = cl > 1 ? geom_cols(d.a.logn1, d.a.K2 + 1, Shape<L>::G) : g;
             const int pf = resident_ctas((const void *)k_passA<R, L>, gl);
-            err = launch_w(d.l2_state, k_passA<R, L>, dim3(round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
+            err = launch_w(d.l2_state, k_passA<R, L>, dim3(d.tiles ? d.tiles : round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
         }
     });
     if (err != cudaSuccess) return err;
@@ -384,7 +384,8 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
-                    err = launch_w(d.l2_state, k_passCsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+                    err = launch_w(d.l2_state, k_passCsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem,
+                                   s, 1, d, 0);
             });
         });
         return err;
@@ -396,10 +397,12 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
         constexpr int L = decltype(lc)::value;
         if (gen) {
             const int pf = resident_ctas((const void *)k_passC<R, L, true>, g);
-            err = launch_w(d.l2_state, k_passC<R, L, true>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+            err = launch_w(d.l2_state, k_passC<R, L, true>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1,
+                           d, pf);
         } else {
             const int pf = resident_ctas((const void *)k_passC<R, L, false>, g);
-            err = launch_w(d.l2_state, k_passC<R, L, false>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf);
+            err = launch_w(d.l2_state, k_passC<R, L, false>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s,
+                           1, d, pf);
         }
     });
     if (err != cudaSuccess) return err;
@@ -576,6 +579,35 @@ template <class R> cudaError_t Ops<R>::adj_step(const AdjDesc &d, cudaStream_t s
         if (e == cudaSuccess) e = launch_cl(k_adjC<R, L>, dim3(ga.blocks), ga.threads, ga.smem, s, 1, d);
     });
     return e;
+}
+
+// Columns per tile of pass A (tiles = CTAs; clustered variants launch whole
+// clusters) and column pairs per tile of pass C, with the tile granularity a
+// partial launch must respect (flame_step_host).
+template <class R> void Ops<R>::tiles(const StepArgs &a, int variant, int *colsA, int *quantA, int *pairsC) {
+    *quantA = 1;
+    if (small_fp64<R>(a.logn1)) {
+        *colsA = 1;
+        *pairsC = 1;
+        return;
+    }
+    Geom g = make_geom<R>(a.logn1, a.K2 + 1, 0);
+    *colsA = g.threads >> (a.logn1 - 4);
+    with_log<R>(a.logn1, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        constexpr int cl = cluster_of<R, L>();
+        if constexpr (sizeof(R) == 4 && L > 0) {
+            if (variant == kVariantRadix8A) {
+                *colsA = ShapeE<L, 8>::G;
+                *quantA = ShapeE<L, 8>::CL;
+            } else if (cl > 1 && variant == kVariantDefault) {
+                *colsA = Shape<L>::G;
+                *quantA = cl;
+            }
+        }
+    });
+    Geom gc = make_geom<R>(a.logn1, (a.K2 + 2) / 2, 0);
+    *pairsC = gc.threads >> (a.logn1 - 4);
 }
 
 }  // namespace flame

@@ -62,6 +62,7 @@ SIGNATURES = {
     "flame_step_heun": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_step_if": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_set_forcing": (_i, [_vp, _vp, ctypes.c_double]),
+    "flame_step_host": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "flame_set_record": (_i, [_vp, _vp, _i, _i]),
     "flame_step_pass": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "flame_step_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp]),
@@ -187,6 +188,23 @@ def flame_step_if(h, state, mean_mode, t, nsteps=1, stream=None):
     _check(load().flame_step_if(ctypes.c_void_p(h), _ptr(state, name="state"),
                                 _ptr(mean_mode, torch.float64, "mean_mode"),
                                 _ptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
+
+
+def _hptr(t: torch.Tensor, dtype=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def flame_step_host(h, state, mean_mode, t, nsteps=1, stream=None):
+    """flame_step on host tensors (pinned for overlapped copies)."""
+    _check(load().flame_step_host(ctypes.c_void_p(h), _hptr(state, name="state"),
+                                  _hptr(mean_mode, torch.float64, "mean_mode"),
+                                  _hptr(t, torch.float64, "t"), int(nsteps), _stream(stream)))
 
 
 def flame_set_forcing(h, forcing=None, forcing0=0.0):
@@ -334,6 +352,12 @@ class Flame:
     def _check_state(self, state):
         if state.dtype != self.cdtype or tuple(state.shape) != self.state_shape:
             raise ValueError(f"state must be {self.cdtype} {self.state_shape}")
+
+    def step_host(self, state, mean_mode, t, nsteps=1, stream=None):
+        """nsteps explicit steps on host tensors (flame_step_host): the copies
+        in and out overlap the step's first and last column passes."""
+        self._check_state(state)
+        flame_step_host(self.h, state, mean_mode, t, nsteps, stream)
 
     def step_heun(self, state, mean_mode, t, nsteps=1, stream=None):
         """nsteps steps of Heun's second-order method (flame_step_heun)."""

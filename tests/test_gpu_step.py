@@ -476,3 +476,24 @@ def test_fp64_short_line_kernels_both_shapes(fl, orc, monkeypatch, points):
         assert _box_err(_host(fl, state), ref, f.K1) < 1e-12, n
         assert t.item() == tref
     f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,shape,nsteps", [
+    ("fp64", (128, 256), 1), ("fp64", (128, 256), 3), ("fp32", (256, 512), 1), ("fp32", (1024, 2048), 4),
+    ("fp32", (4096, 8192), 1), ("fp32", (512, 256), 2)])
+def test_step_on_host_buffers_equals_device_steps(fl, prec, shape, nsteps):
+    # flame_step_host (chunked copies overlapping the first pass A and the
+    # last pass C, partial launches over the tiles) gives exactly the
+    # results of flame_step on device buffers
+    n1, n2 = shape
+    f, st0, state, mean, t = _setup(fl, n1, n2, prec, 64, 33, amp=1e-2)
+    hs = state.cpu().pin_memory()
+    hm = torch.zeros(1, dtype=torch.float64).pin_memory()
+    ht = torch.full((1,), float(f.params.t0), dtype=torch.float64).pin_memory()
+    f.step_host(hs, hm, ht, nsteps)
+    f.step(state, mean, t, nsteps)
+    torch.cuda.synchronize()
+    assert torch.equal(hs, state.cpu())
+    assert hm.item() == mean.item() and ht.item() == t.item()
+    f.close()
