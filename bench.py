@@ -370,24 +370,22 @@ def run_ours(args):
     achieved = pbytes[dom] / (avg[dom] * 1e-3) / 1e9
     step_bytes = sum(pbytes[q] for q in seq) / args.steps
 
-    # end to end through the public API with host buffers (pinned), copies
-    # of the step's inputs and results inside the timed region
+    # end to end through the public API with host buffers (pinned): one
+    # flame_step_host call per step, its copies of the state, mean mode and
+    # time in and out inside the timed region (the library overlaps them
+    # with the step's first and last column passes)
     hs = state.cpu().pin_memory()
     hm = mean.cpu().pin_memory()
     ht = t.cpu().pin_memory()
+    f.step_host(hs, hm, ht, 1, stream)  # first call: the handle's device copy and copy stream
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
     for k in range(max(3, args.steps // 2)):
         flush.zero_()
         e0.record(stream)
-        state.copy_(hs, non_blocking=True)
-        mean.copy_(hm, non_blocking=True)
-        t.copy_(ht, non_blocking=True)
-        f.step(state, mean, t, 1, stream)
-        hs.copy_(state, non_blocking=True)
-        hm.copy_(mean, non_blocking=True)
-        ht.copy_(t, non_blocking=True)
+        f.step_host(hs, hm, ht, 1, stream)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
