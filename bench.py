@@ -335,11 +335,15 @@ def run_ours(args):
             ev[len(seq)].record(stream)
         return seq
 
-    run_steps(args.warmup)
+    # The timed region: one flame_step(K) call, the call a user makes (K
+    # steps as one captured CUDA graph; consecutive passes are programmatic
+    # dependent launches), bracketed by events on the launching stream.
+    f.step(state, mean, t, args.warmup, stream)  # warm-up (and graph capture of W steps)
+    f.step(state, mean, t, args.steps, stream)   # capture the graph of K steps
     f.sync_status()
     torch.cuda.synchronize()
-    seq = sequence(args.steps)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(seq) + 1)]
+    t_a = torch.cuda.Event(enable_timing=True)
+    t_b = torch.cuda.Event(enable_timing=True)
     flush.zero_()  # L2 starts cold; the steps then stream their working set (> L2) back to back
     if world > 1:
         dist.barrier()
@@ -347,18 +351,30 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.__enter__()
     wall0 = time.perf_counter()
-    run_steps(args.steps, evs)
+    t_a.record(stream)
+    f.step(state, mean, t, args.steps, stream)
+    t_b.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    total_ms = reduce_max(t_a.elapsed_time(t_b), device="cuda")
+    # Per-kernel durations for the roofline: the same steps launched pass by
+    # pass as flame_step enqueues them, one event before every launch.
+    run_steps(args.warmup)
+    seq = sequence(args.steps)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(seq) + 1)]
+    flush.zero_()
+    torch.cuda.synchronize()
+    run_steps(args.steps, evs)
+    torch.cuda.synchronize()
     # keep the GPU busy with more steps of the same workload so the clock
     # samples see it under load (not timed)
-    run_steps(max(200, args.steps))
+    f.step(state, mean, t, max(200, args.steps), stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     f.sync_status()
     launch_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(seq))]
-    total_ms = reduce_max(evs[0].elapsed_time(evs[-1]), device="cuda")
+    passwise_ms = evs[0].elapsed_time(evs[-1])
     kinds = sorted(set(seq))
     kind_ms = {ps: [ms for ms, q in zip(launch_ms, seq) if q == ps] for ps in kinds}
     avg = {ps: sum(v) / len(v) for ps, v in kind_ms.items()}
@@ -434,6 +450,7 @@ def run_ours(args):
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "alg_bytes": pbytes[dom], "avg_ms": avg[dom]},
             "passes_ms": {PASS_NAMES[ps]: avg[ps] for ps in kinds},
+            "passwise_ms_per_step": passwise_ms / args.steps,
             "step_effective_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},

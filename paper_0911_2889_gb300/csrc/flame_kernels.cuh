@@ -316,6 +316,12 @@ __device__ __forceinline__ void l2_prefetch(const void *begin, size_t bytes) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((unsigned)(e - b)) : "memory");
 }
 
+// Programmatic dependent launch: wait until the previous kernel on the
+// stream has completed and its memory is visible (a no-op when the launch is
+// an ordinary one), and let the next kernel's CTAs be scheduled.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Tensor stores (TMA) from shared memory.  The writing threads fence their
 // shared-memory stores towards the async proxy, the CTA synchronises, then one
 // thread issues the copies, commits them as a bulk group and waits until they
@@ -453,6 +459,8 @@ template <int E> struct ShapeE<0, E> {  // runtime-length kernels: no clusters
 template <class R, int LOG, int E, bool CLU = true, bool TMA = false, bool GMAP = false>
 __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
+    griddep_wait();
+    griddep_launch();
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -670,6 +678,8 @@ template <class F> __device__ __forceinline__ F group_sum(F v, int T, F *scratch
 template <class R, int LOG, int E, bool TMA = false, bool GMAP = false, bool AREA = false>
 __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
+    griddep_wait();
+    griddep_launch();
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -946,6 +956,8 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
 template <class R, int LOG, bool FUSE_A = false, int E = 16, bool GEN = true>
 __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
+    griddep_wait();
+    griddep_launch();
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     static_assert(E == 16 || ((E == 8 || E == 4) && !FUSE_A),

@@ -109,12 +109,23 @@ template <class R, class F> static void with_log(int logn, F &&f) {
 // multiple of cl; cl <= 1: none) and, when w.bytes > 0, an L2 persisting
 // access window over [w.base, w.base + w.bytes) (a fraction w.hit of its
 // accesses persisting, the rest streaming).
+// With pdl, the launch is a programmatic dependent launch: its CTAs may be
+// scheduled while the previous kernel on the stream drains, and wait in
+// hardware (griddepcontrol.wait, the first statement of every step pass's
+// body) until that kernel has completed and its memory is visible.  Only
+// the step passes, whose bodies begin with that wait, are launched so.
+// Opt-in (FLAME_PDL=1): at 4096 x 8192 the graph-captured steps measured
+// 0.2026 ms per step with it against 0.1967 ms without.
+static bool pdl_on() {
+    const char *v = getenv("FLAME_PDL");
+    return v && strcmp(v, "1") == 0;
+}
 template <class... KArgs, class... Args>
-static cudaError_t launch_w(const L2Window &w, void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
-                            cudaStream_t s, int cl, Args... args) {
+static cudaError_t launch_x(const L2Window &w, bool pdl, void (*kernel)(KArgs...), dim3 grid, int threads,
+                            size_t smem, cudaStream_t s, int cl, Args... args) {
     const cudaError_t oe = opt_in((const void *)kernel);
     if (oe != cudaSuccess) return oe;
-    if (cl <= 1 && w.bytes == 0) {
+    if (cl <= 1 && w.bytes == 0 && !pdl) {
         kernel<<<grid, threads, smem, s>>>(args...);
         return cudaGetLastError();
     }
@@ -123,8 +134,13 @@ static cudaError_t launch_w(const L2Window &w, void (*kernel)(KArgs...), dim3 gr
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[3];
     unsigned n = 0;
+    if (pdl) {
+        attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
     if (cl > 1) {
         attr[n].id = cudaLaunchAttributeClusterDimension;
         attr[n].val.clusterDim.x = cl;
@@ -144,6 +160,17 @@ static cudaError_t launch_w(const L2Window &w, void (*kernel)(KArgs...), dim3 gr
     cfg.attrs = attr;
     cfg.numAttrs = n;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <class... KArgs, class... Args>
+static cudaError_t launch_w(const L2Window &w, void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
+                            cudaStream_t s, int cl, Args... args) {
+    return launch_x(w, false, kernel, grid, threads, smem, s, cl, args...);
+}
+// a step pass of one flame: L2 window and programmatic dependent launch
+template <class... KArgs, class... Args>
+static cudaError_t launch_s(const L2Window &w, void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
+                            cudaStream_t s, int cl, Args... args) {
+    return launch_x(w, pdl_on(), kernel, grid, threads, smem, s, cl, args...);
 }
 template <class... KArgs, class... Args>
 static cudaError_t launch_cl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t s, int cl,
@@ -251,7 +278,7 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
-                    err = launch_w(d.l2_state, k_passAsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, 0);
+                    err = launch_s(d.l2_state, k_passAsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, 0);
             });
         });
         return err;
@@ -263,21 +290,21 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
         constexpr int cl = cluster_of<R, L>();
         if (sizeof(R) == 4 && L > 0 && variant == kVariantTma && uv_map) {  // tensor-store write-out
             const int pf = resident_ctas((const void *)k_passAt<R, L>, g);
-            err = launch_w(d.l2_state, k_passAt<R, L>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
+            err = launch_s(d.l2_state, k_passAt<R, L>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, pf, *uv_map);
         } else if (cl > 1 && (variant == kVariantDirect || variant == kVariantTma)) {  // direct stores
             Geom gd = g;
             const int pf = resident_ctas((const void *)k_passAd<R, L>, gd);
-            err = launch_w(d.l2_state, k_passAd<R, L>, dim3(d.tiles ? d.tiles : gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
+            err = launch_s(d.l2_state, k_passAd<R, L>, dim3(d.tiles ? d.tiles : gd.blocks), gd.threads, gd.smem, s, 1, d, pf);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8A) {
             const Geom g8 = geom_passA8<R, L>(d.a.K2 + 1);
             constexpr int cl8 = ShapeE<L, 8>::CL;
             const int pf = resident_ctas((const void *)k_passA8<R, L>, g8);
-            err = launch_w(d.l2_state, k_passA8<R, L>, dim3(d.tiles ? d.tiles : round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
+            err = launch_s(d.l2_state, k_passA8<R, L>, dim3(d.tiles ? d.tiles : round_up(g8.blocks, cl8)), g8.threads, g8.smem, s, cl8, d, pf);
         } else {
             // the compile-time kernels assume Shape<L>::G groups per CTA
             Geom gl = cl > 1 ? geom_cols(d.a.logn1, d.a.K2 + 1, Shape<L>::G) : g;
             const int pf = resident_ctas((const void *)k_passA<R, L>, gl);
-            err = launch_w(d.l2_state, k_passA<R, L>, dim3(d.tiles ? d.tiles : round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
+            err = launch_s(d.l2_state, k_passA<R, L>, dim3(d.tiles ? d.tiles : round_up(gl.blocks, cl)), gl.threads, gl.smem, s, cl, d, pf);
         }
     });
     if (err != cudaSuccess) return err;
@@ -309,7 +336,7 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
             const Geom g = geom_small_fp64<R, E>(d.a.logm, d.a.n1 / 2, (size_t)(1 << d.a.logm) * sizeof(typename VecOf<R>::c));
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
-                if (d.a.logm == L) err = launch_cl(k_passBsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+                if (d.a.logm == L) err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
             });
         });
         return err;
@@ -322,16 +349,16 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
             Geom gb = g;
             if (kSharedTw<R, L, 16>) gb.smem += kTwSmemBytes;
             const int pf = resident_ctas((const void *)k_passBt<R, L>, gb);
-            err = launch_cl(k_passBt<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf, *gk_map);
+            err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBt<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf, *gk_map);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {
             const Geom g8 = geom_passB8<R>(L, d.a.n1 / 2);
             const int pf = resident_ctas((const void *)k_passB8<R, L>, g8);
-            err = launch_cl(k_passB8<R, L>, dim3(g8.blocks), g8.threads, g8.smem, s, 1, d, pf);
+            err = launch_s(L2Window{nullptr, 0, 0.f}, k_passB8<R, L>, dim3(g8.blocks), g8.threads, g8.smem, s, 1, d, pf);
         } else {
             Geom gb = g;
             if (kSharedTw<R, L, 16>) gb.smem += kTwSmemBytes;
             const int pf = resident_ctas((const void *)k_passB<R, L>, gb);
-            err = launch_cl(k_passB<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf);
+            err = launch_s(L2Window{nullptr, 0, 0.f}, k_passB<R, L>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf);
         }
     });
     if (err != cudaSuccess) return err;
@@ -384,7 +411,7 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
-                    err = launch_w(d.l2_state, k_passCsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem,
+                    err = launch_s(d.l2_state, k_passCsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem,
                                    s, 1, d, 0);
             });
         });
@@ -397,11 +424,11 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
         constexpr int L = decltype(lc)::value;
         if (gen) {
             const int pf = resident_ctas((const void *)k_passC<R, L, true>, g);
-            err = launch_w(d.l2_state, k_passC<R, L, true>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1,
+            err = launch_s(d.l2_state, k_passC<R, L, true>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1,
                            d, pf);
         } else {
             const int pf = resident_ctas((const void *)k_passC<R, L, false>, g);
-            err = launch_w(d.l2_state, k_passC<R, L, false>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s,
+            err = launch_s(d.l2_state, k_passC<R, L, false>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s,
                            1, d, pf);
         }
     });
@@ -418,11 +445,11 @@ cudaError_t Ops<R>::passCA(const FlameDesc &d, cudaStream_t s, const CUtensorMap
         if constexpr (sizeof(R) == 4 && L > 0) {
             if (general_epilogue(d)) {
                 const int pf = resident_ctas((const void *)k_passCA<R, L, true>, g);
-                err = launch_w(d.l2_state, k_passCA<R, L, true>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf,
+                err = launch_s(d.l2_state, k_passCA<R, L, true>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf,
                                *uv_map);
             } else {
                 const int pf = resident_ctas((const void *)k_passCA<R, L, false>, g);
-                err = launch_w(d.l2_state, k_passCA<R, L, false>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf,
+                err = launch_s(d.l2_state, k_passCA<R, L, false>, dim3(g.blocks), g.threads, g.smem, s, 1, d, pf,
                                *uv_map);
             }
         }
