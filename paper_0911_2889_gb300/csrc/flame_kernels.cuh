@@ -401,6 +401,13 @@ struct Roots32 {
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// 1/x and sqrt(x) (x > 0) for the area terms: FP32 within a few ulp from the
+// hardware reciprocal and reciprocal square root, FP64 correctly rounded
+__device__ __forceinline__ float rcp_r(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_r(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+
 // b * exp(i pi r / E) * sgn with the factor a compile-time constant
 template <int R_, int E, int SGN, class C> __device__ __forceinline__ C mul_root(C b) {
     using Real = decltype(C::x);
@@ -803,7 +810,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
             const C ph = st0[k1];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const int m = (int)(((long)k1 * (2 * pair + q)) % a.n1);
+                const int m = (k1 * (2 * pair + q)) & (a.n1 - 1);  // N1 a power of two
                 C w = __ldg(t1r + ((2 * m < a.n1) ? 2 * m : 2 * m - a.n1));
                 if (2 * m >= a.n1) w = C{-w.x, -w.y};
                 p0[q] += 2 * (ph.x * w.x - ph.y * w.y);
@@ -822,7 +829,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
                 P1 = C{p0[1], 0};
             } else if (kk < half) {
                 const C v0 = ld_uv_s<R>(stage0 + kk).v, v1 = ld_uv_s<R>(stage1 + kk).v;
-                const R f = is2 / (R)kk;  // P = V / (i s2 k) = (V.y, -V.x) / (s2 k)
+                const R f = is2 * rcp_r((R)kk);  // P = V / (i s2 k) = (V.y, -V.x) / (s2 k)
                 P0 = C{v0.y * f, -v0.x * f};
                 P1 = C{v1.y * f, -v1.x * f};
             }
@@ -845,7 +852,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
                 const CV<V> ph = phi_park[t + r * T];
                 const V pv = second ? ph.im : ph.re;
                 const R R0 = rr + pv.x, R1 = rr + pv.y;
-                apart += R0 * sqrt(fma_rn(R0, R0, gv[r].x)) + R1 * sqrt(fma_rn(R1, R1, gv[r].y));
+                apart += R0 * sqrt_r(fma_rn(R0, R0, gv[r].x)) + R1 * sqrt_r(fma_rn(R1, R1, gv[r].y));
             }
         }
     };
@@ -1281,8 +1288,8 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBt(FlameDesc d, int 
 }
 // pass B that also sums the rows' surface area (the per-step record); its
 // shared memory (three more row-length buffers) allows one CTA per SM
-template <class R, int LOG, int E>
-__global__ void __launch_bounds__(E == 16 ? 256 : 128, 1) k_passB_area(FlameDesc d) {
+template <class R, int LOG, int E, int NT>
+__global__ void __launch_bounds__(NT, 1) k_passB_area(FlameDesc d) {
     passB_body<R, LOG, E, false, false, true>(d, blockIdx.x, gridDim.x, 0);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)

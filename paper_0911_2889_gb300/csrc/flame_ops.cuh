@@ -382,10 +382,26 @@ template <class R> cudaError_t Ops<R>::passB_area(const FlameDesc &d, cudaStream
             if (g.smem + 4096 > (size_t)optin) return;
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
-                if (d.a.logm == L) err = launch_cl(k_passB_area<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d);
+                if (d.a.logm == L)
+                    err = launch_cl(k_passB_area<R, L, E, 128>, dim3(g.blocks), g.threads, g.smem, s, 1, d);
             });
         });
         return err;
+    }
+    // FP32 compile-time rows: 8 points per thread, 512-thread CTAs (one per
+    // SM: the area buffers take most of the shared memory, and 16 warps hide
+    // more latency than the 8 of 16 points per thread)
+    if constexpr (sizeof(R) == 4) if (d.a.logm >= 8 && d.a.logm <= 12) {
+        Geom g = geom_passB8<R>(d.a.logm, d.a.n1 / 2);
+        const int G = g.threads / (M / 8);
+        g.smem += (size_t)G * area_extra;
+        if (g.smem + 4096 > (size_t)optin) return cudaErrorNotSupported;
+        with_log<R>(d.a.logm, [&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if constexpr (L > 0) err = launch_cl(k_passB_area<R, L, 8, 512>, dim3(g.blocks), g.threads, g.smem, s, 1, d);
+        });
+        if (err != cudaSuccess) return err;
+        return cudaGetLastError();
     }
     Geom g = make_geom<R>(d.a.logm, d.a.n1 / 2, 0, (size_t)M * sizeof(typename VecOf<R>::c) + area_extra);
     with_log<R>(d.a.logm, [&](auto lc) {
@@ -396,7 +412,7 @@ template <class R> cudaError_t Ops<R>::passB_area(const FlameDesc &d, cudaStream
             err = cudaErrorNotSupported;
             return;
         }
-        err = launch_cl(k_passB_area<R, L, 16>, dim3(ga.blocks), ga.threads, ga.smem, s, 1, d);
+        err = launch_cl(k_passB_area<R, L, 16, 256>, dim3(ga.blocks), ga.threads, ga.smem, s, 1, d);
     });
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
