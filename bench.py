@@ -20,7 +20,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -31,6 +30,15 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="flame-step-4096x8192-fp32mixed", n1=4096, n2=8192, prec="fp32", kmax=256,
                 seed=0, gamma=0.8, t0=200.0, dt=1e-3)
 L2_BYTES = 129 * 1024 * 1024
+
+
+def workload_config(world):
+    """The `config` object of the JSON line, the same for both arms."""
+    w = WORKLOAD
+    return {"workload": w["workload"], "grid": [w["n1"], w["n2"]], "kmax": w["kmax"],
+            "l2": "inputs larger than L2: each step streams its 235 MB working set (state 33.5 MB, "
+                  "uv 134 MB, gk 67 MB) through the 129 MB L2; flushed once before the timed steps",
+            "parallelism": f"replicas{world}"}
 FLUSH_BYTES = 512 * 1024 * 1024
 
 
@@ -56,60 +64,71 @@ def pass_bytes(n1, n2, K1, K2, esz):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled through NVML every
+    ~0.5 ms while the timed region runs.  The device is found by its UUID,
+    so CUDA_VISIBLE_DEVICES renumbering does not matter.  Reads only: no
+    setting of the GPU is changed."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap,utilization.gpu")
+    # clock-event reason bits of NVML's public header
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-
-    def __enter__(self):
+    def __init__(self, device_index):
+        self.samples, self.max_mhz, self.error = [], None, None
+        self._stop = threading.Event()
+        self._thread = None
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "20"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except Exception:
-            self.proc = None
-        time.sleep(0.3)
+            import ctypes
+            import torch
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            uuid = getattr(torch.cuda.get_device_properties(device_index), "uuid", None)
+            if uuid is None:
+                raise RuntimeError("device UUID not exposed")
+            self._h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByUUID(f"GPU-{uuid}".encode(), ctypes.byref(self._h)) != 0:
+                raise RuntimeError("no NVML handle for the device")
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(self._h, 1, ctypes.byref(mx)) == 0:  # 1 = SM clock
+                self.max_mhz = float(mx.value)
+            self._nv, self._ct = nv, ctypes
+            self._reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except Exception as e:  # noqa: BLE001 - reported in the summary
+            self._nv, self.error = None, f"{type(e).__name__}: {e}"
+
+    def _poll(self):
+        ct, nv = self._ct, self._nv
+        clk, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self._stop.is_set():
+            if nv.nvmlDeviceGetClockInfo(self._h, 1, ct.byref(clk)) == 0 and \
+                    self._reasons(self._h, ct.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            time.sleep(0.0005)
+
+    def start(self):
+        if self._nv is not None:
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
         return self
 
-    def __exit__(self, *exc):
-        self.lines = []
-        if self.proc:
-            time.sleep(0.2)
-            self.proc.terminate()
-            out, _ = self.proc.communicate(timeout=10)
-            self.lines = [l for l in out.splitlines() if l.strip()]
+    def stop(self):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join()
 
     def summary(self):
-        """Median SM clock over the samples taken with the GPU busy (>= 50 %
-        utilisation); the throttle reasons seen in those samples."""
-        sm, mx, reasons, total = [], None, set(), 0
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
-            parts = [p.strip() for p in l.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                clk, mxc, util = float(parts[0]), float(parts[1]), float(parts[7])
-            except ValueError:
-                continue
-            total += 1
-            mx = mxc
-            if util < 50:
-                continue
-            sm.append(clk)
-            for n, v in zip(names, parts[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples under load"], "samples": total}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples_under_load": len(sm), "samples": total}
+        """Median SM clock over the samples of the timed region and every
+        clock-event reason seen active in them."""
+        if not self.samples:
+            why = self.error or "no samples in the timed region"
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [why], "samples": 0}
+        seen = set()
+        for _, bits in self.samples:
+            seen.update(n for b, n in self.REASONS.items() if bits & b)
+        return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(seen), "samples": len(self.samples), "source": "nvml"}
 
 
 def cpu_oracle_step_time(w, nsteps=1):
@@ -146,7 +165,7 @@ def run_reference(args):
         "impl": "reference", "metric": "grid_point_updates_per_s", "value": v, "unit": "points/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w["workload"], "grid": [w["n1"], w["n2"]]},
+        "data": "synthetic", "config": workload_config(args.gpus),
         "cpu_baseline": {"value": v, "unit": "points/s", "cores": threads, "kind": "oracle",
                          "sample": "one full FP64 oracle step of the 4096x8192 workload per timed step"},
         "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -349,13 +368,14 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
-    clk.__enter__()
+    clk.start()
     wall0 = time.perf_counter()
     t_a.record(stream)
     f.step(state, mean, t, args.steps, stream)
     t_b.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clk.stop()
     total_ms = reduce_max(t_a.elapsed_time(t_b), device="cuda")
     # Per-kernel durations for the roofline: the same steps launched pass by
     # pass as flame_step enqueues them, one event before every launch.
@@ -365,10 +385,6 @@ def run_ours(args):
     flush.zero_()
     torch.cuda.synchronize()
     run_steps(args.steps, evs)
-    torch.cuda.synchronize()
-    # keep the GPU busy with more steps of the same workload so the clock
-    # samples see it under load (not timed)
-    f.step(state, mean, t, max(200, args.steps), stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -429,7 +445,6 @@ def run_ours(args):
         fp64_peak = flame.flame_fma_peak("fp64")
         traj64 = measure_trajectory(flame, inputs, 128, 256, "fp64", 16, 100, fp64_peak)
         traj32 = measure_trajectory(flame, inputs, 1024, 2048, "fp32", 256, 1000)
-    clk.__exit__(None, None, None)
 
     if rank == 0:
         cpu = None
@@ -442,10 +457,8 @@ def run_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w["workload"], "grid": [n1, n2], "kmax": w["kmax"],
-                       "l2": "inputs larger than L2: each step streams its 235 MB working set (state 33.5 MB, "
-                             "uv 134 MB, gk 67 MB) through the 129 MB L2; flushed once before the timed steps",
-                       "fused_column_passes": fused, "parallelism": f"replicas{world}"},
+            "config": workload_config(world),
+            "fused_column_passes": fused,
             "roofline": {"bound": "hbm", "kernel": f"pass{PASS_NAMES[dom]}", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "alg_bytes": pbytes[dom], "avg_ms": avg[dom]},
