@@ -633,6 +633,35 @@ def run_profile(args):
     f.close()
 
 
+def run_profile_ensemble(args):
+    """The ensemble of measure_batched for ncu or a quick timing: builds the
+    256 flames, runs 8 warm-up steps and then `--profile-ensemble N` steps in
+    one flame_step_batch call, and prints their event time per step."""
+    import torch
+    from paper_0911_2889_gb300 import flame, inputs
+    grids = inputs.batch_grids(256)
+    fl, ss, ms, ts = [], [], [], []
+    for i, (n1, n2) in enumerate(grids):
+        f = flame.Flame(n1, n2, prec="fp32", gamma=0.8, t0=200.0, dt=1e-3)
+        st = inputs.spectrum_ic(n1, n2, inputs.batch_kmax(n1), 1000 + i, K1=f.K1, K2=f.K2)
+        fl.append(f)
+        ss.append(torch.from_numpy(flame.box_to_abi(st)).cuda().to(f.cdtype))
+        ms.append(torch.zeros(1, dtype=torch.float64, device="cuda"))
+        ts.append(torch.full((1,), 200.0, dtype=torch.float64, device="cuda"))
+    hs = [f.h for f in fl]
+    s = torch.cuda.current_stream()
+    flame.flame_step_batch(hs, ss, ms, ts, nsteps=8)
+    torch.cuda.synchronize()
+    n = args.profile_ensemble
+    ms_ = _ev_time(lambda: flame.flame_step_batch(hs, ss, ms, ts, nsteps=n), s)
+    for f in fl:
+        f.sync_status()
+        f.close()
+    classes = sorted({g: grids.count(g) for g in grids}.items())
+    print(json.dumps({"profile_ensemble_steps": n, "ms_per_step": ms_ / n,
+                      "classes": [[list(g), c] for g, c in classes]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -645,8 +674,12 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="run N plain steps for ncu and exit")
     ap.add_argument("--grid", type=int, nargs=2, default=None, help="grid for --profile")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="precision for --profile")
+    ap.add_argument("--profile-ensemble", type=int, default=0,
+                    help="run the 256-flame ensemble for N batch steps (after 8 warm-up steps) and exit")
     args = ap.parse_args()
-    if args.profile:
+    if args.profile_ensemble:
+        run_profile_ensemble(args)
+    elif args.profile:
         run_profile(args)
     elif args.suite:
         run_suite(args)

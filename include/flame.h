@@ -35,8 +35,9 @@
  *
  * ERRORS: no call aborts.  A call that returns a non-OK status has enqueued
  * no work on the stream.  flame_last_error() gives a thread-local message for
- * the last failing call.  Errors detected on the device (non-finite values)
- * set a status word in the handle, read and cleared by flame_sync_status().
+ * the last failing call.  Errors detected on the device (non-finite values;
+ * out-of-range indices in the index-checking build) set status words in the
+ * handle, read and cleared by flame_sync_status().
  *
  * A handle is not thread-safe: calls on one handle must not overlap in time
  * on the host, and two enqueued calls on one handle must be ordered (same
@@ -58,7 +59,9 @@ typedef enum {
     FLAME_ECUDA = 3,         /* a CUDA runtime call failed                  */
     FLAME_EUNSUPPORTED = 4,  /* valid request the library does not handle   */
     FLAME_ETIMEOUT = 5,      /* a bounded device-side wait ran out          */
-    FLAME_ENONFINITE = 6     /* a step produced NaN or Inf                  */
+    FLAME_ENONFINITE = 6,    /* a step produced NaN or Inf                  */
+    FLAME_EBOUNDS = 7        /* index-checking build: an index was outside
+                                its array (the access was skipped)          */
 } flame_status;
 
 typedef enum {
@@ -361,8 +364,25 @@ flame_status flame_step_noalloc(const flame_params *params, void *state, double 
  * stream and synchronises.  EINVAL on a bad argument, ECUDA on a CUDA error. */
 flame_status flame_fma_peak(int prec, double *flops_per_s);
 
-/* Synchronises the handle's device status word and returns it
- * (FLAME_OK, FLAME_ENONFINITE or FLAME_ETIMEOUT); clears it. */
+/* Index-checking build.  A library compiled with -DFLAME_DEBUG_BOUNDS
+ * (paper_0911_2889_gb300/build.py, debug=True: libflame_debug.so) checks
+ * every computed global-memory index of the step passes, the standalone FFT
+ * passes and flame_state_from_field against the extent of its array before
+ * the access; a failing check skips the access and records FLAME_EBOUNDS,
+ * with the check's site, index and extent, in the handle's status words
+ * (reported by flame_sync_status).  It stands in for a memory checker, and
+ * the kernels then run slower.
+ *
+ * flame_debug_bounds_probe runs one such check of (index, extent) on the
+ * stream with no memory access at all: index outside [0, extent) makes the
+ * next flame_sync_status return FLAME_EBOUNDS.  It lets a test see the
+ * reporting path without any out-of-range access.  The normal build has no
+ * checks and returns FLAME_EUNSUPPORTED.  EINVAL on a null handle. */
+flame_status flame_debug_bounds_probe(flame_t h, int index, int extent, void *stream);
+
+/* Synchronises the handle's device status words and returns the status they
+ * hold (FLAME_OK, FLAME_ENONFINITE, FLAME_ETIMEOUT or, in the index-checking
+ * build, FLAME_EBOUNDS); clears them. */
 flame_status flame_sync_status(flame_t h);
 
 /* Static description of a status code. */

@@ -14,7 +14,10 @@
 #include <string>
 #include <vector>
 
+#include <unistd.h>  // getpid (the tuner cache file's temporary name)
+
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "flame.h"
 #include "flame_internal.h"
@@ -66,6 +69,21 @@ constexpr int kGraphCache = 8;
 }  // namespace
 
 void flame::set_last_error(const char *msg) { g_err = msg; }
+
+namespace {
+// NVTX range over a host-side scope: one per ABI call and one per pass
+// enqueued outside a graph, so that a profiler attached to the process
+// (ncu --nvtx, nsys) attributes the kernels to the call and pass that
+// launched them.  Without a tool attached a push/pop costs a few
+// nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+#define FLAME_RANGE(name) NvtxRange flame_nvtx_range_(name)
 
 namespace {
 // the CUDA driver's tensor-map encoder, looked up once (null when unavailable)
@@ -156,6 +174,9 @@ struct flame_ctx {
     std::vector<FlameDesc> batch_key;
     // graphs of the current binding: (steps per launch, executable)
     std::vector<std::pair<int, cudaGraphExec_t>> batch_graphs;
+    // side streams and events of a capture with one branch per size class
+    std::vector<cudaStream_t> batch_streams;
+    std::vector<cudaEvent_t> batch_events;
     // adjoint arena (grown on demand by flame_adjoint) and the graphs of its
     // calls, keyed by every pointer and size of the call
     void *adj = nullptr;
@@ -210,6 +231,8 @@ void free_ctx(flame_ctx *h) {
     cudaFree(h->batch_desc);
     cudaFreeHost(h->batch_host);
     if (h->batch_up) cudaEventDestroy(h->batch_up);
+    for (cudaStream_t q : h->batch_streams) cudaStreamDestroy(q);
+    for (cudaEvent_t ev : h->batch_events) cudaEventDestroy(ev);
     cudaFree(h->tw1);
     cudaFree(h->twm);
     cudaFree(h->uv);
@@ -304,12 +327,26 @@ cudaError_t enqueue_step(flame_ctx *h, const FlameDesc &d, cudaStream_t s) {
     cudaError_t e;
     if (d.rec && h->rec_area && first_stage(d.stage)) return enqueue_step_area(h, d, s);
     if (h->p.prec == FLAME_FP64) {
-        if ((e = Ops<double>::passA(d, s, h->var_a)) != cudaSuccess) return e;
-        if ((e = Ops<double>::passB(d, s, h->var_b)) != cudaSuccess) return e;
+        {
+            FLAME_RANGE("flame pass A");
+            if ((e = Ops<double>::passA(d, s, h->var_a)) != cudaSuccess) return e;
+        }
+        {
+            FLAME_RANGE("flame pass B");
+            if ((e = Ops<double>::passB(d, s, h->var_b)) != cudaSuccess) return e;
+        }
+        FLAME_RANGE("flame pass C");
         return Ops<double>::passC(d, s);
     }
-    if ((e = Ops<float>::passA(d, s, h->var_a, h->map())) != cudaSuccess) return e;
-    if ((e = Ops<float>::passB(d, s, h->var_b, h->gmap())) != cudaSuccess) return e;
+    {
+        FLAME_RANGE("flame pass A");
+        if ((e = Ops<float>::passA(d, s, h->var_a, h->map())) != cudaSuccess) return e;
+    }
+    {
+        FLAME_RANGE("flame pass B");
+        if ((e = Ops<float>::passB(d, s, h->var_b, h->gmap())) != cudaSuccess) return e;
+    }
+    FLAME_RANGE("flame pass C");
     return Ops<float>::passC(d, s);
 }
 
@@ -402,6 +439,86 @@ using TuneKey = std::tuple<int, int, int, int, int, int>;
 std::map<TuneKey, std::tuple<int, int, bool>> g_tune;
 std::mutex g_tune_mu;
 
+// Autotuner cache file (FLAME_TUNE_CACHE=path): a flat JSON object mapping
+// "<GPU name>|<N1>x<N2>|<K1>,<K2>|<precision>" to [pass A variant, pass B
+// variant, fused column passes (0/1)].  A handle created with a key that the
+// file holds takes its choice without timing anything; a new choice is added
+// to the file (rewritten through a temporary file and a rename, so that a
+// reader never sees half a file).  Entries of other keys are kept.
+std::string tune_file_key(const flame_ctx *h) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        return std::string();
+    }
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|%dx%d|%d,%d|%s", prop.name, h->p.n_theta, h->p.n_phi, h->p.K1, h->p.K2,
+             h->p.prec == FLAME_FP64 ? "fp64" : "fp32");
+    for (char *c = buf; *c; ++c)
+        if (*c == '"' || *c == '\\') *c = '_';  // keep the key a plain JSON string
+    return buf;
+}
+
+// Parses the cache file into key -> (a, b, fuse); a malformed file reads as
+// empty (it is then rewritten with the entries this process adds).
+std::map<std::string, std::tuple<int, int, int>> read_tune_file(const char *path) {
+    std::map<std::string, std::tuple<int, int, int>> out;
+    FILE *f = fopen(path, "rb");
+    if (!f) return out;
+    std::string s;
+    char chunk[4096];
+    size_t n;
+    while ((n = fread(chunk, 1, sizeof chunk, f)) > 0) s.append(chunk, n);
+    fclose(f);
+    size_t i = 0;
+    auto skip = [&]() {
+        while (i < s.size() && (s[i] == ' ' || s[i] == '\n' || s[i] == '\r' || s[i] == '\t')) ++i;
+    };
+    skip();
+    if (i >= s.size() || s[i] != '{') return {};
+    ++i;
+    while (true) {
+        skip();
+        if (i < s.size() && s[i] == '}') break;
+        if (i >= s.size() || s[i] != '"') return {};
+        const size_t e = s.find('"', i + 1);
+        if (e == std::string::npos) return {};
+        const std::string key = s.substr(i + 1, e - i - 1);
+        i = e + 1;
+        skip();
+        if (i >= s.size() || s[i] != ':') return {};
+        ++i;
+        skip();
+        int a = 0, b = 0, fu = 0, used = 0;
+        if (sscanf(s.c_str() + i, "[ %d , %d , %d ]%n", &a, &b, &fu, &used) != 3 || used == 0) return {};
+        i += (size_t)used;
+        out[key] = std::make_tuple(a, b, fu);
+        skip();
+        if (i < s.size() && s[i] == ',') {
+            ++i;
+            continue;
+        }
+        skip();
+        if (i < s.size() && s[i] == '}') break;
+        return {};
+    }
+    return out;
+}
+
+void write_tune_file(const char *path, const std::map<std::string, std::tuple<int, int, int>> &m) {
+    const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return;  // the cache is optional
+    fputs("{\n", f);
+    size_t k = 0;
+    for (const auto &kv : m)
+        fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), std::get<0>(kv.second), std::get<1>(kv.second),
+                std::get<2>(kv.second), ++k < m.size() ? "," : "");
+    fputs("}\n", f);
+    const bool ok = fclose(f) == 0;
+    if (!ok || rename(tmp.c_str(), path) != 0) remove(tmp.c_str());
+}
+
 // Fusion of pass C with the next pass A needs the FP32 compile-time column
 // kernels and the uv tensor map; FLAME_FUSE=0 disables it.
 bool fuse_allowed(const flame_ctx *h) {
@@ -439,6 +556,23 @@ flame_status autotune(flame_ctx *h) {
             h->var_a = std::get<0>(it->second);
             h->var_b = std::get<1>(it->second);
             h->fuse = std::get<2>(it->second) && fuse_allowed(h);
+            return FLAME_OK;
+        }
+    }
+    const char *cache_path = getenv("FLAME_TUNE_CACHE");
+    const std::string fkey = cache_path && *cache_path ? tune_file_key(h) : std::string();
+    if (!fkey.empty()) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        const auto m = read_tune_file(cache_path);
+        auto it = m.find(fkey);
+        if (it != m.end()) {
+            h->var_a = std::get<0>(it->second);
+            h->var_b = std::get<1>(it->second);
+            h->fuse = std::get<2>(it->second) != 0 && fuse_allowed(h);
+            // a variant the handle cannot run (no tensor map) falls back to the default shape
+            if (h->var_a == flame::kVariantTma && !h->has_uv_map) h->var_a = flame::kVariantDefault;
+            if (h->var_b == flame::kVariantTmaB && !h->has_gk_map) h->var_b = flame::kVariantDefault;
+            g_tune[key] = std::make_tuple(h->var_a, h->var_b, h->fuse);
             return FLAME_OK;
         }
     }
@@ -544,6 +678,11 @@ flame_status autotune(flame_ctx *h) {
     if (e != cudaSuccess) return fail(FLAME_ECUDA, "autotune: %s", cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = std::make_tuple(h->var_a, h->var_b, h->fuse);
+    if (!fkey.empty()) {
+        auto m = read_tune_file(cache_path);
+        m[fkey] = std::make_tuple(h->var_a, h->var_b, h->fuse ? 1 : 0);
+        write_tune_file(cache_path, m);
+    }
     return FLAME_OK;
 }
 
@@ -626,6 +765,7 @@ const char *flame_status_str(flame_status s) {
     case FLAME_EUNSUPPORTED: return "unsupported";
     case FLAME_ETIMEOUT: return "device wait timed out";
     case FLAME_ENONFINITE: return "non-finite value";
+    case FLAME_EBOUNDS: return "index out of bounds (index-checking build)";
     }
     return "unknown status";
 }
@@ -633,6 +773,7 @@ const char *flame_status_str(flame_status s) {
 const char *flame_last_error(void) { return g_err.c_str(); }
 
 flame_status flame_create(const flame_params *params, flame_t *out) {
+    FLAME_RANGE("flame_create");
     if (!params || !out) return fail(FLAME_EINVAL, "flame_create: null pointer");
     if (inject("param")) return fail(FLAME_EINVAL, "flame_create: injected parameter fault");
     flame_params p = *params;
@@ -695,7 +836,7 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
               dev_alloc(&h->uv, n1 * ldk * 2 * h->csz) && dev_alloc(&h->gk, n1 * ((ldk + 1) & ~(size_t)1) * h->csz) &&
               dev_alloc(&h->spec, n1 * m1 * h->csz) && dev_alloc(&h->aw, n1 * ldk * 2 * h->csz) &&
               dev_alloc((void **)&h->rowsum, n1 * sizeof(double)) && dev_alloc((void **)&h->dscal, 16 * sizeof(double)) &&
-              dev_alloc((void **)&h->status, sizeof(int));
+              dev_alloc((void **)&h->status, flame::kStatusWords * sizeof(int));
     if (!ok) {
         cudaGetLastError();
         free_ctx(h);
@@ -709,7 +850,7 @@ flame_status flame_create(const flame_params *params, flame_t *out) {
     }
     flame_status st = p.prec == FLAME_FP64 ? alloc_tables<double>(h) : alloc_tables<float>(h);
     if (st == FLAME_OK) {
-        e = cudaMemsetAsync(h->status, 0, sizeof(int), h->cap);
+        e = cudaMemsetAsync(h->status, 0, flame::kStatusWords * sizeof(int), h->cap);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->dscal, 0, 16 * sizeof(double), h->cap);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap);
         if (e != cudaSuccess) st = fail(FLAME_ECUDA, "flame_create: %s", cudaGetErrorString(e));
@@ -761,6 +902,7 @@ flame_status flame_get_params(flame_t h, flame_params *out) {
 size_t flame_state_len(flame_t h) { return h ? (size_t)(2 * h->p.K1 + 1) * (size_t)(h->p.K2 + 1) : 0; }
 
 flame_status flame_fft_r2c(flame_t h, const void *real_in, void *spec_out, void *stream) {
+    FLAME_RANGE("flame_fft_r2c");
     if (!h || !real_in || !spec_out) return fail(FLAME_EINVAL, "flame_fft_r2c: null pointer");
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_fft_r2c: injected launch fault");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -768,20 +910,21 @@ flame_status flame_fft_r2c(flame_t h, const void *real_in, void *spec_out, void 
     if (h->p.prec == FLAME_FP64) {
         using C = double2;
         CUDA_TRY(Ops<double>::rows_r2c(static_cast<const double *>(real_in), static_cast<C *>(spec_out),
-                                       h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+                                       h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s, h->status));
         CUDA_TRY(Ops<double>::cols(static_cast<C *>(spec_out), static_cast<C *>(spec_out), h->logn1, M + 1,
-                                   M + 1, -1, static_cast<const C *>(h->tw1), s));
+                                   M + 1, -1, static_cast<const C *>(h->tw1), s, h->status));
     } else {
         using C = float2;
         CUDA_TRY(Ops<float>::rows_r2c(static_cast<const float *>(real_in), static_cast<C *>(spec_out),
-                                      h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+                                      h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s, h->status));
         CUDA_TRY(Ops<float>::cols(static_cast<C *>(spec_out), static_cast<C *>(spec_out), h->logn1, M + 1,
-                                  M + 1, -1, static_cast<const C *>(h->tw1), s));
+                                  M + 1, -1, static_cast<const C *>(h->tw1), s, h->status));
     }
     return FLAME_OK;
 }
 
 flame_status flame_state_from_field(flame_t h, const void *field, void *state, double *mean_mode, void *stream) {
+    FLAME_RANGE("flame_state_from_field");
     if (!h || !field || !state || !mean_mode) return fail(FLAME_EINVAL, "flame_state_from_field: null pointer");
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_state_from_field: injected launch fault");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -790,21 +933,22 @@ flame_status flame_state_from_field(flame_t h, const void *field, void *state, d
         using C = double2;
         C *spec = static_cast<C *>(h->spec);
         CUDA_TRY(Ops<double>::rows_r2c(static_cast<const double *>(field), spec, n1, h->logm,
-                                       static_cast<const C *>(h->twm), s));
-        CUDA_TRY(Ops<double>::cols(spec, spec, h->logn1, M + 1, M + 1, -1, static_cast<const C *>(h->tw1), s));
-        CUDA_TRY(Ops<double>::box_from_spec(spec, static_cast<C *>(state), mean_mode, n1, n2, h->p.K1, h->p.K2, s));
+                                       static_cast<const C *>(h->twm), s, h->status));
+        CUDA_TRY(Ops<double>::cols(spec, spec, h->logn1, M + 1, M + 1, -1, static_cast<const C *>(h->tw1), s, h->status));
+        CUDA_TRY(Ops<double>::box_from_spec(spec, static_cast<C *>(state), mean_mode, n1, n2, h->p.K1, h->p.K2, s, h->status));
     } else {
         using C = float2;
         C *spec = static_cast<C *>(h->spec);
         CUDA_TRY(Ops<float>::rows_r2c(static_cast<const float *>(field), spec, n1, h->logm,
-                                      static_cast<const C *>(h->twm), s));
-        CUDA_TRY(Ops<float>::cols(spec, spec, h->logn1, M + 1, M + 1, -1, static_cast<const C *>(h->tw1), s));
-        CUDA_TRY(Ops<float>::box_from_spec(spec, static_cast<C *>(state), mean_mode, n1, n2, h->p.K1, h->p.K2, s));
+                                      static_cast<const C *>(h->twm), s, h->status));
+        CUDA_TRY(Ops<float>::cols(spec, spec, h->logn1, M + 1, M + 1, -1, static_cast<const C *>(h->tw1), s, h->status));
+        CUDA_TRY(Ops<float>::box_from_spec(spec, static_cast<C *>(state), mean_mode, n1, n2, h->p.K1, h->p.K2, s, h->status));
     }
     return FLAME_OK;
 }
 
 flame_status flame_fft_c2r(flame_t h, const void *spec_in, void *real_out, void *stream) {
+    FLAME_RANGE("flame_fft_c2r");
     if (!h || !spec_in || !real_out) return fail(FLAME_EINVAL, "flame_fft_c2r: null pointer");
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_fft_c2r: injected launch fault");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -812,20 +956,21 @@ flame_status flame_fft_c2r(flame_t h, const void *spec_in, void *real_out, void 
     if (h->p.prec == FLAME_FP64) {
         using C = double2;
         CUDA_TRY(Ops<double>::cols(static_cast<const C *>(spec_in), static_cast<C *>(h->spec), h->logn1, M + 1,
-                                   M + 1, 1, static_cast<const C *>(h->tw1), s));
+                                   M + 1, 1, static_cast<const C *>(h->tw1), s, h->status));
         CUDA_TRY(Ops<double>::rows_c2r(static_cast<const C *>(h->spec), static_cast<double *>(real_out),
-                                       h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+                                       h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s, h->status));
     } else {
         using C = float2;
         CUDA_TRY(Ops<float>::cols(static_cast<const C *>(spec_in), static_cast<C *>(h->spec), h->logn1, M + 1,
-                                  M + 1, 1, static_cast<const C *>(h->tw1), s));
+                                  M + 1, 1, static_cast<const C *>(h->tw1), s, h->status));
         CUDA_TRY(Ops<float>::rows_c2r(static_cast<const C *>(h->spec), static_cast<float *>(real_out),
-                                      h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s));
+                                      h->p.n_theta, h->logm, static_cast<const C *>(h->twm), s, h->status));
     }
     return FLAME_OK;
 }
 
 flame_status flame_step_heun(flame_t h, void *state, double *mean_mode, double *t, int nsteps, void *stream) {
+    FLAME_RANGE("flame_step_heun");
     if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step_heun: null pointer");
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step_heun: nsteps=%d < 0", nsteps);
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_heun: injected launch fault");
@@ -833,6 +978,7 @@ flame_status flame_step_heun(flame_t h, void *state, double *mean_mode, double *
 }
 
 flame_status flame_step_if(flame_t h, void *state, double *mean_mode, double *t, int nsteps, void *stream) {
+    FLAME_RANGE("flame_step_if");
     if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step_if: null pointer");
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step_if: nsteps=%d < 0", nsteps);
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_if: injected launch fault");
@@ -840,6 +986,7 @@ flame_status flame_step_if(flame_t h, void *state, double *mean_mode, double *t,
 }
 
 flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, int nsteps, void *stream) {
+    FLAME_RANGE("flame_step");
     if (!h || !state || !mean_mode || !t) return fail(FLAME_EINVAL, "flame_step: null pointer");
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step: nsteps=%d < 0", nsteps);
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step: injected launch fault");
@@ -848,6 +995,7 @@ flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t, in
 
 flame_status flame_step_host(flame_t h, void *host_state, double *host_mean, double *host_t, int nsteps,
                              void *stream) {
+    FLAME_RANGE("flame_step_host");
     if (!h || !host_state || !host_mean || !host_t) return fail(FLAME_EINVAL, "flame_step_host: null pointer");
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_step_host: nsteps=%d < 0", nsteps);
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_host: injected launch fault");
@@ -961,6 +1109,8 @@ flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode
     if (pass < 0 || pass > 3) return fail(FLAME_EINVAL, "flame_step_pass: pass=%d not in 0..3", pass);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const FlameDesc d = make_desc(h, state, mean_mode, t);
+    static const char *const names[4] = {"flame pass A", "flame pass B", "flame pass C", "flame pass CA"};
+    FLAME_RANGE(names[pass]);
     if (pass == 3) {
         if (!h->fuse) return fail(FLAME_EUNSUPPORTED, "flame_step_pass: no fused column pass for this handle");
         CUDA_TRY(Ops<float>::passCA(d, s, h->map()));
@@ -977,6 +1127,7 @@ flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode
 
 flame_status flame_step_batch(const flame_t *hs, void *const *states, double *const *mean_modes,
                               double *const *ts, int nflames, int nsteps, void *stream) {
+    FLAME_RANGE("flame_step_batch");
     if (!hs || !states || !mean_modes || !ts) return fail(FLAME_EINVAL, "flame_step_batch: null pointer");
     if (nflames < 0 || nsteps < 0) return fail(FLAME_EINVAL, "flame_step_batch: negative count");
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_step_batch: injected launch fault");
@@ -1082,37 +1233,78 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
     }
     const FlameDesc *dev = static_cast<const FlameDesc *>(h0->batch_desc);
     const CUtensorMap *dmaps = reinterpret_cast<const CUtensorMap *>(static_cast<char *>(h0->batch_desc) + mofs);
-    // one step of every flame: per pass, one grouped launch per size class
+    // one pass of one size class: a grouped launch over the class's flames
+    auto enqueue_pass = [&](size_t ci, int pass, cudaStream_t q) -> cudaError_t {
+        const auto &rg = ranges[ci];
+        const StepArgs &a = flat[rg.first].a;
+        const FlameDesc *d = dev + rg.first;
+        const int nf = (int)rg.second;
+        const flame_ctx *hc = class_handle[ci];
+        const CUtensorMap *um = class_maps[ci] ? dmaps + rg.first : nullptr;
+        const CUtensorMap *gm = class_maps[ci] ? dmaps + flat.size() + rg.first : nullptr;
+        const int va = force_a >= 0 ? force_a : hc->var_a, vb = force_b >= 0 ? force_b : hc->var_b;
+        if (h0->p.prec == FLAME_FP64)
+            return pass == 0 ? Ops<double>::passA_batch(d, nf, a, q, va)
+                 : pass == 1 ? Ops<double>::passB_batch(d, nf, a, q, vb)
+                             : Ops<double>::passC_batch(d, nf, a, q);
+        return pass == 0 ? Ops<float>::passA_batch(d, nf, a, q, va, um)
+             : pass == 1 ? Ops<float>::passB_batch(d, nf, a, q, vb, gm)
+                         : Ops<float>::passC_batch(d, nf, a, q);
+    };
+    // n steps of every flame.  In one stream: per step and pass, one grouped
+    // launch per size class.  With FLAME_BATCH_STREAMS=1 the capture forks
+    // one branch per size class (its own stream, joined at the end), so that
+    // the classes' passes are independent nodes of the graph and a
+    // compute-bound pass of one class may run beside a memory-bound pass of
+    // another.
+    // FLAME_BATCH_VARIANTS=a,b: the grouped launches use these pass A and B
+    // variants (in flame_tuning's numbering) instead of the variants the
+    // autotuner chose for a single flame of the class's grid
+    int force_a = -1, force_b = -1;
+    if (const char *bv = getenv("FLAME_BATCH_VARIANTS")) {
+        int fa = 0, fb = 0;
+        if (sscanf(bv, "%d,%d", &fa, &fb) == 2) {
+            force_a = fa;
+            force_b = fb;
+        }
+    }
+    const char *bs = getenv("FLAME_BATCH_STREAMS");
+    const bool branches = bs && strcmp(bs, "1") == 0 && ranges.size() > 1;
     auto enqueue_steps = [&](int n, cudaStream_t q) -> cudaError_t {
         cudaError_t le = cudaSuccess;
-        for (int st = 0; st < n && le == cudaSuccess; ++st) {
-            for (int pass = 0; pass < 3 && le == cudaSuccess; ++pass) {
-                for (auto &rg : ranges) {
-                    const StepArgs &a = flat[rg.first].a;
-                    const FlameDesc *d = dev + rg.first;
-                    const int nf = (int)rg.second;
-                    const size_t ci = &rg - &ranges[0];
-                    const flame_ctx *hc = class_handle[ci];
-                    const CUtensorMap *um = class_maps[ci] ? dmaps + rg.first : nullptr;
-                    const CUtensorMap *gm = class_maps[ci] ? dmaps + flat.size() + rg.first : nullptr;
-                    if (h0->p.prec == FLAME_FP64)
-                        le = pass == 0 ? Ops<double>::passA_batch(d, nf, a, q, hc->var_a)
-                           : pass == 1 ? Ops<double>::passB_batch(d, nf, a, q, hc->var_b)
-                                       : Ops<double>::passC_batch(d, nf, a, q);
-                    else
-                        le = pass == 0 ? Ops<float>::passA_batch(d, nf, a, q, hc->var_a, um)
-                           : pass == 1 ? Ops<float>::passB_batch(d, nf, a, q, hc->var_b, gm)
-                                       : Ops<float>::passC_batch(d, nf, a, q);
-                    if (le != cudaSuccess) break;
-                }
-            }
+        if (!branches) {
+            for (int st = 0; st < n && le == cudaSuccess; ++st)
+                for (int pass = 0; pass < 3 && le == cudaSuccess; ++pass)
+                    for (size_t ci = 0; ci < ranges.size() && le == cudaSuccess; ++ci) le = enqueue_pass(ci, pass, q);
+            return le;
+        }
+        const size_t nc = ranges.size();
+        while (h0->batch_streams.size() < nc) {
+            cudaStream_t ns = nullptr;
+            if ((le = cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking)) != cudaSuccess) return le;
+            h0->batch_streams.push_back(ns);
+        }
+        while (h0->batch_events.size() < nc + 1) {
+            cudaEvent_t ev = nullptr;
+            if ((le = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return le;
+            h0->batch_events.push_back(ev);
+        }
+        if ((le = cudaEventRecord(h0->batch_events[nc], q)) != cudaSuccess) return le;  // fork
+        for (size_t ci = 0; ci < nc && le == cudaSuccess; ++ci) {
+            cudaStream_t b = h0->batch_streams[ci];
+            le = cudaStreamWaitEvent(b, h0->batch_events[nc], 0);
+            for (int st = 0; st < n && le == cudaSuccess; ++st)
+                for (int pass = 0; pass < 3 && le == cudaSuccess; ++pass) le = enqueue_pass(ci, pass, b);
+            if (le == cudaSuccess) le = cudaEventRecord(h0->batch_events[ci], b);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(q, h0->batch_events[ci], 0);  // join
         }
         return le;
     };
     // graphs of kBatchChunk steps (fewer for a short call), replayed
     auto graph_of = [&](int n, cudaGraphExec_t *out) -> flame_status {
+        const int key = n | (branches ? 1 << 30 : 0);  // steps and capture form
         for (auto &g : h0->batch_graphs)
-            if (g.first == n) {
+            if (g.first == key) {
                 *out = g.second;
                 return FLAME_OK;
             }
@@ -1127,7 +1319,7 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
         const cudaError_t ie = cudaGraphInstantiate(out, graph, 0);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) return fail(FLAME_ECUDA, "flame_step_batch instantiate: %s", cudaGetErrorString(ie));
-        h0->batch_graphs.emplace_back(n, *out);
+        h0->batch_graphs.emplace_back(key, *out);
         return FLAME_OK;
     };
     const int chunk = nsteps < kBatchChunk ? nsteps : kBatchChunk;
@@ -1143,6 +1335,7 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
 
 flame_status flame_area(flame_t h, const void *state, const double *mean_mode, const double *t,
                         double *area_out, void *dA_dstate, double *dA_dmean, void *stream) {
+    FLAME_RANGE("flame_area");
     if (!h || !state || !mean_mode || !t || !area_out) return fail(FLAME_EINVAL, "flame_area: null pointer");
     if (inject("launch")) return fail(FLAME_ECUDA, "flame_area: injected launch fault");
     flame::AdjDesc d;
@@ -1169,6 +1362,7 @@ flame_status flame_area(flame_t h, const void *state, const double *mean_mode, c
 flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, const double *t_start, int nsteps,
                            int ckpt_every, const void *lambda_T, const double *lambda0_T, void *grad_state0,
                            double *grad_mean0, double *grad_gamma, void *stream) {
+    FLAME_RANGE("flame_adjoint");
     if (!h || !state0 || !mean0 || !t_start || !lambda_T || !lambda0_T || !grad_state0 || !grad_mean0 || !grad_gamma)
         return fail(FLAME_EINVAL, "flame_adjoint: null pointer");
     if (nsteps < 0) return fail(FLAME_EINVAL, "flame_adjoint: nsteps=%d < 0", nsteps);
@@ -1315,14 +1509,28 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, c
     return FLAME_OK;
 }
 
+flame_status flame_debug_bounds_probe(flame_t h, int index, int extent, void *stream) {
+    if (!h) return fail(FLAME_EINVAL, "flame_debug_bounds_probe: null handle");
+    const cudaError_t e = flame::bounds_probe(h->status, index, extent, static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        return fail(FLAME_EUNSUPPORTED, "flame_debug_bounds_probe: not an index-checking build");
+    }
+    CUDA_TRY(e);
+    return FLAME_OK;
+}
+
 flame_status flame_sync_status(flame_t h) {
     if (!h) return fail(FLAME_EINVAL, "flame_sync_status: null handle");
     CUDA_TRY(cudaDeviceSynchronize());
-    int v = 0;
-    CUDA_TRY(cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemset(h->status, 0, sizeof(int)));
-    if (v & (1 << flame::kStatusTimeout)) return fail(FLAME_ETIMEOUT, "a device-side wait timed out");
-    if (v & (1 << flame::kStatusNonfinite)) return fail(FLAME_ENONFINITE, "a step produced NaN or Inf");
+    int v[flame::kStatusWords] = {0, 0, 0, 0};
+    CUDA_TRY(cudaMemcpy(v, h->status, sizeof v, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(h->status, 0, sizeof v));
+    if (v[0] & (1 << flame::kStatusBounds))
+        return fail(FLAME_EBOUNDS, "index check failed at site %d: index %d not in [0, %d) (the access was skipped)",
+                    v[1], v[2], v[3]);
+    if (v[0] & (1 << flame::kStatusTimeout)) return fail(FLAME_ETIMEOUT, "a device-side wait timed out");
+    if (v[0] & (1 << flame::kStatusNonfinite)) return fail(FLAME_ENONFINITE, "a step produced NaN or Inf");
     return FLAME_OK;
 }
 

@@ -12,6 +12,36 @@ constexpr unsigned kLinearOnly = 1u;
 constexpr unsigned kNonlinearOnly = 2u;
 constexpr int kStatusNonfinite = 0;
 constexpr int kStatusTimeout = 1;
+constexpr int kStatusBounds = 2;
+// The status word is followed by three words that the index-checking build
+// (FLAME_DEBUG_BOUNDS) fills on its first failed check: the check's site,
+// the index and the extent it was checked against.
+constexpr int kStatusWords = 4;
+
+// Sites of the index checks of the FLAME_DEBUG_BOUNDS build (reported by
+// flame_sync_status with the failing index).
+enum BoundsSite : int {
+    kSiteAState = 1,    // pass A: state column entry
+    kSiteAUv = 2,       // pass A: (U, V) store (direct and cluster write-outs)
+    kSiteATma = 3,      // pass A: tensor-store coordinates (column, row pair)
+    kSiteBUv = 4,       // pass B: row-pair (U, V) load
+    kSiteBGk = 5,       // pass B: G store (direct write-out)
+    kSiteBTma = 6,      // pass B: tensor-store coordinates (row pair, column pair)
+    kSiteBArow = 7,     // pass B (area variant): row-pair area sum; state column 0
+    kSiteCGk = 8,       // pass C: column-pair load
+    kSiteCState = 9,    // pass C: state load and store (incl. the k2 = 0 mirror)
+    kSiteCForcing = 10, // pass C: forcing entry
+    kSiteCSave = 11,    // pass C: stage buffer entry
+    kSiteCRec = 12,     // pass C: record entry, area row sums
+    kSiteCAUv = 13,     // fused pass C + A: (U, V) store and tensor-store coordinates
+    kSiteFftIn = 14,    // standalone 2-D FFT passes: input entry
+    kSiteFftOut = 15,   // standalone 2-D FFT passes: output entry
+    kSiteBoxSpec = 16,  // state from a field: spectrum entry and state entry
+    kSiteProbe = 17,    // flame_debug_bounds_probe (a check with no access)
+};
+// One index check of (i, n) with no memory access, recorded in status
+// (index-checking build); returns cudaErrorNotSupported in the normal build.
+cudaError_t bounds_probe(int *status, int i, int n, cudaStream_t s);
 
 // Time-stepping stage of a pass C launch (the update its epilogue applies,
 // with F = omega Phi + N, N = c ghat + f the non-stiff part, E the exact
@@ -139,13 +169,17 @@ void set_last_error(const char *msg);
 template <class R> struct Ops {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     static cudaError_t init_twiddles(C *tab, int logN, cudaStream_t s);
-    static cudaError_t rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s);
-    static cudaError_t rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s);
+    // (status: the handle's status words, for the index checks of the
+    // FLAME_DEBUG_BOUNDS build; unused otherwise)
+    static cudaError_t rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s,
+                                int *status = nullptr);
+    static cudaError_t rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s,
+                                int *status = nullptr);
     static cudaError_t cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw,
-                            cudaStream_t s);
+                            cudaStream_t s, int *status = nullptr);
     // retained modes of an r2c spectrum -> compact box + FP64 mean
     static cudaError_t box_from_spec(const C *spec, C *state, double *mean, int n1, int n2, int K1, int K2,
-                                     cudaStream_t s);
+                                     cudaStream_t s, int *status = nullptr);
     // One step pass for one flame (desc by value) or for nflames flames of
     // the same grid (descs: device array of nflames entries, shape from a).
     // variant: kVariantDefault, or a tuned alternative (pass A: kVariantDirect

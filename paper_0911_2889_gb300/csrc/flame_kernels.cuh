@@ -26,6 +26,37 @@
 namespace flame {
 
 template <class R> using CplxT = typename VecOf<R>::c;  // float2 / double2
+
+// Index checks of the index-checking build (-DFLAME_DEBUG_BOUNDS).
+// FLAME_IN(status, i, n, site) is true when 0 <= i < n.  Otherwise it sets
+// kStatusBounds in the status word, records the first failure (site, index,
+// extent) in the three words after it, and is false: the caller then skips
+// the access, so a bad index is reported instead of touching memory outside
+// its array.  In the normal build it is the constant true and the index
+// expression is not evaluated.
+#ifdef FLAME_DEBUG_BOUNDS
+static __device__ __noinline__ bool bounds_fail(int *status, int site, long long i, long long n) {
+    if (status) {
+        atomicOr(status, 1 << kStatusBounds);
+        if (atomicCAS(status + 1, 0, site) == 0) {
+            status[2] = (int)i;
+            status[3] = (int)n;
+        }
+    }
+    return false;
+}
+#define FLAME_IN(status, i, n, site)                                                     \
+    ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n) ||          \
+     ::flame::bounds_fail((status), (site), (long long)(i), (long long)(n)))
+#else
+#define FLAME_IN(status, i, n, site) true
+#endif
+// Extents (complex entries) of the step's arrays: the compact box (state,
+// forcing, stage buffer), the (U, V) workspace and the G workspace (column
+// pairs: an even number of columns).
+__host__ __device__ __forceinline__ long long box_len(const StepArgs &a) { return (long long)(2 * a.K1 + 1) * a.ldk; }
+__host__ __device__ __forceinline__ long long uv_len(const StepArgs &a) { return 2LL * a.n1 * a.ldk; }
+__host__ __device__ __forceinline__ long long gk_len(const StepArgs &a) { return (long long)a.n1 * ((a.ldk + 1) & ~1); }
 static_assert(sizeof(float2) == sizeof(VecOf<float>::type) && sizeof(double2) == sizeof(VecOf<double>::type), "C and V sizes");
 
 // s1, s2 in the kernel's precision (the FP32 copies are rounded on the host)
@@ -117,7 +148,7 @@ template <class R> __device__ __forceinline__ CplxT<R> lane1(CV<typename VecOf<R
 // (FP64) goes to *mean.
 template <class R>
 __global__ void k_box_from_spec(const CplxT<R> *__restrict__ spec, CplxT<R> *__restrict__ state, double *mean,
-                                int n1, int n2, int K1, int K2) {
+                                int n1, int n2, int K1, int K2, int *status) {
     using C = CplxT<R>;
     const int ld1 = 2 * K1 + 1, ldm = n2 / 2 + 1;
     const long total = (long)ld1 * (K2 + 1);
@@ -131,10 +162,11 @@ __global__ void k_box_from_spec(const CplxT<R> *__restrict__ spec, CplxT<R> *__r
         } else {
             const bool mirror = k2 == 0 && k1 < 0;
             const int row = mirror ? -k1 : (k1 < 0 ? k1 + n1 : k1);
-            const C s = spec[(size_t)row * ldm + k2];
+            const long long si = (long long)row * ldm + k2;
+            const C s = FLAME_IN(status, si, (long long)n1 * ldm, kSiteBoxSpec) ? spec[si] : C{0, 0};
             v = C{s.x * rinv, (mirror ? -s.y : s.y) * rinv};
         }
-        state[i] = v;
+        if (FLAME_IN(status, i, total, kSiteBoxSpec)) state[i] = v;
     }
 }
 
@@ -176,13 +208,14 @@ template <class R> __global__ void k_twiddles(CplxT<R> *tab, int logN, int LE) {
 // complex FFT of h[m] = x[2m] + i x[2m+1] followed by the real-input
 // post-processing  Y[k] = E[k] + exp(-2 pi i k/N2) O[k],
 // E = (H[k] + conj H[M-k])/2, O = (H[k] - conj H[M-k])/(2i).
-template <class R>
+// LOG > 0: half length 2^LOG fixed at compile time; LOG = 0: any length.
+template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_r2c(const R *__restrict__ in, CplxT<R> *__restrict__ out, int n1,
-                                                  int logm, const CplxT<R> *__restrict__ tw) {
+                                                  int logm, const CplxT<R> *__restrict__ tw, int *status) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int M = 1 << logm, T = M >> 4, ldo = M + 1;
+    const int M = LOG > 0 ? 1 << LOG : 1 << logm, T = M >> 4, ldo = M + 1;
     const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
     const int pair = blockIdx.x * G + g;
     const bool valid = pair < (n1 >> 1);
@@ -193,16 +226,17 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_r2c(const R *__rest
     CV<V> x[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        C a = valid ? __ldg(ra + t + r * T) : C{0, 0};
-        C b = valid ? __ldg(rb + t + r * T) : C{0, 0};
+        const bool in = valid && FLAME_IN(status, (long long)(2 * pair + 1) * M + t + r * T, (long long)n1 * M, kSiteFftIn);
+        C a = in ? __ldg(ra + t + r * T) : C{0, 0};
+        C b = in ? __ldg(rb + t + r * T) : C{0, 0};
         x[r] = pack2<R>(a, b);
     }
-    line_fft<-1>(x, logm, t, sm, tw, CtaBarrier{});
+    fft_line<-1, LOG>(x, logm, t, sm, tw);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 16; ++r) sm.st(t + r * T, x[r]);
     __syncthreads();
-    const C *P = tw + tw_real_offset(logm);
+    const C *P = tw + tw_real_offset(LOG > 0 ? LOG : logm);
     C *oa = out + (size_t)(2 * pair) * ldo, *ob = oa + ldo;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -214,12 +248,12 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_r2c(const R *__rest
         CV<V> O{vmul(vadd(h.im, hc.im), vbc(hf)), vmul(vsub(hc.re, h.re), vbc(hf))};
         C w = __ldg(P + k);  // exp(+2 pi i k/N2); forward uses the conjugate
         CV<V> Y = cadd(E, cmul_s(O, w.x, -w.y));
-        if (valid) {
+        if (valid && FLAME_IN(status, (long long)(2 * pair + 1) * ldo + k, (long long)n1 * ldo, kSiteFftOut)) {
             oa[k] = lane0<R>(Y);
             ob[k] = lane1<R>(Y);
         }
     }
-    if (valid && t == 0) {
+    if (valid && t == 0 && FLAME_IN(status, (long long)(2 * pair + 1) * ldo + M, (long long)n1 * ldo, kSiteFftOut)) {
         CV<V> h0 = x[0];
         oa[M] = C{h0.re.x - h0.im.x, 0};
         ob[M] = C{h0.re.y - h0.im.y, 0};
@@ -229,28 +263,30 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_r2c(const R *__rest
 // Row pass of c2r: pre-processing H[k] = (Y[k] + conj Y[M-k]) +
 // i exp(+2 pi i k/N2) (Y[k] - conj Y[M-k]), half-length inverse FFT, then
 // x[2m] = Re h[m], x[2m+1] = Im h[m].
-template <class R>
+template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_c2r(const CplxT<R> *__restrict__ in, R *__restrict__ out, int n1,
-                                                  int logm, const CplxT<R> *__restrict__ tw) {
+                                                  int logm, const CplxT<R> *__restrict__ tw, int *status) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int M = 1 << logm, T = M >> 4, ldi = M + 1;
+    const int M = LOG > 0 ? 1 << LOG : 1 << logm, T = M >> 4, ldi = M + 1;
     const int g = threadIdx.x / T, t = threadIdx.x % T, G = blockDim.x / T;
     const int pair = blockIdx.x * G + g;
     const bool valid = pair < (n1 >> 1);
     V *base = reinterpret_cast<V *>(smraw) + (size_t)g * 2 * plane_len(M);
     auto sm = make_planes(base, M);
     const C *ia = in + (size_t)(2 * pair) * ldi, *ib = ia + ldi;
-    const C *P = tw + tw_real_offset(logm);
+    const C *P = tw + tw_real_offset(LOG > 0 ? LOG : logm);
     CV<V> x[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int k = t + r * T;
-        C a = valid ? __ldg(ia + k) : C{0, 0};
-        C b = valid ? __ldg(ib + k) : C{0, 0};
-        C ac = valid ? __ldg(ia + M - k) : C{0, 0};
-        C bc = valid ? __ldg(ib + M - k) : C{0, 0};
+        const bool in = valid && FLAME_IN(status, (long long)(2 * pair + 1) * ldi + M - k, (long long)n1 * ldi, kSiteFftIn) &&
+                        FLAME_IN(status, (long long)(2 * pair + 1) * ldi + k, (long long)n1 * ldi, kSiteFftIn);
+        C a = in ? __ldg(ia + k) : C{0, 0};
+        C b = in ? __ldg(ib + k) : C{0, 0};
+        C ac = in ? __ldg(ia + M - k) : C{0, 0};
+        C bc = in ? __ldg(ib + M - k) : C{0, 0};
         CV<V> y = pack2<R>(a, b), yc = pack2<R>(ac, bc);
         CV<V> S{vadd(y.re, yc.re), vsub(y.im, yc.im)};
         CV<V> D{vsub(y.re, yc.re), vadd(y.im, yc.im)};
@@ -258,11 +294,12 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_c2r(const CplxT<R> 
         CV<V> wD = cmul_s(D, w.x, w.y);
         x[r] = cadd_rot<1>(S, wD);
     }
-    line_fft<1>(x, logm, t, sm, tw, CtaBarrier{});
+    fft_line<1, LOG>(x, logm, t, sm, tw);
     if (valid) {
         C *oa = reinterpret_cast<C *>(out) + (size_t)(2 * pair) * M, *ob = oa + M;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
+            if (!FLAME_IN(status, (long long)(2 * pair + 1) * M + t + r * T, (long long)n1 * M, kSiteFftOut)) continue;
             oa[t + r * T] = lane0<R>(x[r]);
             ob[t + r * T] = lane1<R>(x[r]);
         }
@@ -272,13 +309,13 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_c2r(const CplxT<R> 
 // Column FFT of length n = 2^logn over ncols columns of a row-major array
 // with row stride ld (complex units); columns 2p, 2p+1 form one thread
 // group; in may equal out.
-template <class R, int DIR>
+template <class R, int DIR, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_cols(const CplxT<R> *in, CplxT<R> *out, int logn, int ncols, int ld,
-                                              const CplxT<R> *__restrict__ tw) {
+                                              const CplxT<R> *__restrict__ tw, int *status) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int n = 1 << logn, T = n >> 4;
+    const int n = LOG > 0 ? 1 << LOG : 1 << logn, T = n >> 4;
     const int G = blockDim.x / T, g = threadIdx.x % G, t = threadIdx.x / G;
     const int c0 = 2 * (blockIdx.x * G + g);
     const bool va = c0 < ncols, vb = c0 + 1 < ncols;
@@ -288,16 +325,18 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_cols(const CplxT<R> *in,
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const size_t row = (size_t)(t + r * T) * ld;
-        C a = va ? in[row + c0] : C{0, 0};
-        C b = vb ? in[row + c0 + 1] : C{0, 0};
+        const long long len = (long long)n * ld;
+        C a = va && FLAME_IN(status, row + c0, len, kSiteFftIn) ? in[row + c0] : C{0, 0};
+        C b = vb && FLAME_IN(status, row + c0 + 1, len, kSiteFftIn) ? in[row + c0 + 1] : C{0, 0};
         x[r] = pack2<R>(a, b);
     }
-    line_fft<DIR>(x, logn, t, sm, tw, CtaBarrier{});
+    fft_line<DIR, LOG>(x, logn, t, sm, tw);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const size_t row = (size_t)(t + r * T) * ld;
-        if (va) out[row + c0] = lane0<R>(x[r]);
-        if (vb) out[row + c0 + 1] = lane1<R>(x[r]);
+        const long long len = (long long)n * ld;
+        if (va && FLAME_IN(status, row + c0, len, kSiteFftOut)) out[row + c0] = lane0<R>(x[r]);
+        if (vb && FLAME_IN(status, row + c0 + 1, len, kSiteFftOut)) out[row + c0 + 1] = lane1<R>(x[r]);
     }
 }
 
@@ -501,7 +540,7 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
             const int n = t + r * T;
             const int k1 = (r < E / 4) ? n : n - N1;
             const bool in_box = valid && ((r < E / 4) ? (n <= a.K1) : (k1 >= -a.K1));
-            if (in_box) {
+            if (in_box && FLAME_IN(d.status, (long long)k2 * ld1 + a.K1 + k1, box_len(a), kSiteAState)) {
                 C phi = __ldg(col + k1);
                 if (k1 == 0 && k2 == 0) phi = C{0, 0};
                 const R f = s1 * (R)k1;
@@ -551,7 +590,8 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
                 reinterpret_cast<const float4 *>(reinterpret_cast<V *>(smraw) + (size_t)(c % GG) * 2 * plane_len_e<E>(NN)),
                 c / GG);
             const float4 v = rb[spad(n)];
-            if (kc <= a.K2) *reinterpret_cast<float4 *>(uv + uv_index(n, kc, a.ldk)) = v;
+            if (kc <= a.K2 && FLAME_IN(d.status, uv_index(n, kc, a.ldk) + 1, uv_len(a), kSiteAUv))
+                *reinterpret_cast<float4 *>(uv + uv_index(n, kc, a.ldk)) = v;
         }
         cluster.sync();
     } else if constexpr (TMA && std::is_same<R, float>::value && LOG > 0) {
@@ -579,14 +619,17 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const int n = t + r * T;
-                *reinterpret_cast<float4 *>(uv + uv_index(n, k2, a.ldk)) = park[n];
+                if (FLAME_IN(d.status, uv_index(n, k2, a.ldk) + 1, uv_len(a), kSiteAUv))
+                    *reinterpret_cast<float4 *>(uv + uv_index(n, k2, a.ldk)) = park[n];
             }
         }
         if (aligned && t == 0 && valid) {
             constexpr int BP = uv_box_pairs(1 << LOG);
             if constexpr (GMAP) tensormap_acquire(tm);
 #pragma unroll 1
-            for (int p0 = 0; p0 < (N1 >> 1); p0 += BP) tma_store_3d(tm, park + 2 * p0, 0, k2, p0);
+            for (int p0 = 0; p0 < (N1 >> 1); p0 += BP)
+                if (FLAME_IN(d.status, k2, a.ldk, kSiteATma) && FLAME_IN(d.status, p0, a.n1 >> 1, kSiteATma))
+                    tma_store_3d(tm, park + 2 * p0, 0, k2, p0);
             bulk_commit_and_wait_read();
         }
     } else if (valid) {
@@ -596,7 +639,8 @@ __device__ __forceinline__ void passA_body(const FlameDesc &d, int tile, int nti
             C U = lane0<R>(x[r]);
             C Vb = lane1<R>(x[r]);
             C Vv{-s2k2 * Vb.y, s2k2 * Vb.x};  // i s2 k2 (synthesis of Phi)
-            st_uv<R>(uv + uv_index(n, k2, a.ldk), U, Vv);
+            if (FLAME_IN(d.status, uv_index(n, k2, a.ldk) + 1, uv_len(a), kSiteAUv))
+                st_uv<R>(uv + uv_index(n, k2, a.ldk), U, Vv);
         }
     }
 }
@@ -754,7 +798,8 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
             const int k = t + r * T;
             UV<R> e1{C{0, 0}, C{0, 0}};
             e0[r] = e1;
-            if (valid && k <= a.K2) {
+            if (valid && k <= a.K2 &&
+                FLAME_IN(d.status, uv_index(2 * pair, 0, a.ldk) + 4 * (long long)k + 3, uv_len(a), kSiteBUv)) {
                 e0[r] = ld_uv<R>(src + 4 * (size_t)k);
                 e1 = ld_uv<R>(src + 4 * (size_t)k + 2);
             }
@@ -807,6 +852,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
         const C *t1r = static_cast<const C *>(d.tw1) + tw_real_offset(a.logn1);  // exp(2 pi i k / 2 N1), k < N1
         R p0[2] = {0, 0};
         for (int k1 = 1 + t; k1 <= a.K1; k1 += T) {
+            if (!FLAME_IN(d.status, a.K1 + k1, box_len(a), kSiteBArow)) continue;
             const C ph = st0[k1];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -874,7 +920,7 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
         area_terms(sq1, true);
         // the row pair's area sum (FP64 across the group's threads)
         const double tot = group_sum<double>((double)apart, T, reinterpret_cast<double *>(phi_park));
-        if (t == 0 && valid) d.arow[pair] = tot;
+        if (t == 0 && valid && FLAME_IN(d.status, pair, a.n1 >> 1, kSiteBArow)) d.arow[pair] = tot;
     }
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -909,8 +955,10 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
             CV<V> Y = cadd(Ev, cmul_s(Ov, w.x, -w.y));
             C *dst = staged ? h_first + 4 * (k >> 1) + (k & 1)
                             : gk + gk_index(2 * pair, k, a.n1);  // row 2p+1 two slots further
-            dst[0] = lane0<R>(Y);
-            dst[2] = lane1<R>(Y);
+            if (staged || FLAME_IN(d.status, gk_index(2 * pair, k, a.n1) + 2, gk_len(a), kSiteBGk)) {
+                dst[0] = lane0<R>(Y);
+                dst[2] = lane1<R>(Y);
+            }
         }
     });
     if constexpr (kTma) {
@@ -921,7 +969,9 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
                 const int nq = (a.ldk + 1) >> 1, BQ = gk_box_pairs(a.ldk);
                 if constexpr (GMAP) tensormap_acquire(tm);
 #pragma unroll 1
-                for (int q0 = 0; q0 < nq; q0 += BQ) tma_store_3d(tm, h_first + 4 * q0, 0, pair, q0);
+                for (int q0 = 0; q0 < nq; q0 += BQ)
+                    if (FLAME_IN(d.status, pair, a.n1 >> 1, kSiteBTma) && FLAME_IN(d.status, q0, (gk_len(a) / a.n1) >> 1, kSiteBTma))
+                        tma_store_3d(tm, h_first + 4 * q0, 0, pair, q0);
                 bulk_commit_and_wait_read();
             }
         }
@@ -1001,13 +1051,14 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     for (int r = 0; r < E; ++r) {
         const int n = t + r * T;
         C p, q;
+        const bool in = va && FLAME_IN(d.status, gk_index(0, c0, N1) + 2 * (long long)n + 1, gk_len(a), kSiteCGk);
         if constexpr (std::is_same<R, float>::value) {
-            const float4 pq = va ? __ldg(reinterpret_cast<const float4 *>(gp) + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 pq = in ? __ldg(reinterpret_cast<const float4 *>(gp) + n) : make_float4(0.f, 0.f, 0.f, 0.f);
             p = C{pq.x, pq.y};
             q = vb ? C{pq.z, pq.w} : C{0, 0};
         } else {
-            p = va ? __ldg(gp + 2 * n) : C{0, 0};
-            q = vb ? __ldg(gp + 2 * n + 1) : C{0, 0};
+            p = in ? __ldg(gp + 2 * n) : C{0, 0};
+            q = (in && vb) ? __ldg(gp + 2 * n + 1) : C{0, 0};
         }
         if (c0 == 0) colsum += (double)p.x;
         x[r] = pack2<R>(p, q);
@@ -1045,8 +1096,9 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         const int n = t + r * T;
         const int k1 = (r < QE) ? n : n - N1;
         const bool in_box = (r < QE) ? (n <= a.K1) : (k1 >= -a.K1);
-        phi[i][0] = (in_box && va) ? sa[k1] : C{0, 0};
-        phi[i][1] = (in_box && vb) ? sb[k1] : C{0, 0};
+        [[maybe_unused]] const long long ia = (long long)c0 * ld1 + a.K1 + k1;
+        phi[i][0] = (in_box && va && FLAME_IN(d.status, ia, box_len(a), kSiteCState)) ? sa[k1] : C{0, 0};
+        phi[i][1] = (in_box && vb && FLAME_IN(d.status, ia + ld1, box_len(a), kSiteCState)) ? sb[k1] : C{0, 0};
     }
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
     const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
@@ -1070,6 +1122,8 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             if (!ok) continue;
             if (k2 == 0 && k1 < 0) continue;  // written as the mirror of +k1
             C *col = side == 0 ? sa : sb;
+            [[maybe_unused]] const long long bi = (long long)k2 * ld1 + a.K1 + k1;  // box index of (k1, k2)
+            if (!FLAME_IN(d.status, bi, box_len(a), kSiteCState)) continue;
             if (k1 == 0 && k2 == 0) {
                 col[0] = C{0, 0};
                 continue;
@@ -1081,13 +1135,14 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             const R cn = nl ? rcs : (R)0;
             // the non-stiff part: c ghat (+ the forcing f_k)
             C nt{rmul(cn, gh.x), rmul(cn, gh.y)};
-            if (fa) {
+            if (fa && FLAME_IN(d.status, bi, box_len(a), kSiteCForcing)) {
                 const C f = fa[(side ? ld1 : 0) + k1];
                 nt = C{radd(nt.x, f.x), radd(nt.y, f.y)};
             }
             // dt F = dt (omega Phi + nt)
             const C df{rmul(rdt, rfma(om, ph.x, nt.x)), rmul(rdt, rfma(om, ph.y, nt.y))};
             C nw;
+            if (stage != kStageEuler && !FLAME_IN(d.status, bi, box_len(a), kSiteCSave)) continue;
             if (stage == kStageEuler || stage == kStageHeun1) {
                 nw = C{radd(ph.x, df.x), radd(ph.y, df.y)};
                 if (stage == kStageHeun1) va_save[(side ? ld1 : 0) + k1] = ph;
@@ -1114,7 +1169,7 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             bad |= !(isfinite(nw.x) && isfinite(nw.y));
             col[k1] = nw;
             nphi[i][side] = nw;
-            if (k2 == 0) col[-k1] = C{nw.x, -nw.y};
+            if (k2 == 0 && FLAME_IN(d.status, a.K1 - k1, box_len(a), kSiteCState)) col[-k1] = C{nw.x, -nw.y};
         }
     }
     if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
@@ -1126,7 +1181,8 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         if (d.rec_area == 1) {
             __shared__ double asum[32];
             double v = 0.0;
-            for (int i = threadIdx.x; i < (a.n1 >> 1); i += blockDim.x) v += d.arow[i];
+            for (int i = threadIdx.x; i < (a.n1 >> 1); i += blockDim.x)
+                if (FLAME_IN(d.status, i, a.n1 >> 1, kSiteCRec)) v += d.arow[i];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if ((threadIdx.x & 31) == 0) asum[threadIdx.x >> 5] = v;
             __syncthreads();
@@ -1149,8 +1205,9 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         if (GEN && d.forcing0 != 0.0) inc += a.dt * d.forcing0;
         const double m = *d.mean;
         long n = __double2ll_rn((d.coef[0] - a.t0) / a.dt);
-        if (GEN && d.rec && stage != kStageHeun2 && stage != kStageIF2) {
-            double *e = d.rec + 4 * (size_t)(((n % d.rec_cap) + d.rec_cap) % d.rec_cap);
+        const long ri = ((n % max(d.rec_cap, 1)) + d.rec_cap) % max(d.rec_cap, 1);
+        if (GEN && d.rec && stage != kStageHeun2 && stage != kStageIF2 && FLAME_IN(d.status, ri, d.rec_cap, kSiteCRec)) {
+            double *e = d.rec + 4 * (size_t)ri;
             e[0] = d.coef[0];
             e[1] = m;
             e[2] = (nl ? d.coef[1] * mg : 0.0) + (GEN ? d.forcing0 : 0.0);
@@ -1178,7 +1235,7 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
 #pragma unroll
             for (int i = 4; i < 8; ++i) {
                 const int k1 = t + (i + 8) * T - N1;
-                if (k1 >= -a.K1) nphi[i][0] = sa[k1];
+                if (k1 >= -a.K1 && FLAME_IN(d.status, a.K1 + k1, box_len(a), kSiteCState)) nphi[i][0] = sa[k1];
             }
         }
         const C *__restrict__ tw1a = static_cast<const C *>(d.tw1);
@@ -1218,13 +1275,16 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int n = t + r * T;
-                    *reinterpret_cast<float4 *>(static_cast<C *>(d.uv) + uv_index(n, k2, a.ldk)) = park[n];
+                    if (FLAME_IN(d.status, uv_index(n, k2, a.ldk) + 1, uv_len(a), kSiteCAUv))
+                        *reinterpret_cast<float4 *>(static_cast<C *>(d.uv) + uv_index(n, k2, a.ldk)) = park[n];
                 }
             }
             if (aligned && t == 0 && valid) {
                 constexpr int BP = uv_box_pairs(1 << LOG);
 #pragma unroll 1
-                for (int p0 = 0; p0 < (N1 >> 1); p0 += BP) tma_store_3d(tm, park + 2 * p0, 0, k2, p0);
+                for (int p0 = 0; p0 < (N1 >> 1); p0 += BP)
+                    if (FLAME_IN(d.status, k2, a.ldk, kSiteCAUv) && FLAME_IN(d.status, p0, a.n1 >> 1, kSiteCAUv))
+                        tma_store_3d(tm, park + 2 * p0, 0, k2, p0);
                 bulk_commit_and_wait_read();
             }
             __syncthreads();  // the park may be overwritten by the next transform

@@ -203,29 +203,51 @@ template <class R> cudaError_t Ops<R>::init_twiddles(C *tab, int logN, cudaStrea
 
 template <class R>
 cudaError_t Ops<R>::box_from_spec(const C *spec, C *state, double *mean, int n1, int n2, int K1, int K2,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int *status) {
     const long total = (long)(2 * K1 + 1) * (K2 + 1);
     const int blocks = (int)std::min<long>((total + 255) / 256, 8L * sm_count());
-    return launch_cl(k_box_from_spec<R>, dim3(blocks), 256, 0, s, 1, spec, state, mean, n1, n2, K1, K2);
+    return launch_cl(k_box_from_spec<R>, dim3(blocks), 256, 0, s, 1, spec, state, mean, n1, n2, K1, K2, status);
 }
 
+// The standalone 2-D FFT passes take the compile-time line length where the
+// step kernels do (FP32, 2^8 .. 2^12), the runtime-length engine otherwise.
 template <class R>
-cudaError_t Ops<R>::rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s) {
+cudaError_t Ops<R>::rows_r2c(const R *in, C *out, int n1, int logm, const C *tw, cudaStream_t s, int *status) {
     Geom g = geom_rows(logm, n1 / 2, 0);
-    return launch_cl(k_rows_r2c<R>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, n1, logm, tw);
+    cudaError_t err = cudaSuccess;
+    with_log<R>(logm, [&](auto lc) {
+        err = launch_cl(k_rows_r2c<R, decltype(lc)::value>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, n1, logm,
+                        tw, status);
+    });
+    return err;
 }
 
 template <class R>
-cudaError_t Ops<R>::rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s) {
+cudaError_t Ops<R>::rows_c2r(const C *in, R *out, int n1, int logm, const C *tw, cudaStream_t s, int *status) {
     Geom g = geom_rows(logm, n1 / 2, 0);
-    return launch_cl(k_rows_c2r<R>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, n1, logm, tw);
+    cudaError_t err = cudaSuccess;
+    with_log<R>(logm, [&](auto lc) {
+        err = launch_cl(k_rows_c2r<R, decltype(lc)::value>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, n1, logm,
+                        tw, status);
+    });
+    return err;
 }
 
 template <class R>
-cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw, cudaStream_t s) {
+cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int dir, const C *tw, cudaStream_t s,
+                         int *status) {
     Geom g = geom_cols(logn, (ncols + 1) / 2, 0);
-    if (dir < 0) return launch_cl(k_cols<R, -1>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, logn, ncols, ld, tw);
-    return launch_cl(k_cols<R, 1>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, logn, ncols, ld, tw);
+    cudaError_t err = cudaSuccess;
+    with_log<R>(logn, [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (dir < 0)
+            err = launch_cl(k_cols<R, -1, L>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, logn, ncols, ld, tw,
+                            status);
+        else
+            err = launch_cl(k_cols<R, 1, L>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, logn, ncols, ld, tw,
+                            status);
+    });
+    return err;
 }
 
 // pass A with 8 points per thread (compile-time length 2^L): fixed shape
@@ -311,8 +333,20 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
     return cudaGetLastError();
 }
 // pass B parks one row of |z|^2 (N2/2 complex) per group in shared memory
-template <class R> static Geom geom_passB(int logm, int nlines) {
-    return make_geom<R>(logm, nlines, 0, (size_t)(1 << logm) * sizeof(typename VecOf<R>::c));
+template <class R> static Geom geom_passB(int logm, int nlines, int hint = 0) {
+    return make_geom<R>(logm, nlines, hint, (size_t)(1 << logm) * sizeof(typename VecOf<R>::c));
+}
+
+// Line groups per CTA of a grouped (ensemble) launch over n flames of
+// nlines lines each.  Per flame, make_geom shrinks G until one flame's grid
+// spans two CTAs per SM; with FLAME_BATCH_GEOM=1 G is chosen for the class's
+// n * nlines lines instead (the flames fill the GPU together).  Returns the
+// hint for make_geom (0: per-flame choice).
+template <class R> static int batch_groups(int logn, int nlines, int n, size_t extra = 0) {
+    const char *v = getenv("FLAME_BATCH_GEOM");
+    if (!v || strcmp(v, "1") != 0) return 0;
+    const Geom all = make_geom<R>(logn, nlines * n, 0, extra);
+    return all.threads / ((1 << logn) >> 4);
 }
 
 // pass B with 8 points per thread: 512-thread CTAs, padding every 8 slots
@@ -488,7 +522,7 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         });
         return err;
     }
-    Geom g = geom_cols(a.logn1, a.K2 + 1, 0);
+    Geom g = geom_cols(a.logn1, a.K2 + 1, batch_groups<R>(a.logn1, a.K2 + 1, n));
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
@@ -524,7 +558,8 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         });
         return err;
     }
-    Geom g = geom_passB<R>(a.logm, a.n1 / 2);
+    Geom g = geom_passB<R>(a.logm, a.n1 / 2,
+                           batch_groups<R>(a.logm, a.n1 / 2, n, (size_t)(1 << a.logm) * sizeof(typename VecOf<R>::c)));
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
@@ -556,7 +591,7 @@ cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         });
         return err;
     }
-    Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, 0);
+    Geom g = geom_cols(a.logn1, (a.K2 + 2) / 2, batch_groups<R>(a.logn1, (a.K2 + 2) / 2, n));
     cudaError_t e = cudaSuccess;
     with_log<R>(a.logn1, [&](auto lc) {
         constexpr int L = decltype(lc)::value;

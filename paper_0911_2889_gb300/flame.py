@@ -20,12 +20,13 @@ import torch
 from . import build as _build
 
 FLAME_OK, FLAME_EINVAL, FLAME_ENOMEM, FLAME_ECUDA = 0, 1, 2, 3
-FLAME_EUNSUPPORTED, FLAME_ETIMEOUT, FLAME_ENONFINITE = 4, 5, 6
+FLAME_EUNSUPPORTED, FLAME_ETIMEOUT, FLAME_ENONFINITE, FLAME_EBOUNDS = 4, 5, 6, 7
 FLAME_FP64, FLAME_FP32_MIXED = 0, 1
 FLAME_LINEAR_ONLY, FLAME_NONLINEAR_ONLY = 1, 2
 
 _STATUS = {0: "FLAME_OK", 1: "FLAME_EINVAL", 2: "FLAME_ENOMEM", 3: "FLAME_ECUDA",
-           4: "FLAME_EUNSUPPORTED", 5: "FLAME_ETIMEOUT", 6: "FLAME_ENONFINITE"}
+           4: "FLAME_EUNSUPPORTED", 5: "FLAME_ETIMEOUT", 6: "FLAME_ENONFINITE",
+           7: "FLAME_EBOUNDS"}
 
 
 class FlameError(RuntimeError):
@@ -70,26 +71,34 @@ SIGNATURES = {
     "flame_adjoint": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "flame_step_noalloc": (_i, [ctypes.POINTER(flame_params), _vp, _vp, _vp, _i, _vp]),
     "flame_fma_peak": (_i, [_i, ctypes.POINTER(ctypes.c_double)]),
+    "flame_debug_bounds_probe": (_i, [_vp, _i, _i, _vp]),
     "flame_sync_status": (_i, [_vp]),
     "flame_status_str": (ctypes.c_char_p, [_i]),
     "flame_last_error": (ctypes.c_char_p, []),
 }
 
 
+def debug_bounds() -> bool:
+    """True when FLAME_DEBUG_BOUNDS=1: the binding then loads the
+    index-checking build libflame_debug.so instead of libflame.so."""
+    return os.environ.get("FLAME_DEBUG_BOUNDS", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_bounds() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Loads libflame.so (building it in-tree first if it is missing)."""
+    """Loads libflame.so, or libflame_debug.so with FLAME_DEBUG_BOUNDS=1
+    (building it in-tree first if it is missing)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            path = library_path()
             if build_if_missing and not os.path.exists(path):
-                _build.build_library()
+                _build.build_library(debug=debug_bounds())
             if not os.path.exists(path):
-                raise RuntimeError(f"libflame.so not found at {path}; run build()")
+                raise RuntimeError(f"{os.path.basename(path)} not found at {path}; run build()")
             lib = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(lib, name)
@@ -132,7 +141,17 @@ def flame_create(params: flame_params) -> int:
     return h.value
 
 
+# Index-checking build: the failures found on the handles destroyed so far
+# (flame_destroy reads a handle's status words first); the test suite run
+# against libflame_debug.so requires it to stay empty.
+bounds_failures: list = []
+
+
 def flame_destroy(h: int):
+    if debug_bounds():
+        lib = load()
+        if lib.flame_sync_status(ctypes.c_void_p(h)) == FLAME_EBOUNDS:
+            bounds_failures.append(lib.flame_last_error().decode(errors="replace"))
     _check(load().flame_destroy(ctypes.c_void_p(h)))
 
 
@@ -266,6 +285,44 @@ def noalloc_state_spec(params: flame_params):
     return dtype, (K2 + 1, 2 * K1 + 1)
 
 
+# Parameters that must agree between a checkpoint and the handle that resumes
+# it (the state's layout and the time lattice t_n = t0 + n dt).
+_CKPT_FIELDS = ("n_theta", "n_phi", "K1", "K2", "gamma", "theta_pi", "s1", "s2", "t0", "dt", "prec", "flags")
+
+
+def checkpoint(params: flame_params, state, mean_mode, t):
+    """Resumable snapshot of a run: host copies of the state box, the FP64
+    mean mode and time, the lattice step index n = round((t - t0) / dt) and
+    the resolved parameters (a dict of tensors and numbers that torch.save
+    writes).  The copies are taken after the work already enqueued on the
+    current stream."""
+    tt = float(t.reshape(-1)[0].item())
+    return {"format": "flame-checkpoint-1",
+            "params": {f: getattr(params, f) for f in _CKPT_FIELDS},
+            "state": state.detach().to("cpu", copy=True),
+            "mean_mode": float(mean_mode.reshape(-1)[0].item()),
+            "t": tt, "step": int(round((tt - params.t0) / params.dt))}
+
+
+def restore(params: flame_params, ckpt, device="cuda"):
+    """(state, mean_mode, t) tensors on `device` from a checkpoint taken
+    with the same parameters; ValueError when they differ (another grid,
+    truncation, precision or time lattice) or the entry is malformed."""
+    if not isinstance(ckpt, dict) or ckpt.get("format") != "flame-checkpoint-1":
+        raise ValueError("not a flame checkpoint")
+    for f in _CKPT_FIELDS:
+        if ckpt["params"].get(f) != getattr(params, f):
+            raise ValueError(f"checkpoint parameter {f}={ckpt['params'].get(f)} differs from {getattr(params, f)}")
+    dtype, shape = noalloc_state_spec(params)
+    st = ckpt["state"]
+    if st.dtype != dtype or tuple(st.shape) != shape:
+        raise ValueError(f"checkpoint state is {st.dtype} {tuple(st.shape)}, expected {dtype} {shape}")
+    state = st.to(device, copy=True)
+    mean = torch.full((1,), ckpt["mean_mode"], dtype=torch.float64, device=device)
+    t = torch.full((1,), ckpt["t"], dtype=torch.float64, device=device)
+    return state, mean, t
+
+
 def flame_step_noalloc(params: flame_params, state, mean_mode, t, nsteps=1, stream=None):
     """flame_step for callers that cannot allocate: scratch is the library's
     static device array (see include/flame.h).  The library receives only
@@ -293,6 +350,12 @@ def flame_fma_peak(prec="fp64") -> float:
 
 def flame_sync_status(h):
     _check(load().flame_sync_status(ctypes.c_void_p(h)))
+
+
+def flame_debug_bounds_probe(h, index, extent, stream=None):
+    """One device index check of (index, extent) with no memory access
+    (index-checking build only; FLAME_EUNSUPPORTED otherwise)."""
+    _check(load().flame_debug_bounds_probe(ctypes.c_void_p(h), int(index), int(extent), _stream(stream)))
 
 
 def flame_status_str(s: int) -> str:
@@ -446,6 +509,15 @@ class Flame:
 
     def sync_status(self):
         flame_sync_status(self.h)
+
+    def checkpoint(self, state, mean_mode, t):
+        """Resumable snapshot of this handle's run (see checkpoint())."""
+        return checkpoint(self.params, state, mean_mode, t)
+
+    def restore(self, ckpt, device="cuda"):
+        """(state, mean_mode, t) from a checkpoint of a run with the same
+        parameters (see restore())."""
+        return restore(self.params, ckpt, device)
 
     def close(self):
         if getattr(self, "h", None):

@@ -46,3 +46,19 @@ def fl():
 def rel_l2(a, b):
     import numpy as np
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(autouse=True)
+def _no_index_check_failures():
+    """Under FLAME_DEBUG_BOUNDS=1 (the index-checking library) every handle a
+    test destroyed must have clean status words: no index outside its
+    array."""
+    yield
+    if os.environ.get("FLAME_DEBUG_BOUNDS", "0") != "1":
+        return
+    import gc
+    from paper_0911_2889_gb300 import flame
+    gc.collect()  # handles dropped without close() are destroyed here
+    failures, flame.bounds_failures[:] = list(flame.bounds_failures), []
+    assert not failures, failures
+

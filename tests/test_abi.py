@@ -106,6 +106,8 @@ def test_new_entry_points_reject_bad_arguments(lib):
     out = ctypes.c_double(0.0)
     assert lib.flame_fma_peak(7, ctypes.byref(out)) == 1
     assert lib.flame_fma_peak(0, None) == 1
+    assert lib.flame_debug_bounds_probe(None, 0, 1, None) == 1
+    assert lib.flame_status_str(7) == b"index out of bounds (index-checking build)"
 
 
 @pytest.mark.gpu

@@ -191,8 +191,11 @@ def test_nonfinite_detected(fl):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("branches", ["0", "1"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_equals_individual(fl, prec):
+def test_batch_equals_individual(fl, monkeypatch, prec, branches):
+    # branches = 1: the ensemble's graph has one branch per size class
+    monkeypatch.setenv("FLAME_BATCH_STREAMS", branches)
     shapes = [(64, 128), (32, 64), (64, 128), (128, 256), (32, 64)]
     fs, ss, ms, ts, ref = [], [], [], [], []
     for i, (n1, n2) in enumerate(shapes):
@@ -221,10 +224,12 @@ def test_batch_equals_individual(fl, prec):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("branches", ["0", "1"])
 @pytest.mark.parametrize("variants", ["3,2", "1,0", None])
-def test_batch_of_compile_time_grids_equals_individual(fl, monkeypatch, variants):
+def test_batch_of_compile_time_grids_equals_individual(fl, monkeypatch, variants, branches):
     # grids with compile-time kernels: the ensemble runs the grouped kernels
     # (with per-flame tensor maps for the tensor-store variants 3 and 2)
+    monkeypatch.setenv("FLAME_BATCH_STREAMS", branches)
     if variants is None:
         monkeypatch.delenv("FLAME_FORCE_VARIANTS", raising=False)
     else:
@@ -264,6 +269,37 @@ def test_every_tuned_variant_matches_oracle(fl, orc, monkeypatch, variants, shap
     assert _box_err(_host(fl, state), ref, f.K1) < 2e-5
     assert t.item() == tref
     f.close()
+
+
+@pytest.mark.gpu
+def test_autotuner_cache_file(fl, monkeypatch, tmp_path):
+    # FLAME_TUNE_CACHE: a handle whose key the file holds takes that choice
+    # without timing; a new key is tuned and added, other entries are kept
+    import json
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("FLAME_TUNE_CACHE", str(path))
+    monkeypatch.delenv("FLAME_FORCE_VARIANTS", raising=False)
+    monkeypatch.delenv("FLAME_AUTOTUNE", raising=False)
+    monkeypatch.delenv("FLAME_FUSE", raising=False)
+    name = torch.cuda.get_device_name()
+    key = f"{name}|256x512|60,120|fp32"      # K not tuned before in this process
+    other = "another GPU|1x1|0,0|fp32"
+    path.write_text(json.dumps({key: [1, 0, 0], other: [0, 0, 1]}))
+    f = fl.Flame(256, 512, prec="fp32", K1=60, K2=120)
+    assert fl.flame_tuning(f.h) == (1, 0) and not fl.flame_fused_steps(f.h)
+    f.close()
+    f = fl.Flame(256, 512, prec="fp32", K1=61, K2=121)
+    va, vb = fl.flame_tuning(f.h)
+    fused = fl.flame_fused_steps(f.h)
+    f.close()
+    d = json.loads(path.read_text())
+    assert d[key] == [1, 0, 0] and d[other] == [0, 0, 1]
+    assert d[f"{name}|256x512|61,121|fp32"] == [va, vb, int(fused)]
+    # a malformed file is ignored and rewritten
+    path.write_text("{not json")
+    f = fl.Flame(256, 512, prec="fp32", K1=62, K2=122)
+    f.close()
+    assert f"{name}|256x512|62,122|fp32" in json.loads(path.read_text())
 
 
 @pytest.mark.gpu
