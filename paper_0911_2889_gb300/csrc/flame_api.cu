@@ -1233,6 +1233,17 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
     }
     const FlameDesc *dev = static_cast<const FlameDesc *>(h0->batch_desc);
     const CUtensorMap *dmaps = reinterpret_cast<const CUtensorMap *>(static_cast<char *>(h0->batch_desc) + mofs);
+    // FLAME_BATCH_VARIANTS=a,b: the grouped launches use these pass A and B
+    // variants (in flame_tuning's numbering) instead of the variants the
+    // autotuner chose for a single flame of the class's grid
+    int force_a = -1, force_b = -1;
+    if (const char *bv = getenv("FLAME_BATCH_VARIANTS")) {
+        int fa = 0, fb = 0;
+        if (sscanf(bv, "%d,%d", &fa, &fb) == 2) {
+            force_a = fa;
+            force_b = fb;
+        }
+    }
     // one pass of one size class: a grouped launch over the class's flames
     auto enqueue_pass = [&](size_t ci, int pass, cudaStream_t q) -> cudaError_t {
         const auto &rg = ranges[ci];
@@ -1257,17 +1268,6 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
     // the classes' passes are independent nodes of the graph and a
     // compute-bound pass of one class may run beside a memory-bound pass of
     // another.
-    // FLAME_BATCH_VARIANTS=a,b: the grouped launches use these pass A and B
-    // variants (in flame_tuning's numbering) instead of the variants the
-    // autotuner chose for a single flame of the class's grid
-    int force_a = -1, force_b = -1;
-    if (const char *bv = getenv("FLAME_BATCH_VARIANTS")) {
-        int fa = 0, fb = 0;
-        if (sscanf(bv, "%d,%d", &fa, &fb) == 2) {
-            force_a = fa;
-            force_b = fb;
-        }
-    }
     const char *bs = getenv("FLAME_BATCH_STREAMS");
     const bool branches = bs && strcmp(bs, "1") == 0 && ranges.size() > 1;
     auto enqueue_steps = [&](int n, cudaStream_t q) -> cudaError_t {
