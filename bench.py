@@ -65,7 +65,7 @@ def pass_bytes(n1, n2, K1, K2, esz):
 
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled through NVML every
-    ~0.5 ms while the timed region runs.  The device is found by its UUID,
+    ~0.2 ms while the timed region runs.  The device is found by its UUID,
     so CUDA_VISIBLE_DEVICES renumbering does not matter.  Reads only: no
     setting of the GPU is changed."""
 
@@ -105,7 +105,7 @@ class ClockSampler:
             if nv.nvmlDeviceGetClockInfo(self._h, 1, ct.byref(clk)) == 0 and \
                     self._reasons(self._h, ct.byref(rs)) == 0:
                 self.samples.append((float(clk.value), int(rs.value)))
-            time.sleep(0.0005)
+            time.sleep(0.0002)
 
     def start(self):
         if self._nv is not None:

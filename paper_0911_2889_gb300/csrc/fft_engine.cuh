@@ -54,7 +54,25 @@ __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ double2 vbc(double s) { return make_double2(s, s); }
 __device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
 
-// Complex number whose re and im each hold the two lines.
+// One line per thread in FP64 (the short-line FP64 step kernels): a V of one
+// double, so that the two lines of a pair run in different warps.  GB300's
+// FP64 units serve each SM sub-partition separately, and a line pair per
+// warp leaves the other sub-partitions' units idle.
+struct D1 {
+    double x;
+};
+__device__ __forceinline__ D1 vneg(D1 a) { return {-a.x}; }
+__device__ __forceinline__ D1 vadd(D1 a, D1 b) { return {a.x + b.x}; }
+__device__ __forceinline__ D1 vsub(D1 a, D1 b) { return {a.x - b.x}; }
+__device__ __forceinline__ D1 vmul(D1 a, D1 b) { return {a.x * b.x}; }
+__device__ __forceinline__ D1 vfma(D1 a, D1 b, D1 c) { return {fma(a.x, b.x, c.x)}; }
+__device__ __forceinline__ D1 vzero(D1) { return {0.0}; }
+// broadcast of a scalar to the V type of the tag
+__device__ __forceinline__ float2 vbc_as(float s, float2) { return make_float2(s, s); }
+__device__ __forceinline__ double2 vbc_as(double s, double2) { return make_double2(s, s); }
+__device__ __forceinline__ D1 vbc_as(double s, D1) { return {s}; }
+
+// Complex number whose re and im each hold the two lines (or one, for D1).
 template <class V> struct CV { V re, im; };
 
 template <class V> __device__ __forceinline__ CV<V> cadd(CV<V> a, CV<V> b) {
@@ -74,11 +92,11 @@ template <int S, class V> __device__ __forceinline__ CV<V> csub_rot(CV<V> a, CV<
 // a * (wr + i wi) with the same scalar twiddle on both lines: two paired
 // multiplies and two paired FMAs (the subtraction is a negated addend)
 template <class V, class R> __device__ __forceinline__ CV<V> cmul_s(CV<V> a, R wr, R wi) {
-    V vr = vbc(wr), vi = vbc(wi);
+    V vr = vbc_as(wr, V{}), vi = vbc_as(wi, V{});
     return {vfma(a.re, vr, vneg(vmul(a.im, vi))), vfma(a.re, vi, vmul(a.im, vr))};
 }
 template <class V, class R> __device__ __forceinline__ CV<V> cscale(CV<V> a, R s) {
-    V v = vbc(s);
+    V v = vbc_as(s, V{});
     return {vmul(a.re, v), vmul(a.im, v)};
 }
 
@@ -262,6 +280,16 @@ template <> struct Planes<double2> {
     __device__ __forceinline__ CV<double2> ld(int i) const { return {re[spad(i)], im[spad(i)]}; }
     __device__ __forceinline__ void st_raw(int j, CV<double2> v) const { re[j] = v.re; im[j] = v.im; }
     __device__ __forceinline__ CV<double2> ld_raw(int j) const { return {re[j], im[j]}; }
+};
+// One-line FP64 exchange buffer: separate re and im planes of `plane`
+// doubles each.
+template <> struct Planes<D1> {
+    double *re, *im;
+    __device__ __forceinline__ Planes(double *base, int plane) : re(base), im(base + plane) {}
+    __device__ __forceinline__ void st(int i, CV<D1> v) const { re[spad(i)] = v.re.x; im[spad(i)] = v.im.x; }
+    __device__ __forceinline__ CV<D1> ld(int i) const { return {{re[spad(i)]}, {im[spad(i)]}}; }
+    __device__ __forceinline__ void st_raw(int j, CV<D1> v) const { re[j] = v.re.x; im[j] = v.im.x; }
+    __device__ __forceinline__ CV<D1> ld_raw(int j) const { return {{re[j]}, {im[j]}}; }
 };
 // Exchange buffer of a group: `base` points at 2 * plane_len(n) V slots.
 __device__ __forceinline__ Planes<float2> make_planes(float2 *base, int n) { return Planes<float2>(base); }

@@ -1001,6 +1001,142 @@ template <class R> __device__ __forceinline__ R kappa_norm(R s1k1, R s2k2) {
     }
 }
 
+// Pass C's epilogue, shared by its kernels: the update of one box entry
+// (a8..a10), the area of the state entering the step for the record, and
+// the mean mode, time and record written by thread 0 of tile 0.
+template <class R> struct EpiArgs {
+    CoefR<R> cf;
+    R s1, s2;
+    int stage;  // kStage*, uniform over the launch
+    bool lin, nl;
+};
+
+// Entry (k1, k2) of the box, k = (k1, k2) != (0, 0) updated from the scaled
+// transform gh = c-free ghat and the entry ph entering the step:
+// Phi <- Phi + dt (omega Phi + c ghat + f) for the Euler stage and the
+// combinations of the two-stage schemes (see kStage*).  col, fcol and scol
+// point at k1 = 0 of column k2 of the state, the forcing (or null) and the
+// stage buffer (or null); the k2 = 0 column also gets the conjugate mirror
+// at -k1.  nw returns the new entry (0 for k = 0); bad collects non-finite
+// results.
+template <class R, bool GEN>
+__device__ __forceinline__ void update_entry(const FlameDesc &d, const EpiArgs<R> &e, int k1, int k2, CplxT<R> gh,
+                                             CplxT<R> ph, CplxT<R> *col, const CplxT<R> *fcol, CplxT<R> *scol,
+                                             CplxT<R> &nw, int &bad) {
+    using C = CplxT<R>;
+    const StepArgs &a = d.a;
+    nw = C{0, 0};
+    [[maybe_unused]] const long long bi = (long long)k2 * (2 * a.K1 + 1) + a.K1 + k1;  // box index of (k1, k2)
+    if (!FLAME_IN(d.status, bi, box_len(a), kSiteCState)) return;
+    if (k1 == 0 && k2 == 0) {
+        col[0] = C{0, 0};
+        return;
+    }
+    const R rdt = e.cf.dt;
+    const R kap = kappa_norm<R>(rmul(e.s1, (R)k1), rmul(e.s2, (R)k2));
+    const R om = e.lin ? rmul(kap, rfma(-kap, e.cf.a, e.cf.b)) : (R)0;
+    const R cn = e.nl ? e.cf.cs : (R)0;
+    // the non-stiff part: c ghat (+ the forcing f_k)
+    C nt{rmul(cn, gh.x), rmul(cn, gh.y)};
+    if (GEN && fcol && FLAME_IN(d.status, bi, box_len(a), kSiteCForcing)) {
+        const C f = fcol[k1];
+        nt = C{radd(nt.x, f.x), radd(nt.y, f.y)};
+    }
+    // dt F = dt (omega Phi + nt)
+    const C df{rmul(rdt, rfma(om, ph.x, nt.x)), rmul(rdt, rfma(om, ph.y, nt.y))};
+    const int stage = GEN ? e.stage : kStageEuler;
+    if (stage != kStageEuler && !FLAME_IN(d.status, bi, box_len(a), kSiteCSave)) return;
+    C v;
+    if (stage == kStageEuler || stage == kStageHeun1) {
+        v = C{radd(ph.x, df.x), radd(ph.y, df.y)};
+        if (stage == kStageHeun1) scol[k1] = ph;
+    } else if (stage == kStageHeun2) {
+        const C sv = scol[k1];
+        const R h = (R)0.5;
+        v = C{rmul(h, radd(radd(sv.x, ph.x), df.x)), rmul(h, radd(radd(sv.y, ph.y), df.y))};
+    } else if (stage == kStageIF1) {
+        // exact propagator of the linear part over the step
+        R ef = (R)1;
+        if (e.lin) {
+            const R ex = rmul(kap, rfma(-kap, e.cf.ia, e.cf.ib));
+            if constexpr (std::is_same<R, float>::value) ef = expf(ex);
+            else ef = exp(ex);
+        }
+        const R hdt = rmul((R)0.5, rdt);
+        v = C{rmul(ef, rfma(rdt, nt.x, ph.x)), rmul(ef, rfma(rdt, nt.y, ph.y))};
+        scol[k1] = C{rmul(ef, rfma(hdt, nt.x, ph.x)), rmul(ef, rfma(hdt, nt.y, ph.y))};
+    } else {  // kStageIF2
+        const C sv = scol[k1];
+        const R hdt = rmul((R)0.5, rdt);
+        v = C{rfma(hdt, nt.x, sv.x), rfma(hdt, nt.y, sv.y)};
+    }
+    bad |= !(isfinite(v.x) && isfinite(v.y));
+    col[k1] = v;
+    nw = v;
+    if (k2 == 0 && FLAME_IN(d.status, a.K1 - k1, box_len(a), kSiteCState)) col[-k1] = C{v.x, -v.y};
+}
+
+// The surface area of the state entering the step, for the record: the
+// area variant of pass B left one FP64 sum per row pair (summed here by
+// tile 0's threads, all of which call this), or the separate area kernels
+// left the total; NaN when the step records no area.
+template <bool GEN> __device__ __forceinline__ double record_area(const FlameDesc &d, int tile, int stage, int N1) {
+    const StepArgs &a = d.a;
+    double area = __longlong_as_double(0x7ff8000000000000LL);
+    if (GEN && tile == 0 && d.rec && stage != kStageHeun2 && stage != kStageIF2) {
+        if (d.rec_area == 1) {
+            __shared__ double asum[32];
+            double v = 0.0;
+            for (int i = threadIdx.x; i < (a.n1 >> 1); i += blockDim.x)
+                if (FLAME_IN(d.status, i, a.n1 >> 1, kSiteCRec)) v += d.arow[i];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) asum[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += asum[w];
+                const double two_pi = 6.283185307179586476925286766559;
+                area = tot * (two_pi * two_pi / ((double)N1 * (double)a.n2 * a.s1 * a.s2));
+            }
+        } else if (d.rec_area == 2) {
+            area = *d.aval;
+        }
+    }
+    return area;
+}
+
+// Thread 0 of tile 0: the mean mode's update from rs, the FP64 sum of column
+// k2 = 0 of gk (N1 N2 times the mean of |grad Phi|^2), the time, and the
+// record entry of the step.
+template <bool GEN>
+__device__ __forceinline__ void finish_step(const FlameDesc &d, int stage, bool nl, int N1, double rs, double area) {
+    const StepArgs &a = d.a;
+    const double mg = rs / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
+    // dt times the mean mode's right-hand side (omega_0 = 0): c mg + f_0
+    double inc = nl ? a.dt * d.coef[1] * mg : 0.0;
+    if (GEN && d.forcing0 != 0.0) inc += a.dt * d.forcing0;
+    const double m = *d.mean;
+    long n = __double2ll_rn((d.coef[0] - a.t0) / a.dt);
+    const long ri = ((n % max(d.rec_cap, 1)) + d.rec_cap) % max(d.rec_cap, 1);
+    if (GEN && d.rec && stage != kStageHeun2 && stage != kStageIF2 && FLAME_IN(d.status, ri, d.rec_cap, kSiteCRec)) {
+        double *e = d.rec + 4 * (size_t)ri;
+        e[0] = d.coef[0];
+        e[1] = m;
+        e[2] = (nl ? d.coef[1] * mg : 0.0) + (GEN ? d.forcing0 : 0.0);
+        e[3] = area;
+    }
+    if (stage == kStageEuler || stage == kStageHeun1 || stage == kStageIF1) {
+        if (stage == kStageHeun1) *d.save_mean = m;
+        if (stage == kStageIF1) *d.save_mean = m + 0.5 * inc;
+        *d.mean = m + inc;
+        *d.t_out = a.t0 + (double)(n + 1) * a.dt;
+    } else {
+        // second stages are evaluated at t_{n+1} and leave t there
+        *d.mean = stage == kStageHeun2 ? 0.5 * (*d.save_mean + m + inc) : *d.save_mean + 0.5 * inc;
+        *d.t_out = a.t0 + (double)n * a.dt;
+    }
+}
+
 // Pass C (a7..a10): columns k2, k2+1 of gk -> forward FFT along j1 (outputs
 // outside |k1| <= K1 unused and dropped at compile time), scaled by
 // 1/(N1 N2) -> ghat; Phi <- Phi + dt (omega Phi + c ghat); the k2 = 0 column
@@ -1101,9 +1237,8 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         phi[i][1] = (in_box && vb && FLAME_IN(d.status, ia + ld1, box_len(a), kSiteCState)) ? sb[k1] : C{0, 0};
     }
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
-    const R ra = cfs.a, rb = cfs.b, rcs = cfs.cs, rdt = cfs.dt;
-    const R s1 = scale1<R>(a), s2 = scale2<R>(a);
     const int stage = GEN ? d.stage : kStageEuler;  // block-uniform
+    const EpiArgs<R> ea{cfs, scale1<R>(a), scale2<R>(a), stage, lin, nl};
     const C *fa = GEN && d.forcing ? static_cast<const C *>(d.forcing) + (size_t)c0 * ld1 + a.K1 : nullptr;
     C *va_save = GEN && d.save ? static_cast<C *>(d.save) + (size_t)c0 * ld1 + a.K1 : nullptr;
     int bad = 0;
@@ -1121,108 +1256,18 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
             const bool ok = in_box && (side == 0 ? va : vb);
             if (!ok) continue;
             if (k2 == 0 && k1 < 0) continue;  // written as the mirror of +k1
-            C *col = side == 0 ? sa : sb;
-            [[maybe_unused]] const long long bi = (long long)k2 * ld1 + a.K1 + k1;  // box index of (k1, k2)
-            if (!FLAME_IN(d.status, bi, box_len(a), kSiteCState)) continue;
-            if (k1 == 0 && k2 == 0) {
-                col[0] = C{0, 0};
-                continue;
-            }
-            C gh = side == 0 ? lane0<R>(x[r]) : lane1<R>(x[r]);
-            C ph = phi[i][side];
-            const R kap = kappa_norm<R>(rmul(s1, (R)k1), rmul(s2, (R)k2));
-            const R om = lin ? rmul(kap, rfma(-kap, ra, rb)) : (R)0;
-            const R cn = nl ? rcs : (R)0;
-            // the non-stiff part: c ghat (+ the forcing f_k)
-            C nt{rmul(cn, gh.x), rmul(cn, gh.y)};
-            if (fa && FLAME_IN(d.status, bi, box_len(a), kSiteCForcing)) {
-                const C f = fa[(side ? ld1 : 0) + k1];
-                nt = C{radd(nt.x, f.x), radd(nt.y, f.y)};
-            }
-            // dt F = dt (omega Phi + nt)
-            const C df{rmul(rdt, rfma(om, ph.x, nt.x)), rmul(rdt, rfma(om, ph.y, nt.y))};
-            C nw;
-            if (stage != kStageEuler && !FLAME_IN(d.status, bi, box_len(a), kSiteCSave)) continue;
-            if (stage == kStageEuler || stage == kStageHeun1) {
-                nw = C{radd(ph.x, df.x), radd(ph.y, df.y)};
-                if (stage == kStageHeun1) va_save[(side ? ld1 : 0) + k1] = ph;
-            } else if (stage == kStageHeun2) {
-                const C sv = va_save[(side ? ld1 : 0) + k1];
-                const R h = (R)0.5;
-                nw = C{rmul(h, radd(radd(sv.x, ph.x), df.x)), rmul(h, radd(radd(sv.y, ph.y), df.y))};
-            } else if (stage == kStageIF1) {
-                // exact propagator of the linear part over the step
-                R ef = (R)1;
-                if (lin) {
-                    const R ex = rmul(kap, rfma(-kap, cfs.ia, cfs.ib));
-                    if constexpr (std::is_same<R, float>::value) ef = expf(ex);
-                    else ef = exp(ex);
-                }
-                const R hdt = rmul((R)0.5, rdt);
-                nw = C{rmul(ef, rfma(rdt, nt.x, ph.x)), rmul(ef, rfma(rdt, nt.y, ph.y))};
-                va_save[(side ? ld1 : 0) + k1] = C{rmul(ef, rfma(hdt, nt.x, ph.x)), rmul(ef, rfma(hdt, nt.y, ph.y))};
-            } else {  // kStageIF2
-                const C sv = va_save[(side ? ld1 : 0) + k1];
-                const R hdt = rmul((R)0.5, rdt);
-                nw = C{rfma(hdt, nt.x, sv.x), rfma(hdt, nt.y, sv.y)};
-            }
-            bad |= !(isfinite(nw.x) && isfinite(nw.y));
-            col[k1] = nw;
-            nphi[i][side] = nw;
-            if (k2 == 0 && FLAME_IN(d.status, a.K1 - k1, box_len(a), kSiteCState)) col[-k1] = C{nw.x, -nw.y};
+            const int off = side ? ld1 : 0;
+            update_entry<R, GEN>(d, ea, k1, k2, side == 0 ? lane0<R>(x[r]) : lane1<R>(x[r]), phi[i][side],
+                                 (side == 0 ? sa : sb), fa ? fa + off : nullptr, va_save ? va_save + off : nullptr,
+                                 nphi[i][side], bad);
         }
     }
     if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
-    // the surface area of the state entering the step, for the record: the
-    // area variant of pass B left one FP64 sum per row pair (summed here by
-    // block 0's threads), or the separate area kernels left the total
-    double area = __longlong_as_double(0x7ff8000000000000LL);
-    if (GEN && tile == 0 && d.rec && stage != kStageHeun2 && stage != kStageIF2) {
-        if (d.rec_area == 1) {
-            __shared__ double asum[32];
-            double v = 0.0;
-            for (int i = threadIdx.x; i < (a.n1 >> 1); i += blockDim.x)
-                if (FLAME_IN(d.status, i, a.n1 >> 1, kSiteCRec)) v += d.arow[i];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if ((threadIdx.x & 31) == 0) asum[threadIdx.x >> 5] = v;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double tot = 0.0;
-                for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += asum[w];
-                const double two_pi = 6.283185307179586476925286766559;
-                area = tot * (two_pi * two_pi / ((double)N1 * (double)a.n2 * a.s1 * a.s2));
-            }
-        } else if (d.rec_area == 2) {
-            area = *d.aval;
-        }
-    }
+    const double area = record_area<GEN>(d, tile, stage, N1);
     if (tile == 0 && threadIdx.x == 0) {
         double rs = 0.0;
         for (int w = 0; w < (int)blockDim.x; w += span) rs += red[w];
-        const double mg = rs / ((double)N1 * (double)a.n2);  // mean of |grad Phi|^2
-        // dt times the mean mode's right-hand side (omega_0 = 0): c mg + f_0
-        double inc = nl ? a.dt * d.coef[1] * mg : 0.0;
-        if (GEN && d.forcing0 != 0.0) inc += a.dt * d.forcing0;
-        const double m = *d.mean;
-        long n = __double2ll_rn((d.coef[0] - a.t0) / a.dt);
-        const long ri = ((n % max(d.rec_cap, 1)) + d.rec_cap) % max(d.rec_cap, 1);
-        if (GEN && d.rec && stage != kStageHeun2 && stage != kStageIF2 && FLAME_IN(d.status, ri, d.rec_cap, kSiteCRec)) {
-            double *e = d.rec + 4 * (size_t)ri;
-            e[0] = d.coef[0];
-            e[1] = m;
-            e[2] = (nl ? d.coef[1] * mg : 0.0) + (GEN ? d.forcing0 : 0.0);
-            e[3] = area;
-        }
-        if (stage == kStageEuler || stage == kStageHeun1 || stage == kStageIF1) {
-            if (stage == kStageHeun1) *d.save_mean = m;
-            if (stage == kStageIF1) *d.save_mean = m + 0.5 * inc;
-            *d.mean = m + inc;
-            *d.t_out = a.t0 + (double)(n + 1) * a.dt;
-        } else {
-            // second stages are evaluated at t_{n+1} and leave t there
-            *d.mean = stage == kStageHeun2 ? 0.5 * (*d.save_mean + m + inc) : *d.save_mean + 0.5 * inc;
-            *d.t_out = a.t0 + (double)n * a.dt;
-        }
+        finish_step<GEN>(d, stage, nl, N1, rs, area);
     }
     if constexpr (FUSE_A && std::is_same<R, float>::value && LOG > 0) {
         // Pass A of the next step (a1, a2) on the two updated columns, from
@@ -1231,6 +1276,7 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
         // threads (the conjugate mirror) and is read back after the barrier,
         // which also frees the exchange buffer.
         __syncthreads();
+        const R s1 = ea.s1, s2 = ea.s2;
         if (c0 == 0) {
 #pragma unroll
             for (int i = 4; i < 8; ++i) {
@@ -1292,6 +1338,202 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
     }
 }
 
+// ----------------------------------------------------------------------------
+// FP64 step passes for short lines (2^4 .. 2^7 points: the FP64 parity and
+// trajectory grids).  Each line is transformed by its own group of
+// T = 2^LOG / E threads (E = 4 or 8 points per thread, one double per
+// point: V = D1), and a CTA holds the groups of one column (pass A: the two
+// fields), one row pair (pass B: two rows x even/odd points) or one column
+// pair (pass C).  A small grid has too few line pairs to give every SM
+// sub-partition a warp; with one line per group its FP64 work spreads over
+// two to four times as many warps.
+// ----------------------------------------------------------------------------
+// offset of the radix-E table (E = 8 or 4) in a line's twiddle allocation
+template <int E> __host__ __device__ constexpr int tw_offset_e(int log) {
+    return E == 8 ? tw_table_len(log, 4) : tw_table_len(log, 4) + tw_table_len(log, 3);
+}
+
+// Pass A (a1, a2) on column k2: group 0 synthesises i s1 k1 Phi (-> U), group
+// 1 synthesises Phi (-> V = i s2 k2 times it); each writes its half of the
+// (U, V) entries of the column.
+template <int LOG, int E> __device__ __forceinline__ void passA1_body(const FlameDesc &d, int k2) {
+    griddep_wait();
+    griddep_launch();
+    using C = double2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const StepArgs &a = d.a;
+    constexpr int N1 = 1 << LOG, T = N1 / E, PL = plane_len_e<E>(N1);
+    const int f = threadIdx.x / T, t = threadIdx.x % T;
+    const int ld1 = 2 * a.K1 + 1;
+    const bool valid = k2 <= a.K2;
+    const Planes<D1> sm(reinterpret_cast<double *>(smraw) + (size_t)f * 2 * PL, PL);
+    const C *tw = static_cast<const C *>(d.tw1) + tw_offset_e<E>(LOG);
+    const C *col = static_cast<const C *>(d.state) + (size_t)k2 * ld1 + a.K1;  // col[k1], k1 = -K1..K1
+    CV<D1> x[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        x[r] = CV<D1>{{0.0}, {0.0}};
+        // band rows r < E/4 (k1 = n >= 0) and r >= 3E/4 (k1 = n - N1 < 0); the rest is padding
+        if (r < E / 4 || r >= 3 * E / 4) {
+            const int n = t + r * T;
+            const int k1 = (r < E / 4) ? n : n - N1;
+            const bool in_box = valid && ((r < E / 4) ? (n <= a.K1) : (k1 >= -a.K1));
+            if (in_box && FLAME_IN(d.status, (long long)k2 * ld1 + a.K1 + k1, box_len(a), kSiteAState)) {
+                C phi = __ldg(col + k1);
+                if (k1 == 0 && k2 == 0) phi = C{0, 0};
+                const double fk = a.s1 * (double)k1;
+                x[r] = f == 0 ? CV<D1>{{-fk * phi.y}, {fk * phi.x}} : CV<D1>{{phi.x}, {phi.y}};
+            }
+        }
+    }
+    line_fft_ct<1, LOG, E>(x, t, sm, tw, CtaBarrier{});
+    if (!valid) return;
+    C *uv = static_cast<C *>(d.uv);
+    const double s2k2 = a.s2 * (double)k2;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const size_t i = uv_index(t + r * T, k2, a.ldk) + f;  // U, or V one slot further
+        if (FLAME_IN(d.status, i, uv_len(a), kSiteAUv))
+            uv[i] = f == 0 ? C{x[r].re.x, x[r].im.x} : C{-s2k2 * x[r].im.x, s2k2 * x[r].re.x};
+    }
+}
+
+// Pass B (a3..a6) on row pair p: group 2q + s takes the grid points 2m + s
+// of row 2p + q (the half-length inverse FFT of Z[k] exp(2 pi i k s / N2),
+// Z = U + iV) and parks g = u^2 + v^2 there; then group q transforms
+// h[m] = g[2m] + i g[2m+1] of row 2p + q forward and writes G[k], k <= K2,
+// after the real-input post-processing.  Groups 2 and 3 transform zeros in
+// the forward step, so that every group meets the same barriers.
+template <int LOG, int E> __device__ __forceinline__ void passB1_body(const FlameDesc &d, int pair) {
+    griddep_wait();
+    griddep_launch();
+    using C = double2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const StepArgs &a = d.a;
+    constexpr int M = 1 << LOG, T = M / E, PL = plane_len_e<E>(M);
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    const int q = g >> 1, s = g & 1;
+    const bool valid = pair < (a.n1 >> 1);
+    double *smd = reinterpret_cast<double *>(smraw);
+    const Planes<D1> sm(smd + (size_t)g * 2 * PL, PL);
+    double *h = smd + 8 * (size_t)PL;  // g of row 2p + q at h[2M q + j], j the grid point
+    const C *tw = static_cast<const C *>(d.twm) + tw_offset_e<E>(LOG);
+    const C *P = static_cast<const C *>(d.twm) + tw_real_offset(LOG);  // exp(2 pi i k / N2), k < M
+    if (pair == 0 && threadIdx.x == 0) store_coef<double>(d.coef, a, *d.t_in, d.stage == kStageIF1);
+    const size_t base = uv_index(2 * pair + q, 0, a.ldk);  // (U, V) of k at base + 4k
+    const C *src = static_cast<const C *>(d.uv) + base;
+    CV<D1> x[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int n = t + r * T;
+        const int kk = (r < E / 2) ? n : M - n;  // |k|: k = n (r < E/2) or n - M
+        C z{0, 0};
+        if (valid && kk <= a.K2 && kk < M / 2 && FLAME_IN(d.status, base + 4LL * kk + 1, uv_len(a), kSiteBUv)) {
+            const C u = __ldg(src + 4 * (size_t)kk), v = __ldg(src + 4 * (size_t)kk + 1);
+            // U[-k] = conj U[k], V[-k] = conj V[k]
+            z = (r < E / 2) ? C{u.x - v.y, u.y + v.x} : C{u.x + v.y, v.x - u.y};
+        }
+        if (s == 1) {
+            C w = __ldg(P + kk);  // exp(2 pi i k / N2) for the signed k
+            if (r >= E / 2) w.y = -w.y;
+            z = C{fma_rn(z.x, w.x, -(z.y * w.y)), fma_rn(z.x, w.y, z.y * w.x)};
+        }
+        x[r] = CV<D1>{{z.x}, {z.y}};
+    }
+    line_fft_ct<1, LOG, E>(x, t, sm, tw, CtaBarrier{});
+#pragma unroll
+    for (int r = 0; r < E; ++r) h[2 * M * q + 2 * (t + r * T) + s] = fma(x[r].re.x, x[r].re.x, x[r].im.x * x[r].im.x);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int m = t + r * T;
+        x[r] = g < 2 ? CV<D1>{{h[2 * M * g + 2 * m]}, {h[2 * M * g + 2 * m + 1]}} : CV<D1>{{0.0}, {0.0}};
+    }
+    line_fft_ct<-1, LOG, E>(x, t, sm, tw, CtaBarrier{});
+    __syncthreads();
+    // the post-processing of k in [0, M/2) reads H[M - k]: H[0] and the upper half go to shared memory
+#pragma unroll
+    for (int r = E / 2; r < E; ++r) sm.st_raw(spad_e<E>(t + r * T), x[r]);
+    if (t == 0) sm.st_raw(0, x[0]);
+    __syncthreads();
+    if (g >= 2 || !valid) return;
+    C *gk = static_cast<C *>(d.gk);
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r) {
+        const int k = t + r * T;
+        if (k > a.K2) continue;
+        const CV<D1> hk = x[r], hc = sm.ld_raw(spad_e<E>((M - k) & (M - 1)));
+        const double ex = 0.5 * (hk.re.x + hc.re.x), ey = 0.5 * (hk.im.x - hc.im.x);
+        const double ox = 0.5 * (hk.im.x + hc.im.x), oy = 0.5 * (hc.re.x - hk.re.x);
+        const C w = __ldg(P + k);  // G = E + O conj(w)
+        const C y{ex + fma_rn(ox, w.x, oy * w.y), ey + fma_rn(oy, w.x, -(ox * w.y))};
+        const size_t i = gk_index(2 * pair + g, k, a.n1);
+        if (FLAME_IN(d.status, i, gk_len(a), kSiteBGk)) gk[i] = y;
+    }
+}
+
+// Pass C (a7..a10) on columns k2 = 2 tile + f (group f = 0, 1): the forward
+// transform of column k2 of gk and the update of its box entries; tile 0
+// sums column 0 in FP64 and finishes the step (mean mode, time, record).
+template <int LOG, int E, bool GEN> __device__ __forceinline__ void passC1_body(const FlameDesc &d, int tile) {
+    griddep_wait();
+    griddep_launch();
+    using C = double2;
+    constexpr int QE = E / 4;  // band registers: r < QE (k1 >= 0) and r >= E - QE (k1 < 0)
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const StepArgs &a = d.a;
+    constexpr int N1 = 1 << LOG, T = N1 / E, PL = plane_len_e<E>(N1);
+    const int f = threadIdx.x / T, t = threadIdx.x % T;
+    const int k2 = 2 * tile + f;
+    const bool valid = k2 <= a.K2;
+    const int ld1 = 2 * a.K1 + 1;
+    const CoefR<double> cfs = load_coef<double>(d.coef);  // derived by pass B
+    const Planes<D1> sm(reinterpret_cast<double *>(smraw) + (size_t)f * 2 * PL, PL);
+    const C *tw = static_cast<const C *>(d.tw1) + tw_offset_e<E>(LOG);
+    const C *gk = static_cast<const C *>(d.gk);
+    CV<D1> x[E];
+    double colsum = 0.0;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const size_t i = gk_index(t + r * T, k2, N1);
+        C p{0, 0};
+        if (valid && FLAME_IN(d.status, i, gk_len(a), kSiteCGk)) p = __ldg(gk + i);
+        if (k2 == 0) colsum += p.x;
+        x[r] = CV<D1>{{p.x}, {p.y}};
+    }
+    // tile 0: the FP64 sum of column 0 over group 0 (the first T <= 32
+    // threads of warp 0) by shuffles, in log2 T steps
+    if (tile == 0 && threadIdx.x < 32) {
+        const unsigned lanes = blockDim.x >= 32 ? 0xffffffffu : (1u << blockDim.x) - 1u;
+        for (int o = T >> 1; o > 0; o >>= 1) colsum += __shfl_xor_sync(lanes, colsum, o);
+    }
+    line_fft_ct<-1, LOG, E>(x, t, sm, tw, CtaBarrier{});
+    const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
+    const int stage = GEN ? d.stage : kStageEuler;
+    const EpiArgs<double> ea{cfs, a.s1, a.s2, stage, lin, nl};
+    C *col = static_cast<C *>(d.state) + (size_t)k2 * ld1 + a.K1;
+    const C *fcol = GEN && d.forcing ? static_cast<const C *>(d.forcing) + (size_t)k2 * ld1 + a.K1 : nullptr;
+    C *scol = GEN && d.save ? static_cast<C *>(d.save) + (size_t)k2 * ld1 + a.K1 : nullptr;
+    int bad = 0;
+    if (valid) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (!(r < QE || r >= E - QE)) continue;
+            const int n = t + r * T;
+            const int k1 = (r < QE) ? n : n - N1;
+            const bool in_box = (r < QE) ? (n <= a.K1) : (k1 >= -a.K1);
+            if (!in_box || (k2 == 0 && k1 < 0)) continue;  // k2 = 0, k1 < 0: the mirror of +k1
+            const long long bi = (long long)k2 * ld1 + a.K1 + k1;
+            const C ph = FLAME_IN(d.status, bi, box_len(a), kSiteCState) ? col[k1] : C{0, 0};
+            C nw;
+            update_entry<double, GEN>(d, ea, k1, k2, C{x[r].re.x, x[r].im.x}, ph, col, fcol, scol, nw, bad);
+        }
+    }
+    if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
+    const double area = record_area<GEN>(d, tile, stage, N1);
+    if (tile == 0 && threadIdx.x == 0) finish_step<GEN>(d, stage, nl, N1, colsum, area);
+}
+
 // Kernel entry points: one flame (descriptor by value) or an ensemble of
 // equal-size flames (descriptor array, flame = blockIdx.y).  LOG > 0: line
 // length 2^LOG fixed at compile time; LOG = 0: any length.
@@ -1309,28 +1551,29 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAt(FlameDesc d, int 
     passA_body<R, LOG, 16, false, true>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf, &tm);
 }
 // FP64 at short compile-time lengths (2^4 .. 2^7), E = 8 or 4 points per
-// thread: one line pair per CTA of 2^LOG / E threads (up to a warp at 128
-// points with E = 4), for the latency-bound small FP64 grids
+// thread, one line per thread group (the passes above): CTAs of 2 (A, C) or
+// 4 (B) groups of 2^LOG / E threads; pass C with the general epilogue (the
+// FP64 grids are small: the plain one would save nothing measurable)
 template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passAsd(FlameDesc d, int pf) {
-    passA_body<R, LOG, E, false>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
+    passA1_body<LOG, E>(d, blockIdx.x + d.tile0);
 }
 template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passBsd(FlameDesc d, int pf) {
-    passB_body<R, LOG, E>(d, blockIdx.x, gridDim.x, pf);
+    passB1_body<LOG, E>(d, blockIdx.x);
 }
 template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passCsd(FlameDesc d, int pf) {
-    passC_body<R, LOG, false, E>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf);
+    passC1_body<LOG, E, true>(d, blockIdx.x + d.tile0);
 }
 template <class R, int LOG, int E>
 __global__ void __launch_bounds__(128, 1) k_passCsd_n(const FlameDesc *__restrict__ ds, int pf) {
-    passC_body<R, LOG, false, E>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+    passC1_body<LOG, E, true>(ds[blockIdx.y], blockIdx.x);
 }
 template <class R, int LOG, int E>
 __global__ void __launch_bounds__(128, 1) k_passAsd_n(const FlameDesc *__restrict__ ds, int pf) {
-    passA_body<R, LOG, E, false>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+    passA1_body<LOG, E>(ds[blockIdx.y], blockIdx.x);
 }
 template <class R, int LOG, int E>
 __global__ void __launch_bounds__(128, 1) k_passBsd_n(const FlameDesc *__restrict__ ds, int pf) {
-    passB_body<R, LOG, E>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+    passB1_body<LOG, E>(ds[blockIdx.y], blockIdx.x);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(FlameDesc d, int pf) {

@@ -284,6 +284,16 @@ template <class R, int E> static Geom geom_small_fp64(int logn, int nlines, size
     g.smem = 2 * (size_t)plane_len_e<E>(1 << logn) * sizeof(typename VecOf<R>::type) + extra;
     return g;
 }
+// CTA of the one-line FP64 short kernels (k_passAsd/Bsd/Csd): `groups` line
+// groups of 2^logn / E threads, each with its own exchange planes, and
+// `extra` bytes more (pass B's parked g of two rows); one CTA per unit
+template <class R, int E> static Geom geom_short1(int logn, int units, int groups, size_t extra) {
+    Geom g;
+    g.threads = groups * ((1 << logn) / E);
+    g.blocks = units;
+    g.smem = (size_t)groups * 2 * plane_len_e<E>(1 << logn) * sizeof(double) + extra;
+    return g;
+}
 // calls f(integral_constant<E>) with the chosen points per thread
 template <class F> static void with_fp64_points(F &&f) {
     if (fp64_points() == 4) f(std::integral_constant<int, 4>{});
@@ -296,7 +306,7 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_small_fp64<R, E>(d.a.logn1, d.a.K2 + 1, 0);
+            const Geom g = geom_short1<R, E>(d.a.logn1, d.a.K2 + 1, 2, 0);
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
@@ -367,7 +377,7 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_small_fp64<R, E>(d.a.logm, d.a.n1 / 2, (size_t)(1 << d.a.logm) * sizeof(typename VecOf<R>::c));
+            const Geom g = geom_short1<R, E>(d.a.logm, d.a.n1 / 2, 4, (size_t)4 * (1 << d.a.logm) * sizeof(double));
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logm == L) err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
@@ -457,7 +467,7 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_small_fp64<R, E>(d.a.logn1, (d.a.K2 + 2) / 2, 0);
+            const Geom g = geom_short1<R, E>(d.a.logn1, (d.a.K2 + 2) / 2, 2, 0);
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
@@ -514,7 +524,7 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_small_fp64<R, E>(a.logn1, a.K2 + 1, 0);
+            const Geom g = geom_short1<R, E>(a.logn1, a.K2 + 1, 2, 0);
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (a.logn1 == L) err = launch_cl(k_passAsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
@@ -550,7 +560,7 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_small_fp64<R, E>(a.logm, a.n1 / 2, (size_t)(1 << a.logm) * sizeof(typename VecOf<R>::c));
+            const Geom g = geom_short1<R, E>(a.logm, a.n1 / 2, 4, (size_t)4 * (1 << a.logm) * sizeof(double));
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (a.logm == L) err = launch_cl(k_passBsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
@@ -583,7 +593,7 @@ cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_small_fp64<R, E>(a.logn1, (a.K2 + 2) / 2, 0);
+            const Geom g = geom_short1<R, E>(a.logn1, (a.K2 + 2) / 2, 2, 0);
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (a.logn1 == L) err = launch_cl(k_passCsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
