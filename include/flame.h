@@ -103,7 +103,8 @@ typedef struct flame_ctx *flame_t;
  * hint only (results are identical either way).  Environment: FLAME_AUTOTUNE=0
  * keeps the default kernel variants, FLAME_FORCE_VARIANTS=a,b fixes them,
  * FLAME_FUSE=0 keeps the column passes of consecutive steps separate,
- * FLAME_BATCH_TMA=1 lets flame_step_batch use the tensor-store variants. */
+ * FLAME_BATCH_TMA=1 lets flame_step_batch use the tensor-store variants,
+ * FLAME_TUNE_CACHE=path keeps the autotuner's choices in a JSON file. */
 flame_status flame_create(const flame_params *params, flame_t *out);
 
 /* Destroys a handle (NULL is accepted).  Synchronises the device. */
@@ -116,9 +117,13 @@ flame_status flame_get_params(flame_t h, flame_params *out);
  * N1, N2/2 in 256..4096 are timed once per grid, precision and device at
  * creation, FLAME_AUTOTUNE=0 disables it): pass A 0 = cluster write-out
  * through distributed shared memory, 1 = direct stores, 2 = 8 points per
- * thread with the cluster write-out, 3 = write-out by tensor (TMA) stores;
- * pass B 0 = 16 points per thread, 1 = 8 points per thread, 2 = 16 points
- * per thread with the write-out by tensor stores.  EINVAL on null pointers. */
+ * thread with the cluster write-out, 3 = write-out by tensor (TMA) stores,
+ * 4 = one line per thread group (N1 <= 2048; pass C then takes the same
+ * form); pass B 0 = 16 points per thread, 1 = 8 points per thread, 2 = 16
+ * points per thread with the write-out by tensor stores, 3 = one line per
+ * thread group (N2/2 <= 2048).  flame_step_batch takes the fastest variants
+ * other than the one-line ones (an ensemble fills the GPU without them),
+ * unless FLAME_FORCE_VARIANTS fixes the variants.  EINVAL on null pointers. */
 flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant);
 
 /* *enabled = 1 when flame_step with nsteps > 1 runs the column pass of each
@@ -295,7 +300,9 @@ flame_status flame_step_pass(flame_t h, int pass, void *state, double *mean_mode
  * descriptors asynchronously on `stream` (from a pinned staging buffer of
  * the first handle); only growing the first handle's descriptor buffers
  * synchronises that stream.  Results equal nflames separate flame_step
- * calls.  hs, states, mean_modes and ts are HOST arrays of nflames entries
+ * calls (the same bits where the flame and its size class run the same
+ * kernel variants; where the autotuner gave a small grid's single flame the
+ * one-line variants, to FP32 rounding).  hs, states, mean_modes and ts are HOST arrays of nflames entries
  * (device pointers).  Calls with the same first handle must be ordered
  * (one stream). */
 flame_status flame_step_batch(const flame_t *hs, void *const *states,

@@ -54,13 +54,23 @@ __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ double2 vbc(double s) { return make_double2(s, s); }
 __device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
 
-// One line per thread in FP64 (the short-line FP64 step kernels): a V of one
-// double, so that the two lines of a pair run in different warps.  GB300's
+// One line per thread (the one-line step kernels): a V of one double or one
+// float, so that the two lines of a pair run in different warps.  GB300's
 // FP64 units serve each SM sub-partition separately, and a line pair per
-// warp leaves the other sub-partitions' units idle.
+// warp leaves the other sub-partitions' units idle; small FP32 grids have
+// too few line pairs to fill the SMs' warp slots.
 struct D1 {
     double x;
 };
+struct F1 {
+    float x;
+};
+__device__ __forceinline__ F1 vneg(F1 a) { return {-a.x}; }
+__device__ __forceinline__ F1 vadd(F1 a, F1 b) { return {a.x + b.x}; }
+__device__ __forceinline__ F1 vsub(F1 a, F1 b) { return {a.x - b.x}; }
+__device__ __forceinline__ F1 vmul(F1 a, F1 b) { return {a.x * b.x}; }
+__device__ __forceinline__ F1 vfma(F1 a, F1 b, F1 c) { return {fmaf(a.x, b.x, c.x)}; }
+__device__ __forceinline__ F1 vzero(F1) { return {0.f}; }
 __device__ __forceinline__ D1 vneg(D1 a) { return {-a.x}; }
 __device__ __forceinline__ D1 vadd(D1 a, D1 b) { return {a.x + b.x}; }
 __device__ __forceinline__ D1 vsub(D1 a, D1 b) { return {a.x - b.x}; }
@@ -71,6 +81,11 @@ __device__ __forceinline__ D1 vzero(D1) { return {0.0}; }
 __device__ __forceinline__ float2 vbc_as(float s, float2) { return make_float2(s, s); }
 __device__ __forceinline__ double2 vbc_as(double s, double2) { return make_double2(s, s); }
 __device__ __forceinline__ D1 vbc_as(double s, D1) { return {s}; }
+__device__ __forceinline__ F1 vbc_as(float s, F1) { return {s}; }
+// the one-line V of a precision
+template <class R> struct OneOf;
+template <> struct OneOf<float> { using type = F1; };
+template <> struct OneOf<double> { using type = D1; };
 
 // Complex number whose re and im each hold the two lines (or one, for D1).
 template <class V> struct CV { V re, im; };
@@ -281,15 +296,21 @@ template <> struct Planes<double2> {
     __device__ __forceinline__ void st_raw(int j, CV<double2> v) const { re[j] = v.re; im[j] = v.im; }
     __device__ __forceinline__ CV<double2> ld_raw(int j) const { return {re[j], im[j]}; }
 };
-// One-line FP64 exchange buffer: separate re and im planes of `plane`
-// doubles each.
-template <> struct Planes<D1> {
-    double *re, *im;
-    __device__ __forceinline__ Planes(double *base, int plane) : re(base), im(base + plane) {}
-    __device__ __forceinline__ void st(int i, CV<D1> v) const { re[spad(i)] = v.re.x; im[spad(i)] = v.im.x; }
-    __device__ __forceinline__ CV<D1> ld(int i) const { return {{re[spad(i)]}, {im[spad(i)]}}; }
-    __device__ __forceinline__ void st_raw(int j, CV<D1> v) const { re[j] = v.re.x; im[j] = v.im.x; }
-    __device__ __forceinline__ CV<D1> ld_raw(int j) const { return {{re[j]}, {im[j]}}; }
+// One-line exchange buffer: separate re and im planes of `plane` reals each.
+template <class V1> struct Planes1 {
+    using Real = decltype(V1::x);
+    Real *re, *im;
+    __device__ __forceinline__ Planes1(Real *base, int plane) : re(base), im(base + plane) {}
+    __device__ __forceinline__ void st(int i, CV<V1> v) const { re[spad(i)] = v.re.x; im[spad(i)] = v.im.x; }
+    __device__ __forceinline__ CV<V1> ld(int i) const { return {{re[spad(i)]}, {im[spad(i)]}}; }
+    __device__ __forceinline__ void st_raw(int j, CV<V1> v) const { re[j] = v.re.x; im[j] = v.im.x; }
+    __device__ __forceinline__ CV<V1> ld_raw(int j) const { return {{re[j]}, {im[j]}}; }
+};
+template <> struct Planes<D1> : Planes1<D1> {
+    using Planes1<D1>::Planes1;
+};
+template <> struct Planes<F1> : Planes1<F1> {
+    using Planes1<F1>::Planes1;
 };
 // Exchange buffer of a group: `base` points at 2 * plane_len(n) V slots.
 __device__ __forceinline__ Planes<float2> make_planes(float2 *base, int n) { return Planes<float2>(base); }

@@ -188,6 +188,10 @@ struct flame_ctx {
     std::vector<AdjGraph> adj_graphs;
     // kernel variants picked by the autotuner for passes A and B
     int var_a = 0, var_b = 0;
+    // the variants the grouped (ensemble) launches of this grid take: the
+    // fastest two-line ones (an ensemble fills the GPU without the one-line
+    // kernels, which measured slower there)
+    int var_a_bat = 0, var_b_bat = 0;
     // tensor map of uv for the tensor-store variant of pass A (FP32)
     CUtensorMap uv_map, gk_map;  // tensor maps of uv and gk for the tensor-store variants (FP32)
     bool has_uv_map = false, has_gk_map = false;
@@ -274,6 +278,7 @@ FlameDesc make_desc(flame_ctx *h, void *state, double *mean, double *t) {
     d.forcing0 = h->forcing0;
     d.rec = h->rec;
     d.rec_cap = h->rec_cap;
+    d.onec = h->var_a == flame::kVariantOneLine;
     return d;
 }
 
@@ -436,12 +441,23 @@ void setup_l2_window(flame_ctx *h, size_t state_bytes) {
 // precision, device) on scratch buffers, and the fastest is kept for the
 // process.  FLAME_AUTOTUNE=0 keeps the default shapes.
 using TuneKey = std::tuple<int, int, int, int, int, int>;
-std::map<TuneKey, std::tuple<int, int, bool>> g_tune;
+// the autotuner's choice for one grid
+struct TuneChoice {
+    int a, b, fuse, a_bat, b_bat;
+};
+std::map<TuneKey, TuneChoice> g_tune;
 std::mutex g_tune_mu;
+
+// two-line stand-ins of the one-line variants (for the grouped launches when
+// only the single-flame choice is known)
+int two_line_a(int v) { return v == flame::kVariantOneLine ? flame::kVariantDirect : v; }
+int two_line_b(int v) { return v == flame::kVariantOneLineB ? flame::kVariantDefault : v; }
 
 // Autotuner cache file (FLAME_TUNE_CACHE=path): a flat JSON object mapping
 // "<GPU name>|<N1>x<N2>|<K1>,<K2>|<precision>" to [pass A variant, pass B
-// variant, fused column passes (0/1)].  A handle created with a key that the
+// variant, fused column passes (0/1), pass A and pass B variants of the
+// grouped launches] (an entry of the first three alone is read too).  A
+// handle created with a key that the
 // file holds takes its choice without timing anything; a new choice is added
 // to the file (rewritten through a temporary file and a rename, so that a
 // reader never sees half a file).  Entries of other keys are kept.
@@ -459,10 +475,10 @@ std::string tune_file_key(const flame_ctx *h) {
     return buf;
 }
 
-// Parses the cache file into key -> (a, b, fuse); a malformed file reads as
-// empty (it is then rewritten with the entries this process adds).
-std::map<std::string, std::tuple<int, int, int>> read_tune_file(const char *path) {
-    std::map<std::string, std::tuple<int, int, int>> out;
+// Parses the cache file into key -> choice; a malformed file reads as empty
+// (it is then rewritten with the entries this process adds).
+std::map<std::string, TuneChoice> read_tune_file(const char *path) {
+    std::map<std::string, TuneChoice> out;
     FILE *f = fopen(path, "rb");
     if (!f) return out;
     std::string s;
@@ -489,10 +505,15 @@ std::map<std::string, std::tuple<int, int, int>> read_tune_file(const char *path
         if (i >= s.size() || s[i] != ':') return {};
         ++i;
         skip();
-        int a = 0, b = 0, fu = 0, used = 0;
-        if (sscanf(s.c_str() + i, "[ %d , %d , %d ]%n", &a, &b, &fu, &used) != 3 || used == 0) return {};
+        int a = 0, b = 0, fu = 0, ab = 0, bb = 0, used = 0;
+        if (sscanf(s.c_str() + i, "[ %d , %d , %d , %d , %d ]%n", &a, &b, &fu, &ab, &bb, &used) == 5 && used > 0) {
+            out[key] = TuneChoice{a, b, fu, ab, bb};
+        } else {
+            used = 0;
+            if (sscanf(s.c_str() + i, "[ %d , %d , %d ]%n", &a, &b, &fu, &used) != 3 || used == 0) return {};
+            out[key] = TuneChoice{a, b, fu, two_line_a(a), two_line_b(b)};
+        }
         i += (size_t)used;
-        out[key] = std::make_tuple(a, b, fu);
         skip();
         if (i < s.size() && s[i] == ',') {
             ++i;
@@ -505,15 +526,15 @@ std::map<std::string, std::tuple<int, int, int>> read_tune_file(const char *path
     return out;
 }
 
-void write_tune_file(const char *path, const std::map<std::string, std::tuple<int, int, int>> &m) {
+void write_tune_file(const char *path, const std::map<std::string, TuneChoice> &m) {
     const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
     FILE *f = fopen(tmp.c_str(), "wb");
     if (!f) return;  // the cache is optional
     fputs("{\n", f);
     size_t k = 0;
     for (const auto &kv : m)
-        fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), std::get<0>(kv.second), std::get<1>(kv.second),
-                std::get<2>(kv.second), ++k < m.size() ? "," : "");
+        fprintf(f, "  \"%s\": [%d, %d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second.a, kv.second.b, kv.second.fuse,
+                kv.second.a_bat, kv.second.b_bat, ++k < m.size() ? "," : "");
     fputs("}\n", f);
     const bool ok = fclose(f) == 0;
     if (!ok || rename(tmp.c_str(), path) != 0) remove(tmp.c_str());
@@ -524,7 +545,10 @@ void write_tune_file(const char *path, const std::map<std::string, std::tuple<in
 bool fuse_allowed(const flame_ctx *h) {
     const char *env = getenv("FLAME_FUSE");
     if (env && strcmp(env, "0") == 0) return false;
-    return h->p.prec == FLAME_FP32_MIXED && h->has_uv_map && h->logn1 >= 8 && h->logn1 <= 12;
+    // (not with the one-line column passes: the fused pass is a two-line
+    // kernel, and fused and separate steps must give the same bits)
+    return h->p.prec == FLAME_FP32_MIXED && h->has_uv_map && h->logn1 >= 8 && h->logn1 <= 12 &&
+           h->var_a != flame::kVariantOneLine;
 }
 
 flame_status autotune(flame_ctx *h) {
@@ -533,10 +557,17 @@ flame_status autotune(flame_ctx *h) {
     if (force) {
         int va = 0, vb = 0;
         if (sscanf(force, "%d,%d", &va, &vb) == 2) {
-            h->var_a = va == 3 ? flame::kVariantTma
+            h->var_a = va == 4   ? flame::kVariantOneLine
+                       : va == 3 ? flame::kVariantTma
                        : va == 2 ? flame::kVariantRadix8A
-                       : va ? flame::kVariantDirect : flame::kVariantDefault;
-            h->var_b = vb == 2 ? flame::kVariantTmaB : vb ? flame::kVariantRadix8 : flame::kVariantDefault;
+                       : va      ? flame::kVariantDirect
+                                 : flame::kVariantDefault;
+            h->var_b = vb == 3   ? flame::kVariantOneLineB
+                       : vb == 2 ? flame::kVariantTmaB
+                       : vb      ? flame::kVariantRadix8
+                                 : flame::kVariantDefault;
+            h->var_a_bat = h->var_a;  // forced: the grouped launches take them too
+            h->var_b_bat = h->var_b;
             h->fuse = fuse_allowed(h);
             return FLAME_OK;
         }
@@ -553,9 +584,11 @@ flame_status autotune(flame_ctx *h) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            h->var_a = std::get<0>(it->second);
-            h->var_b = std::get<1>(it->second);
-            h->fuse = std::get<2>(it->second) && fuse_allowed(h);
+            h->var_a = it->second.a;
+            h->var_b = it->second.b;
+            h->var_a_bat = it->second.a_bat;
+            h->var_b_bat = it->second.b_bat;
+            h->fuse = it->second.fuse && fuse_allowed(h);
             return FLAME_OK;
         }
     }
@@ -566,13 +599,17 @@ flame_status autotune(flame_ctx *h) {
         const auto m = read_tune_file(cache_path);
         auto it = m.find(fkey);
         if (it != m.end()) {
-            h->var_a = std::get<0>(it->second);
-            h->var_b = std::get<1>(it->second);
-            h->fuse = std::get<2>(it->second) != 0 && fuse_allowed(h);
+            h->var_a = it->second.a;
+            h->var_b = it->second.b;
+            h->var_a_bat = it->second.a_bat;
+            h->var_b_bat = it->second.b_bat;
             // a variant the handle cannot run (no tensor map) falls back to the default shape
             if (h->var_a == flame::kVariantTma && !h->has_uv_map) h->var_a = flame::kVariantDefault;
             if (h->var_b == flame::kVariantTmaB && !h->has_gk_map) h->var_b = flame::kVariantDefault;
-            g_tune[key] = std::make_tuple(h->var_a, h->var_b, h->fuse);
+            if (h->var_a_bat == flame::kVariantTma && !h->has_uv_map) h->var_a_bat = flame::kVariantDefault;
+            if (h->var_b_bat == flame::kVariantTmaB && !h->has_gk_map) h->var_b_bat = flame::kVariantDefault;
+            h->fuse = it->second.fuse != 0 && fuse_allowed(h);
+            g_tune[key] = TuneChoice{h->var_a, h->var_b, h->fuse ? 1 : 0, h->var_a_bat, h->var_b_bat};
             return FLAME_OK;
         }
     }
@@ -596,8 +633,8 @@ flame_status autotune(flame_ctx *h) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(sc, init, sizeof init, cudaMemcpyHostToDevice, h->cap);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const FlameDesc d = make_desc(h, st, sc, sc + 1);
-    // pass 0: A, 1: B, 2: C then A (variant), 3: C fused with A
+    FlameDesc d = make_desc(h, st, sc, sc + 1);
+    // pass 0: A, 1: B, 2: C then A (variant, with its pass C), 3: C fused with A
     auto time_it = [&](int pass, int variant, float *ms) -> cudaError_t {
         cudaError_t r = cudaSuccess;
         float total = 0.f;
@@ -607,6 +644,7 @@ flame_status autotune(flame_ctx *h) {
                 if (pass == 0) r = Ops<float>::passA(d, h->cap, variant, h->map());
                 else if (pass == 1) r = Ops<float>::passB(d, h->cap, variant, h->gmap());
                 else if (pass == 2) {
+                    d.onec = variant == flame::kVariantOneLine;
                     r = Ops<float>::passC(d, h->cap);
                     if (r == cudaSuccess) r = Ops<float>::passA(d, h->cap, variant, h->map());
                 } else {
@@ -622,25 +660,39 @@ flame_status autotune(flame_ctx *h) {
         *ms = total / 3.f;
         return r;
     };
-    const int avars[4] = {flame::kVariantDefault, flame::kVariantDirect, flame::kVariantRadix8A, flame::kVariantTma};
-    const int bvars[3] = {flame::kVariantDefault, flame::kVariantRadix8, flame::kVariantTmaB};
-    float best_a = 1e30f, best_b = 1e30f;
+    // pass A variants are timed with their pass C (the one-line pass A
+    // brings the one-line pass C)
+    const int avars[5] = {flame::kVariantDefault, flame::kVariantDirect, flame::kVariantRadix8A, flame::kVariantTma,
+                          flame::kVariantOneLine};
+    const int bvars[4] = {flame::kVariantDefault, flame::kVariantRadix8, flame::kVariantTmaB, flame::kVariantOneLineB};
+    float best_a = 1e30f, best_b = 1e30f, best_a2 = 1e30f, best_b2 = 1e30f;
     for (int v : avars) {
         if (v == flame::kVariantTma && !h->has_uv_map) continue;
+        if (v == flame::kVariantOneLine && h->logn1 > 11) continue;
         float ms = 0;
-        if (e == cudaSuccess) e = time_it(0, v, &ms);
+        if (e == cudaSuccess) e = time_it(2, v, &ms);
         if (e == cudaSuccess && ms < best_a) {
             best_a = ms;
             h->var_a = v;
         }
+        if (e == cudaSuccess && v != flame::kVariantOneLine && ms < best_a2) {
+            best_a2 = ms;
+            h->var_a_bat = v;
+        }
     }
+    d.onec = h->var_a == flame::kVariantOneLine;
     for (int v : bvars) {
         if (v == flame::kVariantTmaB && !h->has_gk_map) continue;
+        if (v == flame::kVariantOneLineB && h->logm > 11) continue;
         float ms = 0;
         if (e == cudaSuccess) e = time_it(1, v, &ms);
         if (e == cudaSuccess && ms < best_b) {
             best_b = ms;
             h->var_b = v;
+        }
+        if (e == cudaSuccess && v != flame::kVariantOneLineB && ms < best_b2) {
+            best_b2 = ms;
+            h->var_b_bat = v;
         }
     }
     // Fused or separate column passes: each way, 4 steps captured as one CUDA
@@ -677,10 +729,10 @@ flame_status autotune(flame_ctx *h) {
     cleanup();
     if (e != cudaSuccess) return fail(FLAME_ECUDA, "autotune: %s", cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = std::make_tuple(h->var_a, h->var_b, h->fuse);
+    g_tune[key] = TuneChoice{h->var_a, h->var_b, h->fuse ? 1 : 0, h->var_a_bat, h->var_b_bat};
     if (!fkey.empty()) {
         auto m = read_tune_file(cache_path);
-        m[fkey] = std::make_tuple(h->var_a, h->var_b, h->fuse ? 1 : 0);
+        m[fkey] = g_tune[key];
         write_tune_file(cache_path, m);
     }
     return FLAME_OK;
@@ -1253,14 +1305,14 @@ flame_status flame_step_batch(const flame_t *hs, void *const *states, double *co
         const flame_ctx *hc = class_handle[ci];
         const CUtensorMap *um = class_maps[ci] ? dmaps + rg.first : nullptr;
         const CUtensorMap *gm = class_maps[ci] ? dmaps + flat.size() + rg.first : nullptr;
-        const int va = force_a >= 0 ? force_a : hc->var_a, vb = force_b >= 0 ? force_b : hc->var_b;
+        const int va = force_a >= 0 ? force_a : hc->var_a_bat, vb = force_b >= 0 ? force_b : hc->var_b_bat;
         if (h0->p.prec == FLAME_FP64)
             return pass == 0 ? Ops<double>::passA_batch(d, nf, a, q, va)
                  : pass == 1 ? Ops<double>::passB_batch(d, nf, a, q, vb)
                              : Ops<double>::passC_batch(d, nf, a, q);
         return pass == 0 ? Ops<float>::passA_batch(d, nf, a, q, va, um)
              : pass == 1 ? Ops<float>::passB_batch(d, nf, a, q, vb, gm)
-                         : Ops<float>::passC_batch(d, nf, a, q);
+                         : Ops<float>::passC_batch(d, nf, a, q, va == flame::kVariantOneLine);
     };
     // n steps of every flame.  In one stream: per step and pass, one grouped
     // launch per size class.  With FLAME_BATCH_STREAMS=1 the capture forks

@@ -5,5 +5,5 @@
 namespace flame {
 template cudaError_t Ops<float>::passC(const FlameDesc &, cudaStream_t);
 template cudaError_t Ops<float>::passCA(const FlameDesc &, cudaStream_t, const CUtensorMap *);
-template cudaError_t Ops<float>::passC_batch(const FlameDesc *, int, const StepArgs &, cudaStream_t);
+template cudaError_t Ops<float>::passC_batch(const FlameDesc *, int, const StepArgs &, cudaStream_t, bool);
 }  // namespace flame

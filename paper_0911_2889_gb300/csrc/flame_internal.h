@@ -66,6 +66,8 @@ constexpr int kVariantRadix8 = 1;   // pass B: 8 points per thread, 512-thread C
 constexpr int kVariantRadix8A = 2;  // pass A: 8 points per thread, cluster write-out
 constexpr int kVariantTma = 3;      // pass A: column written by tensor stores (FP32)
 constexpr int kVariantTmaB = 2;     // pass B: row pair written by tensor stores (FP32)
+constexpr int kVariantOneLine = 4;  // pass A (and with it pass C): one line per thread group (FP32, 2^8..2^11)
+constexpr int kVariantOneLineB = 3; // pass B: one line per thread group (FP32, 2^8..2^11)
 
 // Plain-old-data arguments of the step kernels.
 struct StepArgs {
@@ -130,6 +132,9 @@ struct FlameDesc {
     // a launch over part of the tiles (pass A and C of one flame): tiles
     // [tile0, tile0 + tiles) of the full grid; tiles = 0: all
     int tile0, tiles;
+    // pass C with one line per thread group (set with pass A's one-line
+    // variant; FP32 column lengths 2^8 .. 2^11)
+    int onec;
     // L2 persisting window over the state for the launches of passes A and
     // C (a launch attribute, not read by the kernels); bytes = 0: none
     L2Window l2_state;
@@ -204,7 +209,8 @@ template <class R> struct Ops {
                                    int variant = 0, const CUtensorMap *maps = nullptr);
     static cudaError_t passB_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
                                    int variant = 0, const CUtensorMap *maps = nullptr);
-    static cudaError_t passC_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s);
+    static cudaError_t passC_batch(const FlameDesc *descs, int nflames, const StepArgs &a, cudaStream_t s,
+                                   bool one_line = false);
     // Tiles (CTAs) of passes A and C: columns per pass-A tile, the tile
     // multiple a partial pass-A launch must use (clusters), column pairs per
     // pass-C tile

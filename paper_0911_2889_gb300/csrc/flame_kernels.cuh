@@ -1339,40 +1339,42 @@ __device__ __forceinline__ void passC_body(const FlameDesc &d, int tile, int nti
 }
 
 // ----------------------------------------------------------------------------
-// FP64 step passes for short lines (2^4 .. 2^7 points: the FP64 parity and
-// trajectory grids).  Each line is transformed by its own group of
-// T = 2^LOG / E threads (E = 4 or 8 points per thread, one double per
-// point: V = D1), and a CTA holds the groups of one column (pass A: the two
-// fields), one row pair (pass B: two rows x even/odd points) or one column
-// pair (pass C).  A small grid has too few line pairs to give every SM
-// sub-partition a warp; with one line per group its FP64 work spreads over
-// two to four times as many warps.
+// One-line step passes: each line is transformed by its own group of
+// T = 2^LOG / E threads (one real per point and component: V = D1 or F1),
+// and a CTA holds the groups of one column (pass A: the two fields), one
+// row pair (pass B: two rows x even/odd points) or one column pair (pass
+// C).  Used for the FP64 short lines (2^4 .. 2^7 points, E = 4 or 8: the
+// FP64 parity and trajectory grids) and, as an autotuned variant, for FP32
+// lines of 2^8 .. 2^11 points (E = 16).  A small grid has too few line
+// pairs to give every SM sub-partition a warp; with one line per group its
+// work spreads over two to four times as many warps.
 // ----------------------------------------------------------------------------
-// offset of the radix-E table (E = 8 or 4) in a line's twiddle allocation
+// offset of the radix-E table (E = 16, 8 or 4) in a line's twiddle allocation
 template <int E> __host__ __device__ constexpr int tw_offset_e(int log) {
-    return E == 8 ? tw_table_len(log, 4) : tw_table_len(log, 4) + tw_table_len(log, 3);
+    return E == 16 ? 0 : E == 8 ? tw_table_len(log, 4) : tw_table_len(log, 4) + tw_table_len(log, 3);
 }
 
 // Pass A (a1, a2) on column k2: group 0 synthesises i s1 k1 Phi (-> U), group
 // 1 synthesises Phi (-> V = i s2 k2 times it); each writes its half of the
 // (U, V) entries of the column.
-template <int LOG, int E> __device__ __forceinline__ void passA1_body(const FlameDesc &d, int k2) {
+template <class R, int LOG, int E> __device__ __forceinline__ void passA1_body(const FlameDesc &d, int k2) {
     griddep_wait();
     griddep_launch();
-    using C = double2;
+    using C = CplxT<R>;
+    using V1 = typename OneOf<R>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     const StepArgs &a = d.a;
     constexpr int N1 = 1 << LOG, T = N1 / E, PL = plane_len_e<E>(N1);
     const int f = threadIdx.x / T, t = threadIdx.x % T;
     const int ld1 = 2 * a.K1 + 1;
     const bool valid = k2 <= a.K2;
-    const Planes<D1> sm(reinterpret_cast<double *>(smraw) + (size_t)f * 2 * PL, PL);
+    const Planes<V1> sm(reinterpret_cast<R *>(smraw) + (size_t)f * 2 * PL, PL);
     const C *tw = static_cast<const C *>(d.tw1) + tw_offset_e<E>(LOG);
     const C *col = static_cast<const C *>(d.state) + (size_t)k2 * ld1 + a.K1;  // col[k1], k1 = -K1..K1
-    CV<D1> x[E];
+    CV<V1> x[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-        x[r] = CV<D1>{{0.0}, {0.0}};
+        x[r] = CV<V1>{{(R)0}, {(R)0}};
         // band rows r < E/4 (k1 = n >= 0) and r >= 3E/4 (k1 = n - N1 < 0); the rest is padding
         if (r < E / 4 || r >= 3 * E / 4) {
             const int n = t + r * T;
@@ -1381,15 +1383,15 @@ template <int LOG, int E> __device__ __forceinline__ void passA1_body(const Flam
             if (in_box && FLAME_IN(d.status, (long long)k2 * ld1 + a.K1 + k1, box_len(a), kSiteAState)) {
                 C phi = __ldg(col + k1);
                 if (k1 == 0 && k2 == 0) phi = C{0, 0};
-                const double fk = a.s1 * (double)k1;
-                x[r] = f == 0 ? CV<D1>{{-fk * phi.y}, {fk * phi.x}} : CV<D1>{{phi.x}, {phi.y}};
+                const R fk = scale1<R>(a) * (R)k1;
+                x[r] = f == 0 ? CV<V1>{{-fk * phi.y}, {fk * phi.x}} : CV<V1>{{phi.x}, {phi.y}};
             }
         }
     }
     line_fft_ct<1, LOG, E>(x, t, sm, tw, CtaBarrier{});
     if (!valid) return;
     C *uv = static_cast<C *>(d.uv);
-    const double s2k2 = a.s2 * (double)k2;
+    const R s2k2 = scale2<R>(a) * (R)k2;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const size_t i = uv_index(t + r * T, k2, a.ldk) + f;  // U, or V one slot further
@@ -1404,25 +1406,26 @@ template <int LOG, int E> __device__ __forceinline__ void passA1_body(const Flam
 // h[m] = g[2m] + i g[2m+1] of row 2p + q forward and writes G[k], k <= K2,
 // after the real-input post-processing.  Groups 2 and 3 transform zeros in
 // the forward step, so that every group meets the same barriers.
-template <int LOG, int E> __device__ __forceinline__ void passB1_body(const FlameDesc &d, int pair) {
+template <class R, int LOG, int E> __device__ __forceinline__ void passB1_body(const FlameDesc &d, int pair) {
     griddep_wait();
     griddep_launch();
-    using C = double2;
+    using C = CplxT<R>;
+    using V1 = typename OneOf<R>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     const StepArgs &a = d.a;
     constexpr int M = 1 << LOG, T = M / E, PL = plane_len_e<E>(M);
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     const int q = g >> 1, s = g & 1;
     const bool valid = pair < (a.n1 >> 1);
-    double *smd = reinterpret_cast<double *>(smraw);
-    const Planes<D1> sm(smd + (size_t)g * 2 * PL, PL);
-    double *h = smd + 8 * (size_t)PL;  // g of row 2p + q at h[2M q + j], j the grid point
+    R *smd = reinterpret_cast<R *>(smraw);
+    const Planes<V1> sm(smd + (size_t)g * 2 * PL, PL);
+    R *h = smd + 8 * (size_t)PL;  // g of row 2p + q at h[2M q + j], j the grid point
     const C *tw = static_cast<const C *>(d.twm) + tw_offset_e<E>(LOG);
     const C *P = static_cast<const C *>(d.twm) + tw_real_offset(LOG);  // exp(2 pi i k / N2), k < M
-    if (pair == 0 && threadIdx.x == 0) store_coef<double>(d.coef, a, *d.t_in, d.stage == kStageIF1);
+    if (pair == 0 && threadIdx.x == 0) store_coef<R>(d.coef, a, *d.t_in, d.stage == kStageIF1);
     const size_t base = uv_index(2 * pair + q, 0, a.ldk);  // (U, V) of k at base + 4k
     const C *src = static_cast<const C *>(d.uv) + base;
-    CV<D1> x[E];
+    CV<V1> x[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int n = t + r * T;
@@ -1438,16 +1441,16 @@ template <int LOG, int E> __device__ __forceinline__ void passB1_body(const Flam
             if (r >= E / 2) w.y = -w.y;
             z = C{fma_rn(z.x, w.x, -(z.y * w.y)), fma_rn(z.x, w.y, z.y * w.x)};
         }
-        x[r] = CV<D1>{{z.x}, {z.y}};
+        x[r] = CV<V1>{{z.x}, {z.y}};
     }
     line_fft_ct<1, LOG, E>(x, t, sm, tw, CtaBarrier{});
 #pragma unroll
-    for (int r = 0; r < E; ++r) h[2 * M * q + 2 * (t + r * T) + s] = fma(x[r].re.x, x[r].re.x, x[r].im.x * x[r].im.x);
+    for (int r = 0; r < E; ++r) h[2 * M * q + 2 * (t + r * T) + s] = fma_rn(x[r].re.x, x[r].re.x, x[r].im.x * x[r].im.x);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int m = t + r * T;
-        x[r] = g < 2 ? CV<D1>{{h[2 * M * g + 2 * m]}, {h[2 * M * g + 2 * m + 1]}} : CV<D1>{{0.0}, {0.0}};
+        x[r] = g < 2 ? CV<V1>{{h[2 * M * g + 2 * m]}, {h[2 * M * g + 2 * m + 1]}} : CV<V1>{{(R)0}, {(R)0}};
     }
     line_fft_ct<-1, LOG, E>(x, t, sm, tw, CtaBarrier{});
     __syncthreads();
@@ -1462,9 +1465,10 @@ template <int LOG, int E> __device__ __forceinline__ void passB1_body(const Flam
     for (int r = 0; r < E / 2; ++r) {
         const int k = t + r * T;
         if (k > a.K2) continue;
-        const CV<D1> hk = x[r], hc = sm.ld_raw(spad_e<E>((M - k) & (M - 1)));
-        const double ex = 0.5 * (hk.re.x + hc.re.x), ey = 0.5 * (hk.im.x - hc.im.x);
-        const double ox = 0.5 * (hk.im.x + hc.im.x), oy = 0.5 * (hc.re.x - hk.re.x);
+        const CV<V1> hk = x[r], hc = sm.ld_raw(spad_e<E>((M - k) & (M - 1)));
+        const R hf = (R)0.5;
+        const R ex = hf * (hk.re.x + hc.re.x), ey = hf * (hk.im.x - hc.im.x);
+        const R ox = hf * (hk.im.x + hc.im.x), oy = hf * (hc.re.x - hk.re.x);
         const C w = __ldg(P + k);  // G = E + O conj(w)
         const C y{ex + fma_rn(ox, w.x, oy * w.y), ey + fma_rn(oy, w.x, -(ox * w.y))};
         const size_t i = gk_index(2 * pair + g, k, a.n1);
@@ -1475,10 +1479,11 @@ template <int LOG, int E> __device__ __forceinline__ void passB1_body(const Flam
 // Pass C (a7..a10) on columns k2 = 2 tile + f (group f = 0, 1): the forward
 // transform of column k2 of gk and the update of its box entries; tile 0
 // sums column 0 in FP64 and finishes the step (mean mode, time, record).
-template <int LOG, int E, bool GEN> __device__ __forceinline__ void passC1_body(const FlameDesc &d, int tile) {
+template <class R, int LOG, int E, bool GEN> __device__ __forceinline__ void passC1_body(const FlameDesc &d, int tile) {
     griddep_wait();
     griddep_launch();
-    using C = double2;
+    using C = CplxT<R>;
+    using V1 = typename OneOf<R>::type;
     constexpr int QE = E / 4;  // band registers: r < QE (k1 >= 0) and r >= E - QE (k1 < 0)
     extern __shared__ __align__(16) unsigned char smraw[];
     const StepArgs &a = d.a;
@@ -1487,11 +1492,11 @@ template <int LOG, int E, bool GEN> __device__ __forceinline__ void passC1_body(
     const int k2 = 2 * tile + f;
     const bool valid = k2 <= a.K2;
     const int ld1 = 2 * a.K1 + 1;
-    const CoefR<double> cfs = load_coef<double>(d.coef);  // derived by pass B
-    const Planes<D1> sm(reinterpret_cast<double *>(smraw) + (size_t)f * 2 * PL, PL);
+    const CoefR<R> cfs = load_coef<R>(d.coef);  // derived by pass B
+    const Planes<V1> sm(reinterpret_cast<R *>(smraw) + (size_t)f * 2 * PL, PL);
     const C *tw = static_cast<const C *>(d.tw1) + tw_offset_e<E>(LOG);
     const C *gk = static_cast<const C *>(d.gk);
-    CV<D1> x[E];
+    CV<V1> x[E];
     double colsum = 0.0;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -1499,18 +1504,29 @@ template <int LOG, int E, bool GEN> __device__ __forceinline__ void passC1_body(
         C p{0, 0};
         if (valid && FLAME_IN(d.status, i, gk_len(a), kSiteCGk)) p = __ldg(gk + i);
         if (k2 == 0) colsum += p.x;
-        x[r] = CV<D1>{{p.x}, {p.y}};
+        x[r] = CV<V1>{{p.x}, {p.y}};
     }
-    // tile 0: the FP64 sum of column 0 over group 0 (the first T <= 32
-    // threads of warp 0) by shuffles, in log2 T steps
-    if (tile == 0 && threadIdx.x < 32) {
-        const unsigned lanes = blockDim.x >= 32 ? 0xffffffffu : (1u << blockDim.x) - 1u;
-        for (int o = T >> 1; o > 0; o >>= 1) colsum += __shfl_xor_sync(lanes, colsum, o);
+    // tile 0: the FP64 sum of column 0 over group 0 (its T threads) by
+    // shuffles within each warp, then across the group's warps
+    if (tile == 0) {
+        if constexpr (T <= 32) {
+            if (threadIdx.x < 32) {
+                const unsigned lanes = blockDim.x >= 32 ? 0xffffffffu : (1u << blockDim.x) - 1u;
+                for (int o = T >> 1; o > 0; o >>= 1) colsum += __shfl_xor_sync(lanes, colsum, o);
+            }
+        } else {
+            __shared__ double wsum[T / 32];
+            for (int o = 16; o > 0; o >>= 1) colsum += __shfl_xor_sync(0xffffffffu, colsum, o);
+            if (f == 0 && (t & 31) == 0) wsum[t >> 5] = colsum;
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int w = 1; w < T / 32; ++w) colsum += wsum[w];
+        }
     }
     line_fft_ct<-1, LOG, E>(x, t, sm, tw, CtaBarrier{});
     const bool lin = !(a.flags & kNonlinearOnly), nl = !(a.flags & kLinearOnly);
     const int stage = GEN ? d.stage : kStageEuler;
-    const EpiArgs<double> ea{cfs, a.s1, a.s2, stage, lin, nl};
+    const EpiArgs<R> ea{cfs, scale1<R>(a), scale2<R>(a), stage, lin, nl};
     C *col = static_cast<C *>(d.state) + (size_t)k2 * ld1 + a.K1;
     const C *fcol = GEN && d.forcing ? static_cast<const C *>(d.forcing) + (size_t)k2 * ld1 + a.K1 : nullptr;
     C *scol = GEN && d.save ? static_cast<C *>(d.save) + (size_t)k2 * ld1 + a.K1 : nullptr;
@@ -1526,7 +1542,7 @@ template <int LOG, int E, bool GEN> __device__ __forceinline__ void passC1_body(
             const long long bi = (long long)k2 * ld1 + a.K1 + k1;
             const C ph = FLAME_IN(d.status, bi, box_len(a), kSiteCState) ? col[k1] : C{0, 0};
             C nw;
-            update_entry<double, GEN>(d, ea, k1, k2, C{x[r].re.x, x[r].im.x}, ph, col, fcol, scol, nw, bad);
+            update_entry<R, GEN>(d, ea, k1, k2, C{x[r].re.x, x[r].im.x}, ph, col, fcol, scol, nw, bad);
         }
     }
     if (bad) atomicOr(d.status, 1 << kStatusNonfinite);
@@ -1550,30 +1566,34 @@ template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passAt(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
     passA_body<R, LOG, 16, false, true>(d, blockIdx.x + d.tile0, gridDim.x + d.tile0, pf, &tm);
 }
-// FP64 at short compile-time lengths (2^4 .. 2^7), E = 8 or 4 points per
-// thread, one line per thread group (the passes above): CTAs of 2 (A, C) or
-// 4 (B) groups of 2^LOG / E threads; pass C with the general epilogue (the
-// FP64 grids are small: the plain one would save nothing measurable)
-template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passAsd(FlameDesc d, int pf) {
-    passA1_body<LOG, E>(d, blockIdx.x + d.tile0);
-}
-template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passBsd(FlameDesc d, int pf) {
-    passB1_body<LOG, E>(d, blockIdx.x);
-}
-template <class R, int LOG, int E> __global__ void __launch_bounds__(128, 1) k_passCsd(FlameDesc d, int pf) {
-    passC1_body<LOG, E, true>(d, blockIdx.x + d.tile0);
+// One line per thread group (the passes above): CTAs of 2 (A, C) or 4 (B)
+// groups of 2^LOG / E threads; pass C with the general epilogue (these
+// kernels serve small grids, where the plain one would save nothing
+// measurable).  MAXT: the largest CTA of the precision's line lengths.
+template <class R> constexpr int kOneLineThreads = sizeof(R) == 8 ? 128 : 512;
+template <class R, int LOG, int E>
+__global__ void __launch_bounds__(kOneLineThreads<R>, 1) k_passA1(FlameDesc d, int pf) {
+    passA1_body<R, LOG, E>(d, blockIdx.x + d.tile0);
 }
 template <class R, int LOG, int E>
-__global__ void __launch_bounds__(128, 1) k_passCsd_n(const FlameDesc *__restrict__ ds, int pf) {
-    passC1_body<LOG, E, true>(ds[blockIdx.y], blockIdx.x);
+__global__ void __launch_bounds__(kOneLineThreads<R>, 1) k_passB1(FlameDesc d, int pf) {
+    passB1_body<R, LOG, E>(d, blockIdx.x);
 }
 template <class R, int LOG, int E>
-__global__ void __launch_bounds__(128, 1) k_passAsd_n(const FlameDesc *__restrict__ ds, int pf) {
-    passA1_body<LOG, E>(ds[blockIdx.y], blockIdx.x);
+__global__ void __launch_bounds__(kOneLineThreads<R>, 1) k_passC1(FlameDesc d, int pf) {
+    passC1_body<R, LOG, E, true>(d, blockIdx.x + d.tile0);
 }
 template <class R, int LOG, int E>
-__global__ void __launch_bounds__(128, 1) k_passBsd_n(const FlameDesc *__restrict__ ds, int pf) {
-    passB1_body<LOG, E>(ds[blockIdx.y], blockIdx.x);
+__global__ void __launch_bounds__(kOneLineThreads<R>, 1) k_passC1_n(const FlameDesc *__restrict__ ds, int pf) {
+    passC1_body<R, LOG, E, true>(ds[blockIdx.y], blockIdx.x);
+}
+template <class R, int LOG, int E>
+__global__ void __launch_bounds__(kOneLineThreads<R>, 1) k_passA1_n(const FlameDesc *__restrict__ ds, int pf) {
+    passA1_body<R, LOG, E>(ds[blockIdx.y], blockIdx.x);
+}
+template <class R, int LOG, int E>
+__global__ void __launch_bounds__(kOneLineThreads<R>, 1) k_passB1_n(const FlameDesc *__restrict__ ds, int pf) {
+    passB1_body<R, LOG, E>(ds[blockIdx.y], blockIdx.x);
 }
 // 8 points per thread, 512-thread CTAs (compile-time FP32 lengths)
 template <class R, int LOG> __global__ void __launch_bounds__(512, 2) k_passA8(FlameDesc d, int pf) {

@@ -284,16 +284,18 @@ template <class R, int E> static Geom geom_small_fp64(int logn, int nlines, size
     g.smem = 2 * (size_t)plane_len_e<E>(1 << logn) * sizeof(typename VecOf<R>::type) + extra;
     return g;
 }
-// CTA of the one-line FP64 short kernels (k_passAsd/Bsd/Csd): `groups` line
+// CTA of the one-line kernels (k_passA1/B1/C1): `groups` line
 // groups of 2^logn / E threads, each with its own exchange planes, and
 // `extra` bytes more (pass B's parked g of two rows); one CTA per unit
 template <class R, int E> static Geom geom_short1(int logn, int units, int groups, size_t extra) {
     Geom g;
     g.threads = groups * ((1 << logn) / E);
     g.blocks = units;
-    g.smem = (size_t)groups * 2 * plane_len_e<E>(1 << logn) * sizeof(double) + extra;
+    g.smem = (size_t)groups * 2 * plane_len_e<E>(1 << logn) * sizeof(R) + extra;
     return g;
 }
+// FP32 lines with one-line kernels (E = 16): 2^8 .. 2^11 points
+template <class R> static bool one_line_fp32(int logn) { return sizeof(R) == 4 && logn >= 8 && logn <= 11; }
 // calls f(integral_constant<E>) with the chosen points per thread
 template <class F> static void with_fp64_points(F &&f) {
     if (fp64_points() == 4) f(std::integral_constant<int, 4>{});
@@ -310,8 +312,19 @@ cudaError_t Ops<R>::passA(const FlameDesc &d, cudaStream_t s, int variant, const
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
-                    err = launch_s(d.l2_state, k_passAsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, 0);
+                    err = launch_s(d.l2_state, k_passA1<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s, 1, d, 0);
             });
+        });
+        return err;
+    }
+    if (variant == kVariantOneLine && one_line_fp32<R>(d.a.logn1)) {
+        cudaError_t err = cudaErrorInvalidValue;
+        const Geom g = geom_short1<R, 16>(d.a.logn1, d.a.K2 + 1, 2, 0);
+        static_for<8, 12>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (d.a.logn1 == L)
+                err = launch_s(d.l2_state, k_passA1<R, L, 16>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s,
+                               1, d, 0);
         });
         return err;
     }
@@ -377,11 +390,21 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_short1<R, E>(d.a.logm, d.a.n1 / 2, 4, (size_t)4 * (1 << d.a.logm) * sizeof(double));
+            const Geom g = geom_short1<R, E>(d.a.logm, d.a.n1 / 2, 4, (size_t)4 * (1 << d.a.logm) * sizeof(R));
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
-                if (d.a.logm == L) err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBsd<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
+                if (d.a.logm == L) err = launch_s(L2Window{nullptr, 0, 0.f}, k_passB1<R, L, E>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
             });
+        });
+        return err;
+    }
+    if (variant == kVariantOneLineB && one_line_fp32<R>(d.a.logm)) {
+        cudaError_t err = cudaErrorInvalidValue;
+        const Geom g = geom_short1<R, 16>(d.a.logm, d.a.n1 / 2, 4, (size_t)4 * (1 << d.a.logm) * sizeof(R));
+        static_for<8, 12>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (d.a.logm == L)
+                err = launch_s(L2Window{nullptr, 0, 0.f}, k_passB1<R, L, 16>, dim3(g.blocks), g.threads, g.smem, s, 1, d, 0);
         });
         return err;
     }
@@ -471,9 +494,20 @@ template <class R> cudaError_t Ops<R>::passC(const FlameDesc &d, cudaStream_t s)
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
                 if (d.a.logn1 == L)
-                    err = launch_s(d.l2_state, k_passCsd<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem,
+                    err = launch_s(d.l2_state, k_passC1<R, L, E>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem,
                                    s, 1, d, 0);
             });
+        });
+        return err;
+    }
+    if (d.onec && one_line_fp32<R>(d.a.logn1)) {
+        cudaError_t err = cudaErrorInvalidValue;
+        const Geom g = geom_short1<R, 16>(d.a.logn1, (d.a.K2 + 2) / 2, 2, 0);
+        static_for<8, 12>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (d.a.logn1 == L)
+                err = launch_s(d.l2_state, k_passC1<R, L, 16>, dim3(d.tiles ? d.tiles : g.blocks), g.threads, g.smem, s,
+                               1, d, 0);
         });
         return err;
     }
@@ -527,8 +561,17 @@ cudaError_t Ops<R>::passA_batch(const FlameDesc *ds, int n, const StepArgs &a, c
             const Geom g = geom_short1<R, E>(a.logn1, a.K2 + 1, 2, 0);
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
-                if (a.logn1 == L) err = launch_cl(k_passAsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+                if (a.logn1 == L) err = launch_cl(k_passA1_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
             });
+        });
+        return err;
+    }
+    if (variant == kVariantOneLine && one_line_fp32<R>(a.logn1)) {
+        cudaError_t err = cudaErrorInvalidValue;
+        const Geom g = geom_short1<R, 16>(a.logn1, a.K2 + 1, 2, 0);
+        static_for<8, 12>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (a.logn1 == L) err = launch_cl(k_passA1_n<R, L, 16>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
         });
         return err;
     }
@@ -560,11 +603,20 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
             constexpr int E = decltype(ec)::value;
-            const Geom g = geom_short1<R, E>(a.logm, a.n1 / 2, 4, (size_t)4 * (1 << a.logm) * sizeof(double));
+            const Geom g = geom_short1<R, E>(a.logm, a.n1 / 2, 4, (size_t)4 * (1 << a.logm) * sizeof(R));
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
-                if (a.logm == L) err = launch_cl(k_passBsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+                if (a.logm == L) err = launch_cl(k_passB1_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
             });
+        });
+        return err;
+    }
+    if (variant == kVariantOneLineB && one_line_fp32<R>(a.logm)) {
+        cudaError_t err = cudaErrorInvalidValue;
+        const Geom g = geom_short1<R, 16>(a.logm, a.n1 / 2, 4, (size_t)4 * (1 << a.logm) * sizeof(R));
+        static_for<8, 12>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (a.logm == L) err = launch_cl(k_passB1_n<R, L, 16>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
         });
         return err;
     }
@@ -588,7 +640,16 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
     return cudaGetLastError();
 }
 template <class R>
-cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s) {
+cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, cudaStream_t s, bool one_line) {
+    if (one_line && one_line_fp32<R>(a.logn1)) {
+        cudaError_t err = cudaErrorInvalidValue;
+        const Geom g = geom_short1<R, 16>(a.logn1, (a.K2 + 2) / 2, 2, 0);
+        static_for<8, 12>([&](auto lc) {
+            constexpr int L = decltype(lc)::value;
+            if (a.logn1 == L) err = launch_cl(k_passC1_n<R, L, 16>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+        });
+        return err;
+    }
     if constexpr (sizeof(R) == 8) if (small_fp64<R>(a.logn1)) {
         cudaError_t err = cudaErrorInvalidValue;
         with_fp64_points([&](auto ec) {
@@ -596,7 +657,7 @@ cudaError_t Ops<R>::passC_batch(const FlameDesc *ds, int n, const StepArgs &a, c
             const Geom g = geom_short1<R, E>(a.logn1, (a.K2 + 2) / 2, 2, 0);
             static_for<4, 8>([&](auto lc) {
                 constexpr int L = decltype(lc)::value;
-                if (a.logn1 == L) err = launch_cl(k_passCsd_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
+                if (a.logn1 == L) err = launch_cl(k_passC1_n<R, L, E>, dim3(g.blocks, n), g.threads, g.smem, s, 1, ds, 0);
             });
         });
         return err;
@@ -674,7 +735,7 @@ template <class R> cudaError_t Ops<R>::adj_step(const AdjDesc &d, cudaStream_t s
 // partial launch must respect (flame_step_host).
 template <class R> void Ops<R>::tiles(const StepArgs &a, int variant, int *colsA, int *quantA, int *pairsC) {
     *quantA = 1;
-    if (small_fp64<R>(a.logn1)) {
+    if (small_fp64<R>(a.logn1) || (variant == kVariantOneLine && one_line_fp32<R>(a.logn1))) {
         *colsA = 1;
         *pairsC = 1;
         return;

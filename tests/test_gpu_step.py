@@ -225,7 +225,7 @@ def test_batch_equals_individual(fl, monkeypatch, prec, branches):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("branches", ["0", "1"])
-@pytest.mark.parametrize("variants", ["3,2", "1,0", None])
+@pytest.mark.parametrize("variants", ["3,2", "1,0", "4,3", None])
 def test_batch_of_compile_time_grids_equals_individual(fl, monkeypatch, variants, branches):
     # grids with compile-time kernels: the ensemble runs the grouped kernels
     # (with per-flame tensor maps for the tensor-store variants 3 and 2)
@@ -248,15 +248,22 @@ def test_batch_of_compile_time_grids_equals_individual(fl, monkeypatch, variants
     for f, (s, m, t) in zip(fs, ref):
         f.step(s, m, t, 3)
     torch.cuda.synchronize()
-    for i in range(len(fs)):
-        assert torch.equal(ss[i], ref[i][0]), i
-        assert torch.equal(ms[i], ref[i][1]) and torch.equal(ts[i], ref[i][2])
+    for i, f in enumerate(fs):
+        if variants is not None or fl.flame_tuning(f.h)[0] != 4 and fl.flame_tuning(f.h)[1] != 3:
+            # the same kernels: the same bits
+            assert torch.equal(ss[i], ref[i][0]), i
+            assert torch.equal(ms[i], ref[i][1]) and torch.equal(ts[i], ref[i][2])
+        else:
+            # tuned one-line kernels for the single flame, two-line grouped
+            # kernels for the ensemble: equal to FP32 rounding
+            assert rel_l2(ss[i].cpu().numpy(), ref[i][0].cpu().numpy()) < 1e-6, i
+            assert abs(ms[i].item() - ref[i][1].item()) <= 1e-6 * abs(ref[i][1].item()) and torch.equal(ts[i], ref[i][2])
     for f in fs:
         f.close()
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("variants", ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2"])
+@pytest.mark.parametrize("variants", ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2", "4,3", "4,0", "0,3"])
 @pytest.mark.parametrize("shape", [(256, 512), (1024, 2048), (4096, 8192)])
 def test_every_tuned_variant_matches_oracle(fl, orc, monkeypatch, variants, shape):
     # the autotuner may pick either shape of passes A and B; each must be exact
@@ -293,8 +300,9 @@ def test_autotuner_cache_file(fl, monkeypatch, tmp_path):
     fused = fl.flame_fused_steps(f.h)
     f.close()
     d = json.loads(path.read_text())
-    assert d[key] == [1, 0, 0] and d[other] == [0, 0, 1]
-    assert d[f"{name}|256x512|61,121|fp32"] == [va, vb, int(fused)]
+    # entries: [pass A, pass B, fused, pass A and pass B of the grouped launches]
+    assert d[key] == [1, 0, 0, 1, 0] and d[other] == [0, 0, 1, 0, 0]
+    assert d[f"{name}|256x512|61,121|fp32"][:3] == [va, vb, int(fused)]
     # a malformed file is ignored and rewritten
     path.write_text("{not json")
     f = fl.Flame(256, 512, prec="fp32", K1=62, K2=122)
@@ -308,7 +316,7 @@ def test_autotuner_choice_is_valid_and_cached(fl, monkeypatch):
     f1 = fl.Flame(512, 1024, prec="fp32")
     f2 = fl.Flame(512, 1024, prec="fp32")
     v1, v2 = fl.flame_tuning(f1.h), fl.flame_tuning(f2.h)
-    assert v1 == v2 and v1[0] in (0, 1, 2, 3) and v1[1] in (0, 1, 2)
+    assert v1 == v2 and v1[0] in (0, 1, 2, 3, 4) and v1[1] in (0, 1, 2, 3)
     f1.close()
     f2.close()
 
