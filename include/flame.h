@@ -121,7 +121,8 @@ flame_status flame_get_params(flame_t h, flame_params *out);
  * 4 = one line per thread group (N1 <= 2048; pass C then takes the same
  * form); pass B 0 = 16 points per thread, 1 = 8 points per thread, 2 = 16
  * points per thread with the write-out by tensor stores, 3 = one line per
- * thread group (N2/2 <= 2048).  flame_step_batch takes the fastest variants
+ * thread group (N2/2 <= 2048), 4 = as 2 with, for N2 = 8192, one exchange
+ * of each row transform inside a warp (other N2: as 2).  flame_step_batch takes the fastest variants
  * other than the one-line ones (an ensemble fills the GPU without them),
  * unless FLAME_FORCE_VARIANTS fixes the variants.  EINVAL on null pointers. */
 flame_status flame_tuning(flame_t h, int *pass_a_variant, int *pass_b_variant);
@@ -183,7 +184,9 @@ flame_status flame_state_from_field(flame_t h, const void *field, void *state,
  * state: compact box (see above), in place.  mean_mode, t: one device double
  * each, in place.  nsteps >= 0 (0 is a no-op).  For nsteps > 1 the step
  * sequence is replayed from a captured CUDA graph (captured on first use per
- * (state, mean_mode, t, nsteps, forcing) binding).  Non-finite results set
+ * (state, mean_mode, t, nsteps, forcing) binding; the handle caches 8 and
+ * keeps the ones it evicts until flame_destroy, so that an eviction never
+ * waits for the device, except once every 64 evictions).  Non-finite results set
  * FLAME_ENONFINITE in the handle's device status word. */
 flame_status flame_step(flame_t h, void *state, double *mean_mode, double *t,
                         int nsteps, void *stream);

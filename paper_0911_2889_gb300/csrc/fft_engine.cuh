@@ -526,4 +526,94 @@ __device__ __forceinline__ void fft_line_s(CV<V> (&x)[16], int t, const Planes<V
     line_fft_ct<DIR, LOG, 16>(x, t, sm, tw, CtaBarrier{}, TwShared<C>{stw, stw + 240});
 }
 
+// 4096-point transform of a line pair over T = 256 threads with one of its
+// two exchanges inside a warp.  With n = 256 a + 16 b + c and
+// k = k_a + 16 k_b + 256 k_c (a, b, c, k_* < 16),
+//   W^(n k) = W16^(a k_a) W4096^((16 b + c) k_a) W16^(b k_b) W256^(c k_b) W16^(c k_c),
+// so the line is three radix-16 passes (over a, b, c) with the twiddles
+// W4096^((16 b + c) k_a) and W256^(c k_b) between them.  Thread t = 16 hi + lo
+// (hi = t / 16, lo = t mod 16) holds 16 values of one digit in registers and
+// the other two digits by its index:
+//   NAT_IN  (natural in, digit-swapped out):
+//     pass 1 (b, c) = (hi, lo), input n = t + 256 r;
+//     pass 2 (k_a, c) = (hi, lo): the first exchange crosses warps;
+//     pass 3 (k_a, k_b) = (hi, lo): the second stays within the 16 threads of
+//     one hi, output k = swap(t) + 256 r, swap(t) = 16 lo + hi.
+//   !NAT_IN (digit-swapped in, natural out):
+//     pass 1 (b, c) = (lo, hi), input n = swap(t) + 256 r;
+//     pass 2 (k_a, c) = (lo, hi): the first exchange stays within the 16
+//     threads of one hi;
+//     pass 3 (k_a, k_b) = (lo, hi): the second crosses warps, output
+//     k = t + 256 r.
+// An inverse transform with NAT_IN followed, after pointwise work, by a
+// forward one without it needs no exchange between the two and gives
+// natural order at both ends.  A warp-local exchange reads and writes only
+// the slots [256 hi, 256 hi + 256) (before padding) of its own 16 threads,
+// so it is ordered by __syncwarp; the cross-warp one by the CTA barrier.
+// Every exchange is bank-conflict free with the one-slot-in-16 padding.
+template <int DIR, bool NAT_IN, class V, class C>
+__device__ __forceinline__ void line_fft4096_wl(CV<V> (&x)[16], int t, const Planes<V> &sm, const TwShared<C> &tw) {
+    const int hi = t >> 4, lo = t & 15;
+    // W4096^(m r) for m = m_lo + 16 m_hi (the factors of TwShared), or
+    // W256^(m_lo r) when m_hi < 0
+    auto twiddle = [&](int m_lo, int m_hi) {
+        const C *t1 = tw.t1 + m_lo, *t2 = tw.t2 + m_lo, *t1h = tw.t1 + m_hi;
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            C w;
+            if (m_hi < 0) w = t1[(r - 1) * 16];
+            else {
+                const C a = t2[(r - 1) * 16], b = t1h[(r - 1) * 16];
+                w = C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+            }
+            x[r] = cmul_s(x[r], w.x, DIR > 0 ? w.y : -w.y);
+        }
+    };
+    // padded slots: spad(base + r stride) = spad(base) + r (stride + stride / 16)
+    // for strides that are multiples of 16, and spad(base) + r for stride 1
+    // from a multiple of 16 (the only forms used below)
+    auto store = [&](int base, auto sc) {
+        constexpr int stride = decltype(sc)::value, ps = stride == 1 ? 1 : stride + stride / 16;
+        const int b = spad(base);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sm.st_raw(b + r * ps, x[r]);
+    };
+    auto load = [&](int base, auto sc) {
+        constexpr int stride = decltype(sc)::value, ps = stride == 1 ? 1 : stride + stride / 16;
+        const int b = spad(base);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = sm.ld_raw(b + r * ps);
+    };
+    using S1 = std::integral_constant<int, 1>;
+    using S16 = std::integral_constant<int, 16>;
+    using S256 = std::integral_constant<int, 256>;
+    dft<16, DIR>(x);                                                          // over a
+    twiddle(NAT_IN ? lo : hi, NAT_IN ? hi : lo);                             // W4096^((16 b + c) k_a)
+    if constexpr (NAT_IN) {
+        __syncthreads();
+        store(t, S256{});             // slot 256 k_a + 16 b + c
+        __syncthreads();
+        load(256 * hi + lo, S16{});   // (k_a, c) = (hi, lo), b = r
+    } else {
+        __syncwarp();
+        store(256 * hi + lo, S16{});  // slot 256 c + 16 k_a + b
+        __syncwarp();
+        load(256 * hi + 16 * lo, S1{});  // (k_a, c) = (lo, hi), b = r
+    }
+    dft<16, DIR>(x);                                                          // over b
+    twiddle(NAT_IN ? lo : hi, -1);                                           // W256^(c k_b)
+    if constexpr (NAT_IN) {
+        __syncwarp();
+        store(256 * hi + lo, S16{});     // slot 256 k_a + 16 k_b + c
+        __syncwarp();
+        load(256 * hi + 16 * lo, S1{});  // (k_a, k_b) = (hi, lo), c = r
+    } else {
+        __syncthreads();
+        store(256 * hi + lo, S16{});  // slot 256 c + 16 k_b + k_a
+        __syncthreads();
+        load(t, S256{});              // (k_a, k_b) = (lo, hi), c = r
+    }
+    dft<16, DIR>(x);                                                          // over c
+}
+
 }  // namespace flame

@@ -65,6 +65,7 @@ int ilog2(int n) {
 constexpr int kGraphChunk = 256;  // steps per captured graph
 constexpr int kBatchChunk = 8;    // ensemble steps per captured graph
 constexpr int kGraphCache = 8;
+constexpr int kRetiredMax = 64;
 
 }  // namespace
 
@@ -164,6 +165,11 @@ struct flame_ctx {
     int *status;
     cudaStream_t cap;  // capture stream
     std::vector<GraphEntry> graphs;
+    // graphs evicted from the caches above, which a stream may still be
+    // running: destroyed by flame_destroy after its device synchronisation,
+    // or all at once when kRetiredMax of them have piled up, so that an
+    // eviction does not wait for the device
+    std::vector<cudaGraphExec_t> retired;
     // ensemble state (owned by the first handle of a batch call): the
     // descriptors, then the flames' uv maps and gk maps (FP32)
     void *batch_desc = nullptr;
@@ -231,6 +237,7 @@ void free_ctx(flame_ctx *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     for (auto &g : h->adj_graphs) cudaGraphExecDestroy(g.exec);
+    for (cudaGraphExec_t g : h->retired) cudaGraphExecDestroy(g);
     for (auto &g : h->batch_graphs) cudaGraphExecDestroy(g.second);
     cudaFree(h->batch_desc);
     cudaFreeHost(h->batch_host);
@@ -562,7 +569,8 @@ flame_status autotune(flame_ctx *h) {
                        : va == 2 ? flame::kVariantRadix8A
                        : va      ? flame::kVariantDirect
                                  : flame::kVariantDefault;
-            h->var_b = vb == 3   ? flame::kVariantOneLineB
+            h->var_b = vb == 4   ? flame::kVariantWarpB
+                       : vb == 3 ? flame::kVariantOneLineB
                        : vb == 2 ? flame::kVariantTmaB
                        : vb      ? flame::kVariantRadix8
                                  : flame::kVariantDefault;
@@ -608,6 +616,8 @@ flame_status autotune(flame_ctx *h) {
             if (h->var_b == flame::kVariantTmaB && !h->has_gk_map) h->var_b = flame::kVariantDefault;
             if (h->var_a_bat == flame::kVariantTma && !h->has_uv_map) h->var_a_bat = flame::kVariantDefault;
             if (h->var_b_bat == flame::kVariantTmaB && !h->has_gk_map) h->var_b_bat = flame::kVariantDefault;
+            if (h->var_b == flame::kVariantWarpB && !h->has_gk_map) h->var_b = flame::kVariantDefault;
+            if (h->var_b_bat == flame::kVariantWarpB && !h->has_gk_map) h->var_b_bat = flame::kVariantDefault;
             h->fuse = it->second.fuse != 0 && fuse_allowed(h);
             g_tune[key] = TuneChoice{h->var_a, h->var_b, h->fuse ? 1 : 0, h->var_a_bat, h->var_b_bat};
             return FLAME_OK;
@@ -664,7 +674,8 @@ flame_status autotune(flame_ctx *h) {
     // brings the one-line pass C)
     const int avars[5] = {flame::kVariantDefault, flame::kVariantDirect, flame::kVariantRadix8A, flame::kVariantTma,
                           flame::kVariantOneLine};
-    const int bvars[4] = {flame::kVariantDefault, flame::kVariantRadix8, flame::kVariantTmaB, flame::kVariantOneLineB};
+    const int bvars[5] = {flame::kVariantDefault, flame::kVariantRadix8, flame::kVariantTmaB, flame::kVariantOneLineB,
+                          flame::kVariantWarpB};
     float best_a = 1e30f, best_b = 1e30f, best_a2 = 1e30f, best_b2 = 1e30f;
     for (int v : avars) {
         if (v == flame::kVariantTma && !h->has_uv_map) continue;
@@ -684,8 +695,13 @@ flame_status autotune(flame_ctx *h) {
     for (int v : bvars) {
         if (v == flame::kVariantTmaB && !h->has_gk_map) continue;
         if (v == flame::kVariantOneLineB && h->logm > 11) continue;
+        if (v == flame::kVariantWarpB && (h->logm != 12 || !h->has_gk_map)) continue;
         float ms = 0;
         if (e == cudaSuccess) e = time_it(1, v, &ms);
+        // the warp-local variant measures level with variant 2 (within the
+        // timing noise): it is taken only when clearly faster, so that the
+        // choice does not flip from run to run
+        if (v == flame::kVariantWarpB) ms *= 1.02f;
         if (e == cudaSuccess && ms < best_b) {
             best_b = ms;
             h->var_b = v;
@@ -755,6 +771,18 @@ flame_status capture_steps(flame_ctx *h, const FlameDesc &d, int scheme, int n, 
     return FLAME_OK;
 }
 
+// An evicted graph may still be pending on some stream: it joins the
+// retired list instead of being destroyed now.
+cudaError_t retire_graph(flame_ctx *h, cudaGraphExec_t exec) {
+    h->retired.push_back(exec);
+    if ((int)h->retired.size() < kRetiredMax) return cudaSuccess;
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    for (cudaGraphExec_t g : h->retired) cudaGraphExecDestroy(g);
+    h->retired.clear();
+    return cudaSuccess;
+}
+
 flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int scheme, int n,
                         cudaGraphExec_t *out) {
     for (auto &g : h->graphs)
@@ -765,9 +793,7 @@ flame_status step_graph(flame_ctx *h, void *state, double *mean, double *t, int 
             return FLAME_OK;
         }
     if ((int)h->graphs.size() >= kGraphCache) {
-        // an evicted graph may still be pending on some stream
-        CUDA_TRY(cudaDeviceSynchronize());
-        cudaGraphExecDestroy(h->graphs.front().exec);
+        CUDA_TRY(retire_graph(h, h->graphs.front().exec));
         h->graphs.erase(h->graphs.begin());
     }
     cudaGraphExec_t exec;
@@ -1530,9 +1556,8 @@ flame_status flame_adjoint(flame_t h, const void *state0, const double *mean0, c
     for (auto &g : h->adj_graphs)
         if (g.key == key) exec = g.exec;
     if (!exec) {
-        if (h->adj_graphs.size() >= 4) {  // an evicted graph may still be pending on some stream
-            CUDA_TRY(cudaDeviceSynchronize());
-            cudaGraphExecDestroy(h->adj_graphs.front().exec);
+        if (h->adj_graphs.size() >= 4) {
+            CUDA_TRY(retire_graph(h, h->adj_graphs.front().exec));
             h->adj_graphs.erase(h->adj_graphs.begin());
         }
         cudaGraph_t graph = nullptr;

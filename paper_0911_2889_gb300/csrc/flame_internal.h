@@ -68,6 +68,7 @@ constexpr int kVariantTma = 3;      // pass A: column written by tensor stores (
 constexpr int kVariantTmaB = 2;     // pass B: row pair written by tensor stores (FP32)
 constexpr int kVariantOneLine = 4;  // pass A (and with it pass C): one line per thread group (FP32, 2^8..2^11)
 constexpr int kVariantOneLineB = 3; // pass B: one line per thread group (FP32, 2^8..2^11)
+constexpr int kVariantWarpB = 4;    // pass B: 4096-point rows with warp-local exchanges, tensor-store write-out (FP32)
 
 // Plain-old-data arguments of the step kernels.
 struct StepArgs {

@@ -726,7 +726,7 @@ template <class F> __device__ __forceinline__ F group_sum(F v, int T, F *scratch
     return s;
 }
 
-template <class R, int LOG, int E, bool TMA = false, bool GMAP = false, bool AREA = false>
+template <class R, int LOG, int E, bool TMA = false, bool GMAP = false, bool AREA = false, bool WL = false>
 __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int ntiles, int pf,
                                            const CUtensorMap *tm = nullptr) {
     griddep_wait();
@@ -768,9 +768,15 @@ __device__ __forceinline__ void passB_body(const FlameDesc &d, int tile, int nti
         if constexpr (STW) return Pt(k);
         else return __ldg(P + k);
     };
+    // WL: 4096-point rows with the warp-local exchanges of line_fft4096_wl;
+    // the inverse transforms take natural order and leave the points in
+    // digit-swapped order, which the pointwise |z|^2 and the forward
+    // transform (digit-swapped in, natural out) take as they are
+    static_assert(!WL || (STW && LOG == 12 && !AREA), "warp-local exchanges: FP32 4096-point rows");
     auto fft = [&](auto dirc, CV<V>(&x)[E]) {
         constexpr int DIR = decltype(dirc)::value;
-        if constexpr (STW) fft_line_s<DIR, LS>(x, t, sm, twm, stw);
+        if constexpr (WL) line_fft4096_wl<DIR, (DIR > 0)>(x, t, sm, TwShared<C>{stw, stw + 240});
+        else if constexpr (STW) fft_line_s<DIR, LS>(x, t, sm, twm, stw);
         else fft_line_e<DIR, LOG, E>(x, a.logm, t, sm, twm);
     };
 
@@ -1657,6 +1663,17 @@ template <class R, int LOG>
 __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBt_n(const FlameDesc *__restrict__ ds, int pf,
                                                                const CUtensorMap *maps) {
     passB_body<R, LOG, 16, true, true>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf, maps + blockIdx.y);
+}
+// 4096-point rows with warp-local exchanges (line_fft4096_wl), G written out
+// by tensor stores
+template <class R>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBw(FlameDesc d, int pf, const __grid_constant__ CUtensorMap tm) {
+    passB_body<R, 12, 16, true, false, false, true>(d, blockIdx.x, gridDim.x, pf, &tm);
+}
+template <class R>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBw_n(const FlameDesc *__restrict__ ds, int pf,
+                                                                 const CUtensorMap *maps) {
+    passB_body<R, 12, 16, true, true, false, true>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf, maps + blockIdx.y);
 }
 template <class R, int LOG>
 __global__ void __launch_bounds__(512, 2) k_passB8_n(const FlameDesc *__restrict__ ds, int pf) {

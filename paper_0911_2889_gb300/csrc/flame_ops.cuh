@@ -412,7 +412,14 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        if (sizeof(R) == 4 && L > 0 && variant == kVariantTmaB && gk_map) {  // tensor-store write-out
+        if constexpr (sizeof(R) == 4 && L == 12) if (variant == kVariantWarpB && gk_map) {
+            Geom gb = g;
+            gb.smem += kTwSmemBytes;
+            const int pf = resident_ctas((const void *)k_passBw<R>, gb);
+            err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBw<R>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf, *gk_map);
+            return;
+        }
+        if (sizeof(R) == 4 && L > 0 && (variant == kVariantTmaB || variant == kVariantWarpB) && gk_map) {  // tensor-store write-out
             Geom gb = g;
             if (kSharedTw<R, L, 16>) gb.smem += kTwSmemBytes;
             const int pf = resident_ctas((const void *)k_passBt<R, L>, gb);
@@ -625,7 +632,11 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        if (sizeof(R) == 4 && L > 0 && variant == kVariantTmaB && maps) {
+        if constexpr (sizeof(R) == 4 && L == 12) if (variant == kVariantWarpB && maps) {
+            err = launch_cl(k_passBw_n<R>, dim3(g.blocks, n), g.threads, g.smem + kTwSmemBytes, s, 1, ds, 0, maps);
+            return;
+        }
+        if (sizeof(R) == 4 && L > 0 && (variant == kVariantTmaB || variant == kVariantWarpB) && maps) {
             const size_t sm = g.smem + (kSharedTw<R, L, 16> ? kTwSmemBytes : 0);
             err = launch_cl(k_passBt_n<R, L>, dim3(g.blocks, n), g.threads, sm, s, 1, ds, 0, maps);
         } else if (sizeof(R) == 4 && L > 0 && variant == kVariantRadix8) {

@@ -21,7 +21,7 @@ import torch
 from increments import INC_MAX_TOL, INC_TOL, dt_for_fraction, increment_errors
 from paper_0911_2889_gb300 import inputs
 
-VARIANTS = ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2", "4,3", "4,0", "0,3"]
+VARIANTS = ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2", "4,3", "4,0", "0,3", "3,4", "1,4"]
 _CACHE = {}
 
 

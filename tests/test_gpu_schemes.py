@@ -154,6 +154,36 @@ def test_multi_step_graphs_equal_single_steps(fl, monkeypatch, scheme, shape):
 
 
 @pytest.mark.gpu
+def test_graph_cache_eviction_keeps_pending_graphs(fl):
+    # 20 buffer sets stepped in turn, each with a 2- and a 3-step call, all
+    # enqueued on one stream without waiting: 40 distinct graphs against a
+    # cache of 8, so graphs are evicted while launches of them are still
+    # queued; every buffer set ends with exactly its single-step result
+    n1, n2 = 256, 512
+    f = fl.Flame(n1, n2, prec="fp32", gamma=0.8, t0=20.0, dt=1e-2)
+    stream = torch.cuda.Stream()
+    sets, refs = [], []
+    for i in range(20):
+        st0 = inputs.spectrum_ic(n1, n2, 32, 300 + i, amp=1e-2, K1=f.K1, K2=f.K2)
+        a, b = _dev(fl, f, st0), _dev(fl, f, st0)
+        sets.append((a,) + _scalars(0.1, 20.0))
+        refs.append((b,) + _scalars(0.1, 20.0))
+    torch.cuda.synchronize()
+    for rep in range(2):
+        for a, ma, ta in sets:
+            f.step(a, ma, ta, 2 + rep, stream)
+    stream.synchronize()
+    for b, mb, tb in refs:
+        for _ in range(5):
+            f.step(b, mb, tb, 1)
+    torch.cuda.synchronize()
+    for (a, ma, ta), (b, mb, tb) in zip(sets, refs):
+        assert torch.equal(a, b)
+        assert ma.item() == mb.item() and ta.item() == tb.item()
+    f.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 @pytest.mark.parametrize("scheme", ["euler", "if"])
 def test_forcing_matches_oracle(fl, orc, prec, tol, scheme):

@@ -263,7 +263,7 @@ def test_batch_of_compile_time_grids_equals_individual(fl, monkeypatch, variants
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("variants", ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2", "4,3", "4,0", "0,3"])
+@pytest.mark.parametrize("variants", ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2", "4,3", "4,0", "0,3", "3,4", "1,4"])
 @pytest.mark.parametrize("shape", [(256, 512), (1024, 2048), (4096, 8192)])
 def test_every_tuned_variant_matches_oracle(fl, orc, monkeypatch, variants, shape):
     # the autotuner may pick either shape of passes A and B; each must be exact
@@ -523,18 +523,21 @@ def test_fp64_short_line_kernels_both_shapes(fl, orc, monkeypatch, points):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("memory", ["pinned", "pageable"])
 @pytest.mark.parametrize("prec,shape,nsteps", [
     ("fp64", (128, 256), 1), ("fp64", (128, 256), 3), ("fp32", (256, 512), 1), ("fp32", (1024, 2048), 4),
     ("fp32", (4096, 8192), 1), ("fp32", (512, 256), 2)])
-def test_step_on_host_buffers_equals_device_steps(fl, prec, shape, nsteps):
+def test_step_on_host_buffers_equals_device_steps(fl, prec, shape, nsteps, memory):
     # flame_step_host (chunked copies overlapping the first pass A and the
     # last pass C, partial launches over the tiles) gives exactly the
-    # results of flame_step on device buffers
+    # results of flame_step on device buffers, from pinned or pageable
+    # host memory
     n1, n2 = shape
     f, st0, state, mean, t = _setup(fl, n1, n2, prec, 64, 33, amp=1e-2)
-    hs = state.cpu().pin_memory()
-    hm = torch.zeros(1, dtype=torch.float64).pin_memory()
-    ht = torch.full((1,), float(f.params.t0), dtype=torch.float64).pin_memory()
+    pin = (lambda x: x.pin_memory()) if memory != "pageable" else (lambda x: x)
+    hs = pin(state.cpu())
+    hm = pin(torch.zeros(1, dtype=torch.float64))
+    ht = pin(torch.full((1,), float(f.params.t0), dtype=torch.float64))
     f.step_host(hs, hm, ht, nsteps)
     f.step(state, mean, t, nsteps)
     torch.cuda.synchronize()
