@@ -1675,6 +1675,15 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBw_n(const FlameDesc
                                                                  const CUtensorMap *maps) {
     passB_body<R, 12, 16, true, true, false, true>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf, maps + blockIdx.y);
 }
+// the same transforms with G written by direct stores (no tensor map): the
+// arithmetic, and so the bits, of k_passBw
+template <class R> __global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBwd(FlameDesc d, int pf) {
+    passB_body<R, 12, 16, false, false, false, true>(d, blockIdx.x, gridDim.x, pf);
+}
+template <class R>
+__global__ void __launch_bounds__(256, kMinBlocks<R>) k_passBwd_n(const FlameDesc *__restrict__ ds, int pf) {
+    passB_body<R, 12, 16, false, false, false, true>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);
+}
 template <class R, int LOG>
 __global__ void __launch_bounds__(512, 2) k_passB8_n(const FlameDesc *__restrict__ ds, int pf) {
     passB_body<R, LOG, 8>(ds[blockIdx.y], blockIdx.x, gridDim.x, pf);

@@ -412,11 +412,17 @@ cudaError_t Ops<R>::passB(const FlameDesc &d, cudaStream_t s, int variant, const
     cudaError_t err = cudaSuccess;
     with_log<R>(d.a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        if constexpr (sizeof(R) == 4 && L == 12) if (variant == kVariantWarpB && gk_map) {
+        if constexpr (sizeof(R) == 4 && L == 12) if (variant == kVariantWarpB) {
             Geom gb = g;
             gb.smem += kTwSmemBytes;
-            const int pf = resident_ctas((const void *)k_passBw<R>, gb);
-            err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBw<R>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf, *gk_map);
+            if (gk_map) {
+                const int pf = resident_ctas((const void *)k_passBw<R>, gb);
+                err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBw<R>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf,
+                               *gk_map);
+            } else {
+                const int pf = resident_ctas((const void *)k_passBwd<R>, gb);
+                err = launch_s(L2Window{nullptr, 0, 0.f}, k_passBwd<R>, dim3(gb.blocks), gb.threads, gb.smem, s, 1, d, pf);
+            }
             return;
         }
         if (sizeof(R) == 4 && L > 0 && (variant == kVariantTmaB || variant == kVariantWarpB) && gk_map) {  // tensor-store write-out
@@ -632,8 +638,9 @@ cudaError_t Ops<R>::passB_batch(const FlameDesc *ds, int n, const StepArgs &a, c
     cudaError_t err = cudaSuccess;
     with_log<R>(a.logm, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
-        if constexpr (sizeof(R) == 4 && L == 12) if (variant == kVariantWarpB && maps) {
-            err = launch_cl(k_passBw_n<R>, dim3(g.blocks, n), g.threads, g.smem + kTwSmemBytes, s, 1, ds, 0, maps);
+        if constexpr (sizeof(R) == 4 && L == 12) if (variant == kVariantWarpB) {
+            if (maps) err = launch_cl(k_passBw_n<R>, dim3(g.blocks, n), g.threads, g.smem + kTwSmemBytes, s, 1, ds, 0, maps);
+            else err = launch_cl(k_passBwd_n<R>, dim3(g.blocks, n), g.threads, g.smem + kTwSmemBytes, s, 1, ds, 0);
             return;
         }
         if (sizeof(R) == 4 && L > 0 && (variant == kVariantTmaB || variant == kVariantWarpB) && maps) {

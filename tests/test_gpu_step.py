@@ -263,6 +263,34 @@ def test_batch_of_compile_time_grids_equals_individual(fl, monkeypatch, variants
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("batch_tma", ["0", "1"])
+def test_batch_of_warp_local_rows_equals_individual(fl, monkeypatch, batch_tma):
+    # pass B variant 4 (warp-local exchanges, N2 = 8192) in the grouped
+    # launches, with and without per-flame tensor maps: the same transforms
+    # as the single flame's kernel, so the same bits
+    monkeypatch.setenv("FLAME_FORCE_VARIANTS", "3,4")
+    monkeypatch.setenv("FLAME_BATCH_TMA", batch_tma)
+    fs, ss, ms, ts, ref = [], [], [], [], []
+    for i in range(2):
+        f, st0, state, mean, t = _setup(fl, 4096, 8192, "fp32", 64, 210 + i, amp=1e-2, gamma=0.7 + 0.05 * i)
+        assert fl.flame_tuning(f.h) == (3, 4)
+        fs.append(f)
+        ss.append(state)
+        ms.append(mean)
+        ts.append(t)
+        ref.append((state.clone(), mean.clone(), t.clone()))
+    fl.flame_step_batch([f.h for f in fs], ss, ms, ts, nsteps=2)
+    for f, (s, m, t) in zip(fs, ref):
+        f.step(s, m, t, 2)
+    torch.cuda.synchronize()
+    for i in range(len(fs)):
+        assert torch.equal(ss[i], ref[i][0]), i
+        assert torch.equal(ms[i], ref[i][1]) and torch.equal(ts[i], ref[i][2])
+    for f in fs:
+        f.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("variants", ["0,0", "1,0", "2,0", "3,0", "0,1", "2,1", "3,1", "3,2", "1,2", "4,3", "4,0", "0,3", "3,4", "1,4"])
 @pytest.mark.parametrize("shape", [(256, 512), (1024, 2048), (4096, 8192)])
 def test_every_tuned_variant_matches_oracle(fl, orc, monkeypatch, variants, shape):
