@@ -10,7 +10,7 @@ handle's status words (FLAME_EBOUNDS).  It stands in for a memory checker.
 - A selection of the GPU parity tests (tiny grids from 16 x 32 up to the
   4096 x 8192 benchmark grid, both precisions, every integrator, forcing,
   the per-step record with the area, ensembles, the fused column pass, the
-  standalone FFTs, host-buffer steps) runs again in a child process against
+  warp-local pass B variant, the standalone FFTs, host-buffer steps) runs again in a child process against
   the index-checking library: each must still match the oracle, and no
   handle may end with a failed check (conftest's autouse fixture).
 - The normal library has no checks: the probe answers FLAME_EUNSUPPORTED.
@@ -30,7 +30,7 @@ CHILD_SELECT = ("one_step_identical_input or linear_and_nonlinear_only or fp32_f
                 "or batch_equals_individual or batch_of_compile_time_grids or fused_multi_step "
                 "or state_from_field or heun_step_matches or fp64_short_line or host_buffers "
                 "or if_step_matches or forcing_matches or multi_step_graphs "
-                "or r2c_c2r_parity or device_record")
+                "or r2c_c2r_parity or device_record or warp_local_rows")
 
 
 def _debug_env():
