@@ -308,10 +308,13 @@ __global__ void __launch_bounds__(256, kMinBlocks<R>) k_rows_c2r(const CplxT<R> 
 
 // Column FFT of length n = 2^logn over ncols columns of a row-major array
 // with row stride ld (complex units); columns 2p, 2p+1 form one thread
-// group; in may equal out.
-template <class R, int DIR, int LOG>
-__global__ void __launch_bounds__(256, kMinBlocks<R>) k_cols(const CplxT<R> *in, CplxT<R> *out, int logn, int ncols, int ld,
-                                              const CplxT<R> *__restrict__ tw, int *status) {
+// group; in may equal out.  The G groups of a CTA take adjacent column
+// pairs and interleave their threads (group = thread mod G), so that one
+// warp's access to a row covers G adjacent column pairs: NT = 512 threads
+// (FP32, 2^10 .. 2^12 points) widens that from 16 to 32 bytes and more.
+template <class R, int DIR, int LOG, int NT = 256>
+__global__ void __launch_bounds__(NT, NT == 256 ? kMinBlocks<R> : 1)
+    k_cols(const CplxT<R> *in, CplxT<R> *out, int logn, int ncols, int ld, const CplxT<R> *__restrict__ tw, int *status) {
     using V = typename VecOf<R>::type;
     using C = CplxT<R>;
     extern __shared__ __align__(16) unsigned char smraw[];

@@ -240,6 +240,19 @@ cudaError_t Ops<R>::cols(const C *in, C *out, int logn, int ncols, int ld, int d
     cudaError_t err = cudaSuccess;
     with_log<R>(logn, [&](auto lc) {
         constexpr int L = decltype(lc)::value;
+        // FP32 columns of 2^10 .. 2^12 points: 512-thread CTAs of 512/T line
+        // groups (one CTA per SM), where the grid still has two CTAs per SM
+        if constexpr (sizeof(R) == 4 && L >= 10 && L <= 12) {
+            constexpr int G = 512 / ((1 << L) >> 4);
+            const int npairs = (ncols + 1) / 2;
+            if (npairs >= 2 * G * sm_count()) {
+                const dim3 grid((npairs + G - 1) / G);
+                const size_t smem = G * group_smem<R>(L);
+                if (dir < 0) err = launch_cl(k_cols<R, -1, L, 512>, grid, 512, smem, s, 1, in, out, logn, ncols, ld, tw, status);
+                else err = launch_cl(k_cols<R, 1, L, 512>, grid, 512, smem, s, 1, in, out, logn, ncols, ld, tw, status);
+                return;
+            }
+        }
         if (dir < 0)
             err = launch_cl(k_cols<R, -1, L>, dim3(g.blocks), g.threads, g.smem, s, 1, in, out, logn, ncols, ld, tw,
                             status);
